@@ -1,0 +1,366 @@
+/*
+ * Bounce-map oracle: a plain, slow FP64 CPU restatement of the discrete
+ * bounce-to-bounce map of the intracavity field of a microchip laser
+ * (A. Yu. Okulov, "Two-dimensional periodic and quasiperiodic spatial
+ * structures in microchip laser resonator": the nonlocal map of eq.
+ * conv_map, its Fresnel-kernel form eq. complex_8F with the complex aperture
+ * of eq. complex_aperture2, and the operator exponent of eq.
+ * limit_of_operators_renorm_final).
+ *
+ * TEST INFRASTRUCTURE ONLY.  The test suite, the smoke check and the CPU
+ * baseline leg of the benchmark are the only callers.  The CUDA library
+ * never links, loads or calls this file, and this file shares no code,
+ * header, table or constant generator with it.
+ *
+ * Conventions (the readings of the paper that the map below takes):
+ *   - Field E and inversion N are n x n, row-major, E[y*n + x], complex
+ *     double (C99 layout: re, im interleaved).
+ *   - Pixel centres: x_j = (j - n/2) / (n/2); the window half-width is 1.
+ *   - Forward DFT kernel exp(-2 pi i j k / n), unnormalised.
+ *   - Signed frequency index m = k for k < n/2, else k - n.
+ *   - Diffraction over one iterate (eq. limit_of_operators_renorm_final,
+ *     exp[i z lap / 2k] on a plane wave exp(i kappa x) gives
+ *     exp(-i z kappa^2 / 2k)):
+ *         E' = IDFT2( DFT2(E) * exp(-i pi alpha (mx^2 + my^2)) ) / n^2,
+ *     with alpha = lambda z / W^2 = (D/W)^2 / N_F, N_F = D^2/(lambda z).
+ *   - Gain slice, mirror and absorbing edge (eq. conv_map's local map f,
+ *     the modulus D_0 of eq. complex_aperture2, the saturable-gain form of
+ *     the class-B equations):
+ *         I = |E'|^2
+ *         E_{n+1} = sqrt(R) * A(x) A(y) * exp(N_n / 2) * E'
+ *         N_{n+1} = N_n + (N0 - N_n (1 + I / Isat)) / T1
+ *     A = 0 on the outer `edge` pixels of each axis, 1 inside.
+ *   - Pump N0 = g0 * exp(-(r / r_p)^order) (super-Gaussian), g0 (uniform)
+ *     or g0 * profile (array).
+ *
+ * Parity unpinned: the long-horizon trajectory (beyond a few tens of
+ * bounces the map is chaotic; long runs are compared by statistics only).
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef double complex cplx;
+
+#define ORC_PI 3.14159265358979323846
+
+/* Parameters of one resonator; mirrored field by field by the ctypes
+ * structure in oracle/__init__.py. */
+typedef struct {
+    int n;                 /* grid side */
+    double alpha;          /* lambda z / W^2 */
+    double g0;             /* small-signal intensity gain exponent per pass */
+    double T1;             /* inversion relaxation time, in bounces */
+    double R;              /* mirror intensity reflectivity */
+    double Isat;           /* saturation intensity */
+    int edge;              /* absorbing edge width in pixels */
+    int pump_kind;         /* 0 super-Gaussian, 1 uniform, 2 array */
+    double pump_order;     /* super-Gaussian exponent */
+    double pump_radius;    /* r_p as a fraction of the window half-width */
+    const double *pump_profile; /* n*n values in [0,1] when pump_kind == 2 */
+} orc_params;
+
+int orc_version(void) { return 1; }
+
+static int is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+/* Signed frequency of DFT bin k. */
+static int signed_freq(int k, int n) { return k < n / 2 ? k : k - n; }
+
+/* ------------------------------------------------------------------------
+ * Discrete Fourier transforms (the library primitive of the split-step
+ * method; eq. limit_of_operators_renorm_final is diagonal in this basis).
+ * ---------------------------------------------------------------------- */
+
+/* Brute-force DFT straight from its definition:
+ * y[k] = sum_j x[j] exp(sign * 2 pi i j k / n).  The product j*k is reduced
+ * modulo n in integers before the angle is formed, so the argument of cos
+ * and sin stays within one turn. */
+void orc_dft(const cplx *x, cplx *y, int n, int sign)
+{
+    for (int k = 0; k < n; ++k) {
+        cplx acc = 0;
+        for (int j = 0; j < n; ++j) {
+            long long jk = ((long long)j * k) % n;
+            double ang = sign * 2.0 * ORC_PI * (double)jk / (double)n;
+            acc += x[j] * (cos(ang) + sin(ang) * _Complex_I);
+        }
+        y[k] = acc;
+    }
+}
+
+/* Radix-2 Cooley-Tukey, decimation in time: bit-reversal reordering, then
+ * log2(n) stages of butterflies.  Each twiddle is evaluated directly with
+ * cos/sin (no recurrence).  Returns -1 if n is not a power of two. */
+int orc_fft(cplx *x, int n, int sign)
+{
+    if (!is_pow2(n)) return -1;
+    for (int i = 1, j = 0; i < n; ++i) {
+        int bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) { cplx t = x[i]; x[i] = x[j]; x[j] = t; }
+    }
+    for (int len = 2; len <= n; len <<= 1) {
+        int half = len / 2;
+        for (int k = 0; k < half; ++k) {
+            double ang = sign * 2.0 * ORC_PI * (double)k / (double)len;
+            cplx w = cos(ang) + sin(ang) * _Complex_I;
+            for (int s = 0; s < n; s += len) {
+                cplx u = x[s + k];
+                cplx v = x[s + k + half] * w;
+                x[s + k] = u + v;
+                x[s + k + half] = u - v;
+            }
+        }
+    }
+    return 0;
+}
+
+/* 2-D transform of an n x n row-major array: every row, then every column. */
+int orc_fft2(cplx *a, int n, int sign, int nthreads)
+{
+    if (!is_pow2(n)) return -1;
+    if (nthreads < 1) nthreads = 1;
+    (void)nthreads;
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+    for (int y = 0; y < n; ++y) orc_fft(a + (size_t)y * n, n, sign);
+#pragma omp parallel num_threads(nthreads)
+    {
+        cplx *col = (cplx *)malloc(sizeof(cplx) * (size_t)n);
+#pragma omp for schedule(static)
+        for (int x = 0; x < n; ++x) {
+            for (int y = 0; y < n; ++y) col[y] = a[(size_t)y * n + x];
+            orc_fft(col, n, sign);
+            for (int y = 0; y < n; ++y) a[(size_t)y * n + x] = col[y];
+        }
+        free(col);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Diffraction over one iterate: the paraxial transfer function
+ * exp(-i pi alpha (mx^2 + my^2)) (eq. limit_of_operators_renorm_final; the
+ * Fresnel kernel of eq. complex_8F in the Fourier basis).
+ * ---------------------------------------------------------------------- */
+
+/* H[ky*n + kx] = exp(-i pi alpha (mx^2 + my^2)).  The product alpha*s with
+ * the integer s = mx^2 + my^2 is formed and reduced modulo 2 in long double,
+ * so the phase keeps its accuracy when pi*alpha*s runs to thousands of
+ * radians. */
+void orc_phase_2d(int n, double alpha, cplx *H)
+{
+    for (int ky = 0; ky < n; ++ky) {
+        long long my = signed_freq(ky, n);
+        for (int kx = 0; kx < n; ++kx) {
+            long long mx = signed_freq(kx, n);
+            long double s = (long double)(mx * mx + my * my);
+            long double t = fmodl((long double)alpha * s, 2.0L);
+            double ph = -ORC_PI * (double)t;
+            H[(size_t)ky * n + kx] = cos(ph) + sin(ph) * _Complex_I;
+        }
+    }
+}
+
+/* E <- IDFT2(DFT2(E) * H) / n^2 with a precomputed H. */
+static void diffract_with(cplx *E, const cplx *H, int n, int nthreads)
+{
+    size_t P = (size_t)n * n;
+    orc_fft2(E, n, -1, nthreads);
+    for (size_t i = 0; i < P; ++i) E[i] *= H[i];
+    orc_fft2(E, n, +1, nthreads);
+    double inv = 1.0 / (double)P;
+    for (size_t i = 0; i < P; ++i) E[i] *= inv;
+}
+
+int orc_diffract(cplx *E, int n, double alpha, int nthreads)
+{
+    if (!is_pow2(n)) return -1;
+    cplx *H = (cplx *)malloc(sizeof(cplx) * (size_t)n * n);
+    if (!H) return -2;
+    orc_phase_2d(n, alpha, H);
+    diffract_with(E, H, n, nthreads);
+    free(H);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Pump, i.e. the unsaturated inversion N0(x, y).
+ * ---------------------------------------------------------------------- */
+
+static double pixel_coord(int j, int n) { return (double)(j - n / 2) / (double)(n / 2); }
+
+void orc_pump(const orc_params *p, double *N0)
+{
+    int n = p->n;
+    for (int y = 0; y < n; ++y) {
+        for (int x = 0; x < n; ++x) {
+            double v;
+            if (p->pump_kind == 1) {
+                v = p->g0;
+            } else if (p->pump_kind == 2) {
+                v = p->g0 * p->pump_profile[(size_t)y * n + x];
+            } else {
+                double xr = pixel_coord(x, n), yr = pixel_coord(y, n);
+                double r = sqrt(xr * xr + yr * yr);
+                v = p->g0 * exp(-pow(r / p->pump_radius, p->pump_order));
+            }
+            N0[(size_t)y * n + x] = v;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Seeded initial noise: splitmix64 (Steele, Lea & Flood, "Fast splittable
+ * pseudorandom number generators", OOPSLA 2014) used as a counter-based
+ * generator, then the Box-Muller transform.
+ * ---------------------------------------------------------------------- */
+
+/* The c-th output (c = 0, 1, ...) of a splitmix64 stream whose state starts
+ * at `seed`: the state after c+1 increments of the golden gamma, passed
+ * through the splitmix64 finaliser. */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t c)
+{
+    uint64_t z = seed + (c + 1) * 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+/* E[i] = sigma * sqrt(-2 ln(1 - u1)) * exp(2 pi i u2), sigma = amp / sqrt(2),
+ * with u1, u2 the top 53 bits of outputs 2i and 2i+1 scaled to [0, 1).
+ * Each of Re and Im is then normal with variance amp^2 / 2, so
+ * E|E|^2 = amp^2. */
+void orc_noise(int n, uint64_t seed, double amp, cplx *E)
+{
+    size_t P = (size_t)n * n;
+    double sigma = amp / sqrt(2.0);
+    for (size_t i = 0; i < P; ++i) {
+        double u1 = (double)(orc_splitmix64(seed, 2 * (uint64_t)i) >> 11) * 0x1.0p-53;
+        double u2 = (double)(orc_splitmix64(seed, 2 * (uint64_t)i + 1) >> 11) * 0x1.0p-53;
+        double rho = sigma * sqrt(-2.0 * log(1.0 - u1));
+        double th = 2.0 * ORC_PI * u2;
+        E[i] = rho * cos(th) + rho * sin(th) * _Complex_I;
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * The bounce map.
+ * ---------------------------------------------------------------------- */
+
+static int inside_edge(int j, int n, int edge) { return j >= edge && j < n - edge; }
+
+/* Local part of the map (eq. conv_map's f, the mirror and the aperture
+ * modulus D_0): gain against the frozen inversion N_n, then relaxation of
+ * N toward the pump driven by the arriving intensity |E'|^2. */
+static void gain_step(cplx *E, double *N, const double *N0, const orc_params *p)
+{
+    int n = p->n;
+    double sqrtR = sqrt(p->R);
+    for (int y = 0; y < n; ++y) {
+        for (int x = 0; x < n; ++x) {
+            size_t i = (size_t)y * n + x;
+            double inten = creal(E[i]) * creal(E[i]) + cimag(E[i]) * cimag(E[i]);
+            double Nn = N[i];
+            double A = (inside_edge(x, n, p->edge) && inside_edge(y, n, p->edge)) ? 1.0 : 0.0;
+            E[i] = sqrtR * A * exp(0.5 * Nn) * E[i];
+            N[i] = Nn + (N0[i] - Nn * (1.0 + inten / p->Isat)) / p->T1;
+        }
+    }
+}
+
+static double mean_intensity(const cplx *E, size_t P)
+{
+    double s = 0.0;
+    for (size_t i = 0; i < P; ++i) s += creal(E[i]) * creal(E[i]) + cimag(E[i]) * cimag(E[i]);
+    return s / (double)P;
+}
+
+/* Run nb bounces in place on (E, N).  hist (may be NULL) receives the mean
+ * intensity <|E_{b+1}|^2> after each bounce b = 0 .. nb-1.
+ * Returns 0, or -1 on invalid parameters, -2 on allocation failure. */
+int orc_run(const orc_params *p, cplx *E, double *N, long long nb, double *hist, int nthreads)
+{
+    int n = p->n;
+    if (!is_pow2(n) || p->T1 <= 0.0 || p->R < 0.0 || p->Isat <= 0.0 || p->edge < 0) return -1;
+    if (p->pump_kind == 2 && !p->pump_profile) return -1;
+    size_t P = (size_t)n * n;
+    cplx *H = (cplx *)malloc(sizeof(cplx) * P);
+    double *N0 = (double *)malloc(sizeof(double) * P);
+    if (!H || !N0) { free(H); free(N0); return -2; }
+    orc_phase_2d(n, p->alpha, H);
+    orc_pump(p, N0);
+    for (long long b = 0; b < nb; ++b) {
+        diffract_with(E, H, n, nthreads);
+        gain_step(E, N, N0, p);
+        if (hist) hist[b] = mean_intensity(E, P);
+    }
+    free(H);
+    free(N0);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Reporting: the far-field spectrum and its dominant spatial frequency.
+ * ---------------------------------------------------------------------- */
+
+/* S = |DFT2(E)|^2 (unnormalised). */
+int orc_spectrum(const cplx *E, int n, double *S, int nthreads)
+{
+    if (!is_pow2(n)) return -1;
+    size_t P = (size_t)n * n;
+    cplx *T = (cplx *)malloc(sizeof(cplx) * P);
+    if (!T) return -2;
+    memcpy(T, E, sizeof(cplx) * P);
+    orc_fft2(T, n, -1, nthreads);
+    for (size_t i = 0; i < P; ++i) S[i] = creal(T[i]) * creal(T[i]) + cimag(T[i]) * cimag(T[i]);
+    free(T);
+    return 0;
+}
+
+/* Dominant spatial frequency, with m and -m taken as one peak: bin k and its
+ * mirror k' = (-ky mod n, -kx mod n) carry the folded power S[k] + S[k']
+ * (S[k] alone when k' == k), filed under the smaller flat index.  With
+ * ring > 0 only bins with max(|mx|, |my|) >= ring compete.  Ties go to the
+ * smaller flat index.  Writes the signed (mx, my) of the winner, its folded
+ * power, and the largest folded power of any other bin. */
+void orc_spectrum_peak(const double *S, int n, int ring, int *mx_out, int *my_out,
+                       double *peak_out, double *runner_up_out)
+{
+    double best = -1.0, second = -1.0;
+    long long best_k = -1;
+    for (int ky = 0; ky < n; ++ky) {
+        for (int kx = 0; kx < n; ++kx) {
+            long long k = (long long)ky * n + kx;
+            long long kp = (long long)((n - ky) % n) * n + (n - kx) % n;
+            if (kp < k) continue;
+            int mx = signed_freq(kx, n), my = signed_freq(ky, n);
+            int amx = mx < 0 ? -mx : mx, amy = my < 0 ? -my : my;
+            int cheb = amx > amy ? amx : amy;
+            if (cheb < ring) continue;
+            double v = (kp == k) ? S[k] : S[k] + S[kp];
+            if (v > best) {
+                second = best;
+                best = v;
+                best_k = k;
+            } else if (v > second) {
+                second = v;
+            }
+        }
+    }
+    if (best_k < 0) {
+        *mx_out = 0; *my_out = 0; *peak_out = 0.0; *runner_up_out = 0.0;
+        return;
+    }
+    *mx_out = signed_freq((int)(best_k % n), n);
+    *my_out = signed_freq((int)(best_k / n), n);
+    *peak_out = best;
+    *runner_up_out = second < 0.0 ? 0.0 : second;
+}

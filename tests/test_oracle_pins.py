@@ -1,0 +1,329 @@
+"""Pins of the FP64 oracle to things other than itself: library FFTs, brute
+force, closed forms of paraxial optics (Talbot self-imaging, Gaussian-beam
+spreading), fixed points and linearisations of the gain/inversion recursion,
+published generator test vectors, and the paper's printed parameters.
+
+A plausible slip in the oracle (a dropped 1/n^2, a flipped propagator sign, an
+exp(N) for exp(N/2), the updated inversion used in the gain, an off-by-one in
+the absorbing edge) fails at least one test here.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as orc
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def crandn(rng, shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+# ----------------------------------------------------------------- transforms
+
+@pytest.mark.parametrize("n", [8, 16, 32])
+@pytest.mark.parametrize("sign", [-1, +1])
+def test_bruteforce_dft_matches_numpy(n, sign):
+    x = crandn(np.random.default_rng(n), n)
+    ref = np.fft.fft(x) if sign < 0 else np.fft.ifft(x) * n
+    assert np.max(np.abs(orc.dft(x, sign) - ref)) < 1e-12 * n
+
+
+@pytest.mark.parametrize("n", [8, 16, 32, 64, 128])
+@pytest.mark.parametrize("sign", [-1, +1])
+def test_fft_matches_bruteforce_dft(n, sign):
+    x = crandn(np.random.default_rng(100 + n), n)
+    assert rel_l2(orc.fft(x, sign), orc.dft(x, sign)) < 1e-13
+
+
+@pytest.mark.parametrize("n", [8, 32, 64])
+def test_fft2_matches_numpy(n):
+    a = crandn(np.random.default_rng(7), (n, n))
+    assert rel_l2(orc.fft2(a, -1), np.fft.fft2(a)) < 1e-14
+    assert rel_l2(orc.fft2(a, +1), np.fft.ifft2(a) * n * n) < 1e-14
+
+
+def test_fft_rejects_non_power_of_two():
+    with pytest.raises(ValueError):
+        orc.fft(np.ones(12), -1)
+
+
+def test_parseval_and_inverse():
+    a = crandn(np.random.default_rng(3), (64, 64))
+    A = orc.fft2(a, -1)
+    assert abs(np.sum(np.abs(A) ** 2) / a.size - np.sum(np.abs(a) ** 2)) < 1e-10 * np.sum(np.abs(a) ** 2)
+    assert rel_l2(orc.fft2(A, +1) / a.size, a) < 1e-14
+
+
+# --------------------------------------------------------------- diffraction
+
+def test_phase_table_unit_modulus_and_symmetry():
+    n, alpha = 64, 0.0173
+    H = orc.phase_2d(n, alpha)
+    assert np.max(np.abs(np.abs(H) - 1.0)) < 1e-15
+    assert H[0, 0] == 1.0
+    k = np.arange(1, n)
+    # H depends on mx^2 + my^2 only: even in each index and symmetric in (mx, my).
+    assert np.max(np.abs(H[:, k] - H[:, n - k])) < 1e-13
+    assert np.max(np.abs(H - H.T)) < 1e-13
+
+
+def test_phase_table_large_argument_range_reduction():
+    # At 2048^2 and N_F = 1000 the phase pi*alpha*m^2 reaches ~2.1e3 rad; a
+    # value of alpha with a short binary expansion lets the exact phase be
+    # written down: alpha = 2^-10, m = 1024 -> pi * 1024 = 512 turns -> 1.
+    n = 2048
+    H = orc.phase_2d(n, 2.0 ** -10)
+    assert abs(H[0, n // 2] - 1.0) < 1e-15            # m = -1024: alpha m^2 = 1024
+    assert abs(H[0, 1000] - np.exp(-1j * np.pi * (1000 ** 2 % 2048) / 1024.0)) < 1e-14
+
+
+def test_diffraction_is_unitary():
+    a = crandn(np.random.default_rng(11), (64, 64))
+    out = orc.diffract(a, 0.0123)
+    assert abs(np.linalg.norm(out) / np.linalg.norm(a) - 1.0) < 1e-13
+
+
+def _talbot_setup(q=8, n=64, seed=5):
+    """Field with q periods across the window: period p = n/q pixels."""
+    rng = np.random.default_rng(seed)
+    p = n // q
+    return np.tile(crandn(rng, (p, p)), (q, q)), p
+
+
+def _alpha_for_distance(lam, z, W):
+    return lam * z / W ** 2
+
+
+def test_talbot_self_imaging():
+    # Talbot length z_T = 2 p^2 / lambda (introduction, point 3, and the
+    # Talbot condition L = m p^2 / lambda of the exact-solutions section).
+    q, n = 8, 64
+    E, p_px = _talbot_setup(q, n)
+    lam, p = 1.064e-6, 50e-6
+    alpha = _alpha_for_distance(lam, 2 * p * p / lam, q * p)
+    assert abs(alpha - 2.0 / q ** 2) < 1e-15
+    assert rel_l2(orc.diffract(E, 2.0 / q ** 2), E) < 1e-13
+    # A field that is not periodic with p does not self-image.
+    F = crandn(np.random.default_rng(6), (n, n))
+    assert rel_l2(orc.diffract(F, 2.0 / q ** 2), F) > 0.5
+
+
+def test_half_talbot_shifts_by_half_period():
+    # At z_T / 2 = p^2 / lambda the pattern returns shifted by p/2 in x and y
+    # (the in-phase / anti-phase Talbot locking of the multiscale section).
+    q, n = 8, 64
+    E, p = _talbot_setup(q, n)
+    out = orc.diffract(E, 1.0 / q ** 2)
+    assert rel_l2(out, np.roll(E, (p // 2, p // 2), axis=(0, 1))) < 1e-13
+
+
+def test_quarter_talbot_closed_form():
+    # At z_T / 4 each spectral line m = q s picks up exp(-i pi s^2 / 2), i.e.
+    # 1 for even s and -i for odd s: per axis a + b * (half-period shift)
+    # with a = (1 - i)/2, b = (1 + i)/2.
+    q, n = 8, 64
+    E, p = _talbot_setup(q, n)
+    a, b = (1 - 1j) / 2, (1 + 1j) / 2
+    h = p // 2
+    sx = np.roll(E, h, axis=1)
+    sy = np.roll(E, h, axis=0)
+    sxy = np.roll(E, (h, h), axis=(0, 1))
+    expect = a * a * E + a * b * (sx + sy) + b * b * sxy
+    assert rel_l2(orc.diffract(E, 0.5 / q ** 2), expect) < 1e-13
+
+
+def test_gaussian_beam_spreading_matches_paraxial_closed_form():
+    # A Gaussian of width a (window half-width 1) after distance z:
+    # (1 + i zeta)^-1 exp(-r^2 / (2 a^2 (1 + i zeta))), zeta = z / (k a^2),
+    # i.e. the prefactor (1 + i N_f^-1)^-1 and envelope of the exact solution
+    # of the exact-solutions section with N_f = k a^2 / z and F = infinity.
+    # With W = 2: alpha = lambda z / W^2 gives zeta = 2 alpha / (pi a^2).
+    n, a, zeta = 128, 0.1, 0.5
+    alpha = zeta * math.pi * a * a / 2.0
+    x = (np.arange(n) - n // 2) / (n // 2)
+    r2 = x[None, :] ** 2 + x[:, None] ** 2
+    E0 = np.exp(-r2 / (2 * a * a)).astype(np.complex128)
+    q = 1 + 1j * zeta
+    expect = np.exp(-r2 / (2 * a * a * q)) / q
+    out = orc.diffract(E0, alpha)
+    assert np.max(np.abs(out - expect)) < 1e-12
+    # The opposite propagator sign gives the conjugate solution: far off.
+    assert np.max(np.abs(out - np.conj(expect))) > 0.1
+
+
+# ----------------------------------------------------- gain and inversion map
+
+def uniform_params(n=8, g0=0.2, T1=10.0, R=0.95, Isat=1.0, alpha=0.01):
+    return orc.make_params(n, alpha, g0, T1, R, Isat=Isat, edge=0, pump_kind=orc.PUMP_UNIFORM)
+
+
+def test_uniform_field_converges_to_saturation_fixed_point():
+    # Uniform field, uniform pump: the fixed point of the map has the round-trip
+    # gain R exp(N*) = 1 and the saturated inversion N* (1 + I*/Isat) = g0
+    # (steady state of dN/dt = (N0 - N)/T1 - sigma |E|^2 N).
+    for g0, R, Isat in [(0.2, 0.95, 1.0), (0.3, 0.9, 2.0)]:
+        p = uniform_params(g0=g0, R=R, Isat=Isat)
+        E0 = np.full((8, 8), 0.3 + 0.1j)
+        N0 = np.full((8, 8), g0)
+        E, N, hist = orc.run(p, E0, N0, 3000)
+        Nstar = -math.log(R)
+        Istar = Isat * (g0 / Nstar - 1.0)
+        assert np.max(np.abs(N - Nstar)) < 1e-12
+        assert np.max(np.abs(np.abs(E) ** 2 - Istar)) < 1e-10
+        assert abs(hist[-1] - Istar) < 1e-10
+
+
+def test_relaxation_oscillation_matches_linearised_map():
+    # Near the fixed point the (I, N) recursion is linear with Jacobian
+    #   [[1, I*], [-N*/(Isat T1), 1 - (1 + I*/Isat)/T1]]
+    # (the round-trip gain R e^N = 1, gain acting with the frozen N_n and the
+    # depletion driven by the arriving intensity).  Its complex eigenvalues
+    # give the relaxation-oscillation frequency ~ sqrt(N* I*/T1) per bounce,
+    # cf. tau_rel = sqrt(T1 tau_c)/sqrt(sigma N0 c tau_c - 1).
+    g0, R, T1, Isat = 0.2, 0.95, 2000.0, 1.0
+    Nstar = -math.log(R)
+    Istar = Isat * (g0 / Nstar - 1.0)
+    p = uniform_params(g0=g0, T1=T1, R=R, Isat=Isat)
+    E0 = np.full((8, 8), math.sqrt(Istar * (1 + 1e-6)) + 0j)
+    N0 = np.full((8, 8), Nstar)
+    _, _, hist = orc.run(p, E0, N0, 2500)
+    d = hist - Istar
+    A = np.stack([d[1:-1], d[:-2]], axis=1)
+    a1, a0 = np.linalg.lstsq(A, d[2:], rcond=None)[0]
+    fit = np.sort_complex(np.roots([1.0, -a1, -a0]))
+    J = np.array([[1.0, Istar], [-Nstar / (Isat * T1), 1.0 - (1.0 + Istar / Isat) / T1]])
+    lam = np.sort_complex(np.linalg.eigvals(J))
+    assert np.max(np.abs(fit - lam)) < 1e-7
+    period = 2 * math.pi / abs(np.angle(lam[0]))
+    assert abs(period / (2 * math.pi / math.sqrt(Nstar * Istar / T1)) - 1.0) < 0.05
+    # The other plausible reading (depletion by the amplified intensity) moves
+    # the damping by a few per cent, far outside the fit's error.
+    J2 = J.copy()
+    J2[1, 1] -= Nstar * Istar / T1
+    assert np.max(np.abs(fit - np.sort_complex(np.linalg.eigvals(J2)))) > 1e-6
+
+
+def test_inversion_relaxes_exponentially_without_field():
+    # No field: N_{n+1} = N_n + (N0 - N_n)/T1, so
+    # N_b = N0 + (N_init - N0) (1 - 1/T1)^b at every pixel.
+    n, T1, nb = 32, 37.0, 50
+    p = orc.make_params(n, 0.02, 0.25, T1, 0.9, edge=3)
+    N0 = orc.pump(p)
+    Ninit = np.random.default_rng(1).uniform(0, 0.4, (n, n))
+    E, N, hist = orc.run(p, np.zeros((n, n), complex), Ninit, nb)
+    assert np.all(E == 0) and np.all(hist == 0)
+    assert np.max(np.abs(N - (N0 + (Ninit - N0) * (1 - 1 / T1) ** nb))) < 1e-14
+
+
+def test_one_bounce_with_identity_diffraction():
+    # alpha = 2 makes exp(-i pi alpha m^2) = 1 for every integer m (the Talbot
+    # distance of a one-period window), leaving the local map alone:
+    # E1 = sqrt(R) A e^{N0/2} E0 and N1 = N0 - N0 |E0|^2 / (Isat T1).
+    n, g0, T1, R, Isat, edge = 32, 0.3, 50.0, 0.9, 1.5, 4
+    p = orc.make_params(n, 2.0, g0, T1, R, Isat=Isat, edge=edge)
+    N0 = orc.pump(p)
+    E0 = crandn(np.random.default_rng(2), (n, n))
+    E1, N1, _ = orc.run(p, E0, N0, 1)
+    A = np.zeros(n)
+    A[edge:n - edge] = 1.0
+    assert np.max(np.abs(E1 - math.sqrt(R) * np.outer(A, A) * np.exp(N0 / 2) * E0)) < 1e-13
+    assert np.max(np.abs(N1 - (N0 - N0 * np.abs(E0) ** 2 / (Isat * T1)))) < 1e-14
+
+
+def test_absorbing_edge_zeroes_exactly_the_outer_band():
+    n, edge = 64, 8
+    p = orc.make_params(n, 0.03, 0.2, 100.0, 0.95, edge=edge)
+    E0 = crandn(np.random.default_rng(4), (n, n))
+    E1, _, _ = orc.run(p, E0, orc.pump(p), 1)
+    mask = np.zeros((n, n), bool)
+    mask[edge:n - edge, edge:n - edge] = True
+    assert np.all(E1[~mask] == 0)
+    assert np.all(np.abs(E1[mask]) > 0)
+
+
+def test_map_without_gain_is_pure_diffraction():
+    # g0 = 0, N = 0, R = 1, no edge: the map is the diffraction operator alone,
+    # so the Talbot pin holds for the whole bounce.
+    q, n = 8, 64
+    E, p_px = _talbot_setup(q, n)
+    p = orc.make_params(n, 2.0 / q ** 2, 0.0, 10.0, 1.0, edge=0)
+    E1, N1, _ = orc.run(p, E, np.zeros((n, n)), 3)
+    assert rel_l2(E1, E) < 1e-13
+
+
+def test_super_gaussian_pump_profile():
+    n, g0 = 16, 0.25
+    p = orc.make_params(n, 0.01, g0, 10.0, 0.9, pump_order=10.0, pump_radius=0.5)
+    N0 = orc.pump(p)
+    c = n // 2
+    assert N0[c, c] == g0                                    # pixel n/2 is the origin
+    assert abs(N0[c, c + 4] - g0 / math.e) < 1e-15           # x = 0.5 = r_p
+    for d, e in [(1, 2), (3, 5), (2, 7)]:
+        assert N0[c + d, c + e] == N0[c - d, c - e] == N0[c + e, c + d]
+    assert np.all(np.diff(N0[c, c:]) < 0)
+
+
+# --------------------------------------------------------------------- noise
+
+def test_splitmix64_published_vectors():
+    # First three outputs of splitmix64 from state 0 (Steele, Lea & Flood 2014;
+    # the reference generator's widely reproduced test vector).
+    assert orc.splitmix64(0, 0) == 0xE220A8397B1DCDAF
+    assert orc.splitmix64(0, 1) == 0x6E789E6AA1B965F4
+    assert orc.splitmix64(0, 2) == 0x06C45D188009454F
+
+
+def test_noise_statistics():
+    n, amp = 256, 1e-6
+    E = orc.noise(n, 14102855, amp)
+    assert abs(np.mean(np.abs(E) ** 2) / amp ** 2 - 1.0) < 0.02
+    assert abs(np.mean(E)) < 0.02 * amp
+    re = E.real.ravel() / (amp / math.sqrt(2))
+    assert abs(np.var(re) - 1.0) < 0.02
+    assert abs(np.mean(re ** 4) - 3.0) < 0.1                # Gaussian kurtosis
+    assert abs(np.mean(E.real * E.imag)) < 0.02 * amp ** 2  # Re, Im uncorrelated
+    assert not np.array_equal(E, orc.noise(n, 14102856, amp))
+
+
+# ---------------------------------------------------------------- spectrum peak
+
+def test_spectrum_peak_folding_and_ring():
+    n = 32
+    y, x = np.mgrid[0:n, 0:n]
+    wave = np.exp(2j * np.pi * (3 * x - 5 * y) / n)
+    S = orc.spectrum(wave)
+    assert abs(S[n - 5, 3] - n ** 4) < 1e-6 * n ** 4
+    mx, my, pk, ru = orc.spectrum_peak(S)
+    # (3, -5) and (-3, 5) are one peak; it is filed under the smaller flat index.
+    assert (mx, my) == (-3, 5) and abs(pk - n ** 4) < 1e-6 * n ** 4 and ru < 1e-12 * pk
+    S2 = orc.spectrum(2.0 + wave)
+    assert orc.spectrum_peak(S2)[:2] == (0, 0)
+    assert orc.spectrum_peak(S2, ring=4)[:2] == (-3, 5)
+
+
+# ----------------------------------------------------- the paper's own numbers
+
+def test_paper_parameters_give_the_quoted_fresnel_range_and_period():
+    with open(os.path.join(GOLDEN, "paper_parameters.json")) as f:
+        g = json.load(f)
+    lam, L = g["wavelength_m"], g["cavity_length_m"]
+    lo, hi = (D * D / (lam * L) for D in g["gain_region_diameter_m"])
+    # "global" Fresnel number D^2/(lambda L) of the quoted geometry: 100..1000.
+    assert g["fresnel_quoted"][0] * 0.9 < lo < g["fresnel_quoted"][0] * 1.5
+    assert g["fresnel_quoted"][1] * 0.9 < hi < g["fresnel_quoted"][1] * 1.1
+    # Lattice period p ~ sqrt(L lambda), quoted as roughly 50-60 um.
+    p = math.sqrt(L * lam)
+    assert 0.8 * g["period_quoted_m"][0] < p < g["period_quoted_m"][1]
+    # alpha = lambda z / W^2 from the Fresnel number and D/W agree.
+    for D in g["gain_region_diameter_m"]:
+        W = D / 0.8
+        assert abs(orc.alpha_from_fresnel(D * D / (lam * L), 0.8) - lam * L / W ** 2) < 1e-15
