@@ -1,0 +1,455 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused FP32 bounce map on 2048^2 resonators.
+
+Workload: two 2048 x 2048 complex64 resonators, Fresnel number 1000,
+g0 in {0.1, 0.3}, T1 = 1e4 bounces, R = 0.9, super-Gaussian pump (order 10,
+radius 0.8), 8-pixel absorbing edge, seeded noise start.  One step = B
+bounces (default 500, one captured CUDA graph) of each resonator; the
+default 20 timed steps are the full 1e4 round trips.
+
+Prints one JSON line.  `value` is resonator round trips per second over the
+timed steps with the state resident on the device (CUDA events on the
+handles' stream, L2 flushed between steps).  Alongside: per-kernel event
+timing and the HBM roofline of the dominant sweep, the same metric end to
+end through the C ABI from pinned host buffers, the plain FP64 GPU path and a
+cuFFT + PyTorch pointwise form on the same GPU (comparisons only), the error
+against the FP64 oracle after one bounce, and the oracle's own rate on the
+host cores.
+
+`--impl reference` times the FP64 CPU oracle on the same workload instead
+(bounded samples of the same resonators per step).
+Under torchrun each rank runs its own pair of resonators (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1410_2855_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "round trips/s at 2048² FP32 vs FP64, % HBM peak; serve p50/p99 latency"
+UNIT = "round trips/s"
+COL_BYTES_PER_PT = 16   # column sweep: read and write the complex64 field
+ROW_BYTES_PER_PT = 24   # row sweep: field (8+8) and inversion (4+4)
+KERNEL_SOURCES = ["fft_core.cuh", "sweep.cuh", "k_fp32.cu"]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--bounces-per-step", type=int, default=500)
+    ap.add_argument("--no-comparisons", action="store_true", help="skip FP64 / cuFFT / oracle legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def workload(rank: int):
+    return [wl.Resonator(n=c.n, fresnel=c.fresnel, g0=c.g0, T1=c.T1, R=c.R, seed=c.seed + 1000 * rank)
+            for c in wl.C3]
+
+
+def config_block(B, extra=None):
+    c = wl.C3[0]
+    cfg = {"workload": "two 2048x2048 complex64 resonators, N_F=1000, g0 in {0.1,0.3}, T1=1e4, R=0.9, "
+                       "super-Gaussian pump (order 10, r=0.8), 8 px edge, 1e4 round trips per resonator",
+           "grid": c.n, "resonators": len(wl.C3), "fresnel": c.fresnel, "g0": [r.g0 for r in wl.C3],
+           "T1": c.T1, "R": c.R, "bounces_per_step": B}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r for r in csv.reader(io.StringIO(self.out or "")) if len(r) >= 9]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1410_2855_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, n: int):
+    """DRAM bytes per launch from the committed ncu summary of this kernel, or
+    None when the summary is missing or the kernel source changed since."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{n}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "kernel_source_sha")):
+            k, v = line.split(":", 1)
+            vals[k.strip(" -*`")] = v.strip(" `")
+    if vals.get("kernel_source_sha") != kernel_source_sha():
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def oracle_params(p):
+    import oracle as orc
+    return orc.make_params(p.n, orc.alpha_from_fresnel(p.fresnel, p.d_over_w), p.g0, p.T1, p.R, Isat=p.Isat,
+                           edge=p.edge, pump_order=p.pump_order, pump_radius=p.pump_radius)
+
+
+def oracle_rate(params_list, E0s, N0s, budget_s=12.0, min_bounces=2):
+    """Bounces/s of the FP64 oracle on the host cores (bounded sample)."""
+    import oracle as orc
+    threads = os.cpu_count() or 1
+    done, t_total, per = 0, 0.0, 1
+    results = {}
+    while True:
+        for i, p in enumerate(params_list):
+            t0 = time.perf_counter()
+            E, N, _ = orc.run(p, E0s[i], N0s[i], per, nthreads=threads, history=False)
+            t_total += time.perf_counter() - t0
+            done += per
+            results.setdefault(i, E)
+        if t_total >= budget_s or done >= 64:
+            if done >= min_bounces:
+                break
+        per = min(per * 2, 4)
+    return done / t_total, threads, done, results
+
+
+# ---------------------------------------------------------------- reference
+
+def run_reference(args):
+    rank, local_rank, world = dist_env()
+    if rank != 0:
+        return
+    import oracle as orc
+    orc.build()
+    res = workload(0)
+    params = [oracle_params(p) for p in res]
+    init = [orc.init_state(p, r.seed, r.noise_amp) for p, r in zip(params, res)]
+    threads = os.cpu_count() or 1
+    # each step: one bounce of each resonator (bounded sample of the workload)
+    for _ in range(args.warmup):
+        for p, (E, N) in zip(params, init):
+            orc.run(p, E, N, 1, nthreads=threads, history=False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for p, (E, N) in zip(params, init):
+            orc.run(p, E, N, 1, nthreads=threads, history=False)
+    dt = time.perf_counter() - t0
+    value = args.steps * len(params) / dt
+    sample = f"{args.steps} steps x 1 bounce of each of the {len(params)} 2048^2 resonators (FP64 oracle, table set-up included)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_block(1, {"l2": "n/a (host)"}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------------- ours
+
+def torch_cufft_rate(p, steps=100):
+    """Comparison only: the same bounce with cuFFT (torch.fft) and PyTorch
+    pointwise kernels in FP32."""
+    import torch
+    n = p.n
+    dev = torch.device("cuda")
+    m = torch.fft.fftfreq(n, d=1.0 / n, device=dev).to(torch.float64)
+    alpha = p.d_over_w ** 2 / p.fresnel
+    ph = torch.remainder(alpha * (m[None, :] ** 2 + m[:, None] ** 2), 2.0)
+    H = torch.polar(torch.ones_like(ph), -math.pi * ph).to(torch.complex64)
+    x = (torch.arange(n, device=dev, dtype=torch.float32) - n // 2) / (n // 2)
+    r2 = x[None, :] ** 2 + x[:, None] ** 2
+    N0 = (p.g0 * torch.exp(-(r2 / p.pump_radius ** 2) ** (p.pump_order / 2))).float()
+    A = torch.zeros(n, device=dev)
+    A[p.edge:n - p.edge] = 1
+    A2 = (A[None, :] * A[:, None]) * math.sqrt(p.R)
+    E = (torch.randn(n, n, device=dev, dtype=torch.complex64) * 1e-6)
+    N = N0.clone()
+
+    def bounce(E, N):
+        Ep = torch.fft.ifft2(torch.fft.fft2(E) * H)
+        inten = Ep.real ** 2 + Ep.imag ** 2
+        E = Ep * (A2 * torch.exp(0.5 * N))
+        N = N + (N0 - N * (1 + inten / p.Isat)) / p.T1
+        return E, N
+
+    for _ in range(5):
+        E, N = bounce(E, N)
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(steps):
+        E, N = bounce(E, N)
+    e.record()
+    torch.cuda.synchronize()
+    return steps / (s.elapsed_time(e) / 1e3)
+
+
+def run_ours(args):
+    import torch
+    from paper_1410_2855_gb300 import build, rt
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    build.build()
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    B, K, W = args.bounces_per_step, args.steps, args.warmup
+    params = workload(rank)
+    res = [rt.Resonator.from_params(p, precision=rt.RT_FP32, cuda_stream=stream.cuda_stream, chunk=B)
+           for p in params]
+    P = params[0].n ** 2
+    E0 = [r.field() for r in res]
+    N0 = [r.inversion() for r in res]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(W):
+            for r in res:
+                rt.rt_step(r.h, B)
+        stream.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local_rank) as clk:
+            for k in range(K):
+                flush.fill_(float(k))
+                evs[k][0].record(stream)
+                for r in res:
+                    rt.rt_step(r.h, B)
+                evs[k][1].record(stream)
+            stream.synchronize()
+            barrier()
+            torch.cuda.synchronize()
+        step_ms = [a.elapsed_time(b) for a, b in evs]
+        total_ms = sum(step_ms)
+        if world > 1:
+            t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+        units = world * K * B * len(res)
+        value = units / (total_ms / 1e3)
+        for r in res:
+            r.sync()
+
+        # per-kernel durations (events on the launching stream around each sweep)
+        reps = 200
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3 * reps)]
+        for i in range(reps):
+            r = res[i % len(res)]
+            e[3 * i].record(stream)
+            rt.rt_sweep(r.h, rt.RT_SWEEP_COLUMNS)
+            e[3 * i + 1].record(stream)
+            rt.rt_sweep(r.h, rt.RT_SWEEP_ROWS)
+            e[3 * i + 2].record(stream)
+        stream.synchronize()
+        col_ms = statistics.mean(e[3 * i].elapsed_time(e[3 * i + 1]) for i in range(reps))
+        row_ms = statistics.mean(e[3 * i + 1].elapsed_time(e[3 * i + 2]) for i in range(reps))
+
+    peak, peak_kind = measured_peak()
+    col_gbs = COL_BYTES_PER_PT * P / (col_ms / 1e3) / 1e9
+    row_gbs = ROW_BYTES_PER_PT * P / (row_ms / 1e3) / 1e9
+    if row_ms >= col_ms:
+        dom, dom_bytes, dom_gbs, dom_ms, dom_name = "row_sweep", ROW_BYTES_PER_PT * P, row_gbs, row_ms, "k_row"
+    else:
+        dom, dom_bytes, dom_gbs, dom_ms, dom_name = "column_sweep", COL_BYTES_PER_PT * P, col_gbs, col_ms, "k_col"
+    bounce_gbs = (COL_BYTES_PER_PT + ROW_BYTES_PER_PT) * P * value / len(res) * len(res) / 1e9 / world
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": config_block(B, {"l2": "flushed between steps (256 MiB write); the two resonators' 96 MiB "
+                                         "state stays L2-resident within a step",
+                                   "graph": f"one CUDA graph per {B} bounces"}),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": dom_gbs, "peak": peak, "unit": "GB/s",
+                     "frac": dom_gbs / peak, "peak_kind": f"of {peak_kind}",
+                     "traffic": profiled_traffic(dom, params[0].n),
+                     "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms},
+        "kernels": {"column_sweep": {"avg_ms": col_ms, "gbs": col_gbs, "bytes_per_launch": COL_BYTES_PER_PT * P},
+                    "row_sweep": {"avg_ms": row_ms, "gbs": row_gbs, "bytes_per_launch": ROW_BYTES_PER_PT * P}},
+        "bounce_hbm_fraction": bounce_gbs / peak,
+        "gpu_launches": 2 * K * B * len(res),
+        "clocks": clk.summary(),
+    }
+
+    if not args.no_comparisons:
+        out.update(comparisons(args, rt, torch, stream, params, res, E0, N0, rank, world))
+    if world > 1:
+        torch.distributed.barrier()
+    for r in res:
+        r.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def comparisons(args, rt, torch, stream, params, res, E0, N0, rank, world):
+    B = args.bounces_per_step
+    extra = {}
+    P = params[0].n ** 2
+    # ---- end to end through the C ABI from pinned host buffers
+    hostE = [torch.from_numpy(e.view(np.float32).copy()).pin_memory() for e in E0]
+    hostN = [torch.from_numpy(nv.copy()).pin_memory() for nv in N0]
+    outE = [torch.empty(P * 2, dtype=torch.float32).pin_memory() for _ in res]
+    K2 = max(2, min(args.steps, 6))
+    with torch.cuda.stream(stream):
+        for r, e, nv in zip(res, hostE, hostN):      # one untimed warm step
+            rt.rt_write_field(r.h, e)
+            rt.rt_write_inversion(r.h, nv)
+            rt.rt_step(r.h, B)
+        for r, o in zip(res, outE):
+            rt.rt_read_field(r.h, o)
+        t0 = time.perf_counter()
+        for _ in range(K2):
+            for r, e, nv in zip(res, hostE, hostN):
+                rt.rt_write_field(r.h, e)
+                rt.rt_write_inversion(r.h, nv)
+                rt.rt_step(r.h, B)
+            for r, o in zip(res, outE):
+                rt.rt_read_field(r.h, o)
+        e2e_s = time.perf_counter() - t0
+    extra["e2e"] = {"value": world * K2 * B * len(res) / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": len(res) * 12 * P, "d2h_bytes_per_step": len(res) * 8 * P,
+                    "steps": K2}
+
+    # ---- plain FP64 GPU path on the same GPU (unfused, six sweeps per bounce)
+    p = params[1]
+    with rt.Resonator.from_params(p, precision=rt.RT_FP64, cuda_stream=stream.cuda_stream, chunk=50) as r64:
+        with torch.cuda.stream(stream):
+            rt.rt_step(r64.h, 50)
+            stream.synchronize()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            rt.rt_step(r64.h, 200)
+            e.record(stream)
+            stream.synchronize()
+        r64.sync()
+        fp64 = 200 / (s.elapsed_time(e) / 1e3)
+    extra["fp64_plain"] = {"value": fp64, "unit": "round trips/s", "resonators": 1, "bounces": 200,
+                           "fused_fp32_speedup": None}
+    extra["torch_cufft_fp32"] = {"value": torch_cufft_rate(p), "unit": "round trips/s", "resonators": 1,
+                                 "note": "comparison only: cuFFT C2C + PyTorch pointwise kernels"}
+    per_res = None
+    if rank == 0:
+        # ---- error after one bounce against the FP64 oracle, and the oracle's rate
+        import oracle as orc
+        orc.build()
+        oparams = [oracle_params(q) for q in params]
+        E0w = [e.astype(np.complex128) for e in E0]
+        N0o = [orc.pump(q) for q in oparams]
+        rate, threads, done, firsts = oracle_rate(oparams, E0w, N0o)
+        errs = []
+        for q, e0, o1 in zip(params, E0, [firsts[i] for i in range(len(params))]):
+            with rt.Resonator.from_params(q, precision=rt.RT_FP32, chunk=0) as r1:
+                r1.set_field(e0)
+                r1.step(1)
+                g1 = r1.field()
+            errs.append(float(np.linalg.norm(g1 - o1) / np.linalg.norm(o1)))
+        extra["error_vs_oracle"] = {"bounce1_rel_l2": errs, "bar": 1e-5}
+        extra["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                 "sample": f"{done} oracle bounces over the two 2048^2 resonators "
+                                           f"(FP64, {threads} threads, table set-up included)"}
+    return extra
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

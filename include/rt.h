@@ -1,0 +1,184 @@
+/*
+ * rt.h -- C ABI of the GB300 bounce-map library.
+ *
+ * The library iterates the discrete bounce-to-bounce map of the intracavity
+ * field E(x, y) of a high-Fresnel-number microchip laser (Okulov, "Two-
+ * dimensional periodic and quasiperiodic spatial structures in microchip
+ * laser resonator"): the nonlocal map of eq. conv_map written, as in the
+ * integral-equation section (eqs. complex_8F, complex_aperture2), as a local
+ * nonlinear gain step followed by the linear Fresnel propagator, the latter
+ * applied in the Fourier basis as the operator exponent of eq.
+ * limit_of_operators_renorm_final.  One bounce n -> n+1 computes
+ *
+ *   E'      = IDFT2( DFT2(E_n) * exp(-i pi alpha (mx^2 + my^2)) ) / n^2
+ *   I       = |E'|^2
+ *   E_{n+1} = sqrt(R) * A(x) A(y) * exp(N_n / 2) * E'
+ *   N_{n+1} = N_n + (N0(x, y) - N_n (1 + I / Isat)) / T1
+ *
+ * with alpha = (D/W)^2 / N_F (N_F = D^2 / (lambda z) the cavity Fresnel
+ * number, D/W the gain-region diameter over the window width), A the hard
+ * absorbing edge (0 on the outer edge_px pixels of each axis), N0 the pump
+ * (unsaturated inversion) and (mx, my) the signed DFT frequencies.  Pixel j
+ * sits at x_j = (j - n/2) / (n/2): the window half-width is 1.
+ *
+ * Layout.  Grids are n x n, row-major (element [y*n + x]).  The field is
+ * interleaved complex: complex64 (2 x float) for RT_FP32 handles, complex128
+ * (2 x double) for RT_FP64 handles.  The inversion is float or double alike.
+ *
+ * Ownership.  The library owns every device buffer it allocates; the caller
+ * owns every pointer it passes in and keeps it valid for the duration of the
+ * call.  Pointers marked "host or device" may point to either (unified
+ * addressing decides the copy direction).
+ *
+ * Errors.  Every call returns an rt_status; none aborts the process.  A
+ * device-side error (non-finite intensity) is sticky: it is reported by the
+ * next call that synchronises (rt_sync, rt_read_*, rt_stats).
+ *
+ * Threading.  A handle is not thread-safe; distinct handles may be used from
+ * distinct threads.  All work of a handle is ordered on its stream.
+ */
+#ifndef RT_H
+#define RT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rt_handle rt_handle;
+
+typedef enum {
+    RT_OK = 0,
+    RT_EINVAL = -1,    /* bad argument: size, range, null pointer, byte count */
+    RT_ENOMEM = -2,    /* device or host allocation failed */
+    RT_ECUDA = -3,     /* a CUDA runtime call failed */
+    RT_ENUMERIC = -4,  /* the field's mean intensity became NaN or Inf */
+    RT_ETIMEOUT = -5,  /* a bounded wait ran out */
+    RT_EBUSY = -6      /* the handle or server cannot take the request now */
+} rt_status;
+
+enum { RT_PUMP_SUPERGAUSS = 0, RT_PUMP_UNIFORM = 1, RT_PUMP_ARRAY = 2 };
+enum { RT_FP32 = 0, RT_FP64 = 1 };
+
+/* Pump, i.e. the unsaturated inversion N0 = g0 * P(x, y):
+ *   RT_PUMP_SUPERGAUSS  P = exp(-(r / radius)^order), r = sqrt(x^2 + y^2),
+ *                       radius as a fraction of the window half-width;
+ *   RT_PUMP_UNIFORM     P = 1;
+ *   RT_PUMP_ARRAY       P = profile[y*n + x] (host array of n*n doubles,
+ *                       copied at creation).
+ * A NULL pump means super-Gaussian, order 10, radius 0.8. */
+typedef struct {
+    int kind;
+    double order;
+    double radius;
+    const double *profile;
+} rt_pump;
+
+/* Options; rt_opts_default fills the defaults listed per field. */
+typedef struct {
+    double Isat;                  /* saturation intensity (1) */
+    int edge_px;                  /* absorbing edge width in pixels (8) */
+    int precision;                /* RT_FP32 (fused FP32 path) or RT_FP64 (plain FP64 path) */
+    unsigned long long seed;      /* noise seed (14102855) */
+    double noise_amp;             /* initial noise amplitude, E|E|^2 = amp^2 (1e-6) */
+    double pump_diam_over_window; /* D/W in alpha = (D/W)^2 / N_F (0.8) */
+    void *cuda_stream;            /* cudaStream_t to run on; NULL = the legacy default stream */
+    long long history_cap;        /* >0: keep the mean intensity of the last history_cap bounces (65536) */
+    int chunk;                    /* bounces per captured CUDA graph in rt_step; 0 = no graphs (500) */
+} rt_opts;
+
+rt_status rt_opts_default(rt_opts *opts);
+
+/* Statistics of a handle (rt_stats). */
+typedef struct {
+    long long bounces;        /* bounces completed since creation */
+    double mean_intensity;    /* <|E|^2> after the last bounce (FP64 accumulation); 0 before any bounce */
+    double alpha;             /* lambda z / W^2 in use */
+    int n;                    /* grid side */
+    int precision;            /* RT_FP32 or RT_FP64 */
+    int last_error;           /* sticky device error as an rt_status (RT_OK if none) */
+    long long history_len;    /* bounces currently held in the history ring */
+} rt_stats_t;
+
+/* Create a resonator of side n (power of two, 16 <= n <= 4096) with Fresnel
+ * number `fresnel` (> 0), pump `pump`, small-signal gain g0 (intensity gain
+ * exponent per pass, >= 0), inversion relaxation time T1 (in bounces, >= 1)
+ * and mirror reflectivity R (0 < R <= 1).  Allocates the field, inversion and
+ * tables on the device, draws the seeded complex Gaussian noise field
+ * (splitmix64 counter stream + Box-Muller, in FP64, rounded to the handle's
+ * precision) and sets N = N0.  Section "Integral equation form", eqs.
+ * complex_8F and complex_aperture2; the noise start and the full inversion
+ * are the initial condition of the map.
+ * Returns RT_EINVAL for out-of-range arguments, RT_ENOMEM, RT_ECUDA. */
+rt_status rt_create(int n, double fresnel, const rt_pump *pump, double g0, double T1, double R,
+                    const rt_opts *opts, rt_handle **out);
+
+/* Enqueue n_bounces (>= 0) iterations of the map on the handle's stream and
+ * return without waiting.  Eq. conv_map / complex_8F per bounce, the
+ * propagator of eq. limit_of_operators_renorm_final. */
+rt_status rt_step(rt_handle *h, long long n_bounces);
+
+/* One half of a bounce, for per-kernel timing: RT_SWEEP_COLUMNS enqueues the
+ * column sweep (1-D diffraction along y of every column), RT_SWEEP_ROWS the
+ * row sweep (1-D diffraction along x of every row, then the local map:
+ * gain, mirror, edge, inversion update, mean intensity).  A bounce is the
+ * column sweep followed by the row sweep, which is exactly what rt_step
+ * enqueues; the propagator factorisation follows from eq.
+ * limit_of_operators_renorm_final with a separable Laplacian.  Calling the
+ * row sweep without the column sweep first is not a bounce of the map.
+ * FP32 handles only (RT_EINVAL otherwise).  Asynchronous. */
+enum { RT_SWEEP_COLUMNS = 0, RT_SWEEP_ROWS = 1 };
+rt_status rt_sweep(rt_handle *h, int which);
+
+/* Wait for the handle's stream; reports a sticky device error. */
+rt_status rt_sync(rt_handle *h);
+
+/* Copy the current field (n*n complex64 or complex128, `bytes` must equal
+ * n*n*8 or n*n*16) to dst (host or device).  Blocks until the copy is done. */
+rt_status rt_read_field(rt_handle *h, void *dst, size_t bytes);
+
+/* Copy the current inversion (n*n float or double) to dst (host or device). Blocks. */
+rt_status rt_read_inversion(rt_handle *h, void *dst, size_t bytes);
+
+/* Replace the field / inversion with src (host or device, same layouts as
+ * the reads): checkpoint restore or a caller-chosen initial condition.
+ * Ordered on the handle's stream; src must stay valid until rt_sync. */
+rt_status rt_write_field(rt_handle *h, const void *src, size_t bytes);
+rt_status rt_write_inversion(rt_handle *h, const void *src, size_t bytes);
+
+/* Set the bounce counter (used when restoring a checkpoint). */
+rt_status rt_set_bounces(rt_handle *h, long long bounces);
+
+/* Synchronise and report counters (bounce count, last mean intensity). */
+rt_status rt_stats(rt_handle *h, rt_stats_t *out);
+
+/* Copy the mean intensity <|E|^2> of the most recent bounces, oldest first,
+ * into dst (host, up to max values); *got receives the count written. */
+rt_status rt_read_history(rt_handle *h, double *dst, long long max, long long *got);
+
+/* Far-field spectrum S = |DFT2(E)|^2 of the current field (n*n float or
+ * double, unnormalised) to dst (host or device).  Blocks. */
+rt_status rt_read_spectrum(rt_handle *h, void *dst, size_t bytes);
+
+/* Dominant spatial frequency of the current field.  Bin k and its mirror
+ * -k (mod n) form one peak of folded power S[k] + S[-k] (S[k] once if
+ * k == -k), filed under the smaller row-major index; with ring > 0 only
+ * bins with max(|mx|, |my|) >= ring compete; ties go to the smaller index.
+ * Writes the signed (mx, my) and the folded power. Blocks. */
+rt_status rt_spectrum_peak(rt_handle *h, int ring, int *mx, int *my, double *power);
+
+/* Release every device buffer and graph of the handle (NULL is accepted). */
+rt_status rt_destroy(rt_handle *h);
+
+/* Static, human-readable name of a status code. */
+const char *rt_status_string(rt_status s);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int rt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RT_H */

@@ -1,0 +1,545 @@
+// C ABI of the bounce-map library (include/rt.h): resonator handles,
+// stepping with captured CUDA graphs, checkpoint reads/writes, statistics and
+// spectrum readout.  Every entry point returns an rt_status and never aborts.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <new>
+
+#include "../../include/rt.h"
+#include "rt_internal.h"
+
+using namespace rtk;
+
+namespace {
+
+// Device-side control block of a handle (one small allocation).
+struct Ctl {
+    unsigned int count;       // arrival counter of the mean-intensity reduction
+    unsigned int peak_count;  // arrival counter of the spectrum-peak reduction
+    int err;                  // sticky device error (0 or RT_ENUMERIC)
+    int pad;
+    long long bounce;         // bounces completed on the device
+    double last_mean;         // mean intensity after the last bounce
+    PeakResult peak;
+};
+
+constexpr int kMaxPart = 4096;  // block partials of any reduction (>= every launch's grid)
+
+rt_status from_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return RT_OK;
+    if (e == cudaErrorMemoryAllocation) return RT_ENOMEM;
+    return RT_ECUDA;
+}
+
+#define RT_TRY(expr)                              \
+    do {                                          \
+        cudaError_t e_ = (expr);                  \
+        if (e_ != cudaSuccess) return from_cuda(e_); \
+    } while (0)
+
+int ilog2(int n)
+{
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+
+// Keeps the handle's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1, want;
+    explicit DeviceGuard(int dev) : want(dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != want) cudaSetDevice(want);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0 && prev != want) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+struct rt_handle {
+    int n = 0, logn = 0, precision = RT_FP32, device = 0;
+    double fresnel = 0, alpha = 0, g0 = 0, T1 = 1, R = 1;
+    rt_opts opts{};
+    rt_pump pump{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    void *E = nullptr, *N = nullptr, *tw = nullptr, *h = nullptr;
+    void *pump_tab = nullptr;     // N0 table (array pump, FP32 path)
+    double *profile = nullptr;    // device copy of the array pump profile
+    void *X = nullptr, *S = nullptr;  // spectrum scratch (lazily allocated)
+    double *part = nullptr;
+    double *peak_val = nullptr;
+    long long *peak_idx = nullptr;
+    double *hist = nullptr;
+    Ctl *ctl = nullptr;
+    long long bounces = 0;
+    int colC = 4;
+    std::map<long long, cudaGraphExec_t> graphs;
+    size_t esz() const { return precision == RT_FP64 ? 16 : 8; }
+    size_t rsz() const { return precision == RT_FP64 ? 8 : 4; }
+    size_t points() const { return (size_t)n * n; }
+};
+
+namespace {
+
+StatParams stat_params(rt_handle *h)
+{
+    StatParams st{};
+    st.part = h->part;
+    st.count = &h->ctl->count;
+    st.hist = h->hist;
+    st.hist_cap = h->opts.history_cap;
+    st.bounce = &h->ctl->bounce;
+    st.last_mean = &h->ctl->last_mean;
+    st.err = &h->ctl->err;
+    return st;
+}
+
+template <typename R>
+GainParams<R> gain_params(rt_handle *h)
+{
+    GainParams<R> g{};
+    g.sqrtR = (R)std::sqrt(h->R);
+    g.invT1 = (R)(1.0 / h->T1);
+    g.invIsat = (R)(1.0 / h->opts.Isat);
+    g.g0 = (R)h->g0;
+    const double r = h->pump.radius;
+    g.inv_rp2 = (R)(1.0 / (r * r));
+    const double half = 0.5 * h->pump.order;
+    g.half_order = (R)half;
+    g.int_half_order = (half == std::floor(half) && half >= 1 && half <= 16) ? (int)half : 0;
+    g.edge = h->opts.edge_px;
+    g.pump_kind = h->pump.kind;
+    g.pump_tab = reinterpret_cast<const R *>(h->pump_tab);
+    return g;
+}
+
+// Default column-tile width of the FP32 column sweep.
+int default_col_c(int logn)
+{
+    if (logn >= 12) return 2;
+    if (logn >= 11) return 4;
+    if (logn >= 10) return 8;
+    return 16;
+}
+
+cudaError_t enqueue_bounce(rt_handle *h, cudaStream_t s)
+{
+    const StatParams st = stat_params(h);
+    if (h->precision == RT_FP32) {
+        float2 *E = static_cast<float2 *>(h->E);
+        const float2 *tw = static_cast<const float2 *>(h->tw), *hh = static_cast<const float2 *>(h->h);
+        cudaError_t e = launch_col_diffract32(h->logn, h->colC, E, tw, hh, s);
+        if (e != cudaSuccess) return e;
+        return launch_row_diffract_gain32(h->logn, E, static_cast<float *>(h->N), tw, hh, gain_params<float>(h), st, s);
+    }
+    double2 *E = static_cast<double2 *>(h->E);
+    const double2 *tw = static_cast<const double2 *>(h->tw), *hh = static_cast<const double2 *>(h->h);
+    cudaError_t e;
+    if ((e = launch_row_fft64(h->logn, E, E, tw, -1, s)) != cudaSuccess) return e;
+    if ((e = launch_col_fft64(h->logn, E, tw, -1, s)) != cudaSuccess) return e;
+    if ((e = launch_mul_h64(h->n, E, hh, s)) != cudaSuccess) return e;
+    if ((e = launch_col_fft64(h->logn, E, tw, +1, s)) != cudaSuccess) return e;
+    if ((e = launch_row_fft64(h->logn, E, E, tw, +1, s)) != cudaSuccess) return e;
+    return launch_gain64(h->n, E, static_cast<double *>(h->N), gain_params<double>(h), st, s);
+}
+
+cudaError_t get_graph(rt_handle *h, long long k, cudaGraphExec_t *out)
+{
+    auto it = h->graphs.find(k);
+    if (it != h->graphs.end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
+    cudaError_t e = h->precision == RT_FP32 ? prepare_bounce32(h->logn, h->colC) : prepare_bounce64(h->logn);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t launch_err = cudaSuccess;
+    for (long long i = 0; i < k && launch_err == cudaSuccess; ++i) launch_err = enqueue_bounce(h, h->capture_stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(h->capture_stream, &g);
+    if (launch_err != cudaSuccess) e = launch_err;
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return e;
+    }
+    cudaGraphExec_t ge = nullptr;
+    e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return e;
+    h->graphs[k] = ge;
+    *out = ge;
+    return cudaSuccess;
+}
+
+rt_status check_device_error(rt_handle *h)
+{
+    int err = 0;
+    RT_TRY(cudaMemcpyAsync(&err, &h->ctl->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    RT_TRY(cudaStreamSynchronize(h->stream));
+    return err ? (rt_status)err : RT_OK;
+}
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+void release(rt_handle *h)
+{
+    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+    void *bufs[] = {h->E, h->N, h->tw, h->h, h->pump_tab, h->profile, h->X, h->S,
+                    h->part, h->peak_val, h->peak_idx, h->hist, h->ctl};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+}
+
+rt_status ensure_spectrum_scratch(rt_handle *h)
+{
+    if (!h->X) RT_TRY(cudaMalloc(&h->X, h->points() * h->esz()));
+    if (!h->S) RT_TRY(cudaMalloc(&h->S, h->points() * h->rsz()));
+    if (!h->peak_val) RT_TRY(cudaMalloc(&h->peak_val, sizeof(double) * kMaxPart));
+    if (!h->peak_idx) RT_TRY(cudaMalloc(&h->peak_idx, sizeof(long long) * kMaxPart));
+    return RT_OK;
+}
+
+// S = |DFT2(E)|^2 into h->S.
+rt_status compute_spectrum(rt_handle *h)
+{
+    rt_status st = ensure_spectrum_scratch(h);
+    if (st != RT_OK) return st;
+    if (h->precision == RT_FP32) {
+        const float2 *tw = static_cast<const float2 *>(h->tw);
+        float2 *X = static_cast<float2 *>(h->X);
+        RT_TRY(launch_row_fft32(h->logn, static_cast<const float2 *>(h->E), X, tw, -1, h->stream));
+        RT_TRY(launch_col_fft32(h->logn, X, tw, -1, h->stream));
+        RT_TRY(launch_power32(h->n, X, static_cast<float *>(h->S), h->stream));
+    } else {
+        const double2 *tw = static_cast<const double2 *>(h->tw);
+        double2 *X = static_cast<double2 *>(h->X);
+        RT_TRY(launch_row_fft64(h->logn, static_cast<const double2 *>(h->E), X, tw, -1, h->stream));
+        RT_TRY(launch_col_fft64(h->logn, X, tw, -1, h->stream));
+        RT_TRY(launch_power64(h->n, X, static_cast<double *>(h->S), h->stream));
+    }
+    return RT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rt_version(void) { return 100; }
+
+const char *rt_status_string(rt_status s)
+{
+    switch (s) {
+    case RT_OK: return "ok";
+    case RT_EINVAL: return "invalid argument";
+    case RT_ENOMEM: return "out of memory";
+    case RT_ECUDA: return "CUDA error";
+    case RT_ENUMERIC: return "non-finite field intensity";
+    case RT_ETIMEOUT: return "bounded wait timed out";
+    case RT_EBUSY: return "busy";
+    default: return "unknown status";
+    }
+}
+
+rt_status rt_opts_default(rt_opts *o)
+{
+    if (!o) return RT_EINVAL;
+    std::memset(o, 0, sizeof(*o));
+    o->Isat = 1.0;
+    o->edge_px = 8;
+    o->precision = RT_FP32;
+    o->seed = 14102855ull;
+    o->noise_amp = 1e-6;
+    o->pump_diam_over_window = 0.8;
+    o->cuda_stream = nullptr;
+    o->history_cap = 65536;
+    o->chunk = 500;
+    return RT_OK;
+}
+
+rt_status rt_create(int n, double fresnel, const rt_pump *pump, double g0, double T1, double R, const rt_opts *opts,
+                    rt_handle **out)
+{
+    if (!out) return RT_EINVAL;
+    *out = nullptr;
+    rt_opts o;
+    if (opts) o = *opts;
+    else rt_opts_default(&o);
+    rt_pump p{RT_PUMP_SUPERGAUSS, 10.0, 0.8, nullptr};
+    if (pump) p = *pump;
+    if (!is_pow2(n) || n < 32 || n > 4096) return RT_EINVAL;
+    if (!finite_pos(fresnel) || !std::isfinite(g0) || g0 < 0.0 || !std::isfinite(T1) || T1 < 1.0) return RT_EINVAL;
+    if (!std::isfinite(R) || R <= 0.0 || R > 1.0) return RT_EINVAL;
+    if (!finite_pos(o.Isat) || o.edge_px < 0 || o.edge_px > n / 2) return RT_EINVAL;
+    if (o.precision != RT_FP32 && o.precision != RT_FP64) return RT_EINVAL;
+    if (!std::isfinite(o.noise_amp) || o.noise_amp < 0.0 || !finite_pos(o.pump_diam_over_window)) return RT_EINVAL;
+    if (o.history_cap < 0 || o.chunk < 0) return RT_EINVAL;
+    if (p.kind == RT_PUMP_SUPERGAUSS && (!finite_pos(p.order) || !finite_pos(p.radius))) return RT_EINVAL;
+    if (p.kind == RT_PUMP_ARRAY && !p.profile) return RT_EINVAL;
+    if (p.kind < RT_PUMP_SUPERGAUSS || p.kind > RT_PUMP_ARRAY) return RT_EINVAL;
+
+    rt_handle *h = new (std::nothrow) rt_handle();
+    if (!h) return RT_ENOMEM;
+    h->n = n;
+    h->logn = ilog2(n);
+    h->precision = o.precision;
+    h->fresnel = fresnel;
+    h->alpha = o.pump_diam_over_window * o.pump_diam_over_window / fresnel;
+    h->g0 = g0;
+    h->T1 = T1;
+    h->R = R;
+    h->opts = o;
+    h->pump = p;
+    h->pump.profile = nullptr;
+    h->stream = static_cast<cudaStream_t>(o.cuda_stream);
+    h->colC = default_col_c(h->logn);
+    cudaGetDevice(&h->device);
+
+    auto fail = [&](rt_status s) {
+        release(h);
+        delete h;
+        return s;
+    };
+#define RT_CREATE_TRY(expr)                       \
+    do {                                          \
+        cudaError_t e_ = (expr);                  \
+        if (e_ != cudaSuccess) return fail(from_cuda(e_)); \
+    } while (0)
+
+    const size_t P = h->points();
+    RT_CREATE_TRY(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+    RT_CREATE_TRY(cudaMalloc(&h->E, P * h->esz()));
+    RT_CREATE_TRY(cudaMalloc(&h->N, P * h->rsz()));
+    RT_CREATE_TRY(cudaMalloc(&h->tw, (size_t)n * h->esz()));
+    RT_CREATE_TRY(cudaMalloc(&h->h, (size_t)n * h->esz()));
+    RT_CREATE_TRY(cudaMalloc(&h->part, sizeof(double) * kMaxPart));
+    RT_CREATE_TRY(cudaMalloc(reinterpret_cast<void **>(&h->ctl), sizeof(Ctl)));
+    RT_CREATE_TRY(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->stream));
+    if (o.history_cap > 0) RT_CREATE_TRY(cudaMalloc(&h->hist, sizeof(double) * (size_t)o.history_cap));
+    if (p.kind == RT_PUMP_ARRAY) {
+        RT_CREATE_TRY(cudaMalloc(&h->profile, sizeof(double) * P));
+        RT_CREATE_TRY(cudaMemcpyAsync(h->profile, p.profile, sizeof(double) * P, cudaMemcpyDefault, h->stream));
+    }
+
+    if (h->precision == RT_FP32) {
+        RT_CREATE_TRY(launch_tables32(n, h->alpha, static_cast<float2 *>(h->tw), static_cast<float2 *>(h->h), h->stream));
+        RT_CREATE_TRY(launch_noise32(n, o.seed, o.noise_amp, static_cast<float2 *>(h->E), h->stream));
+        RT_CREATE_TRY(launch_pump32(n, p.kind, g0, p.order, p.radius, h->profile, static_cast<float *>(h->N), h->stream));
+        if (p.kind == RT_PUMP_ARRAY) {
+            RT_CREATE_TRY(cudaMalloc(&h->pump_tab, sizeof(float) * P));
+            RT_CREATE_TRY(cudaMemcpyAsync(h->pump_tab, h->N, sizeof(float) * P, cudaMemcpyDeviceToDevice, h->stream));
+        }
+    } else {
+        RT_CREATE_TRY(launch_tables64(n, h->alpha, static_cast<double2 *>(h->tw), static_cast<double2 *>(h->h), h->stream));
+        RT_CREATE_TRY(launch_noise64(n, o.seed, o.noise_amp, static_cast<double2 *>(h->E), h->stream));
+        RT_CREATE_TRY(launch_pump64(n, p.kind, g0, p.order, p.radius, h->profile, static_cast<double *>(h->N), h->stream));
+        if (p.kind == RT_PUMP_ARRAY) {
+            RT_CREATE_TRY(cudaMalloc(&h->pump_tab, sizeof(double) * P));
+            RT_CREATE_TRY(cudaMemcpyAsync(h->pump_tab, h->N, sizeof(double) * P, cudaMemcpyDeviceToDevice, h->stream));
+        }
+    }
+    RT_CREATE_TRY(cudaStreamSynchronize(h->stream));
+#undef RT_CREATE_TRY
+    *out = h;
+    return RT_OK;
+}
+
+rt_status rt_step(rt_handle *h, long long nb)
+{
+    if (!h || nb < 0) return RT_EINVAL;
+    if (nb == 0) return RT_OK;
+    DeviceGuard dg(h->device);
+    const long long K = h->opts.chunk;
+    long long left = nb;
+    if (K > 0 && left >= K) {
+        cudaGraphExec_t ge;
+        RT_TRY(get_graph(h, K, &ge));
+        for (; left >= K; left -= K) RT_TRY(cudaGraphLaunch(ge, h->stream));
+    }
+    for (; left > 0; --left) RT_TRY(enqueue_bounce(h, h->stream));
+    h->bounces += nb;
+    return RT_OK;
+}
+
+rt_status rt_sweep(rt_handle *h, int which)
+{
+    if (!h || h->precision != RT_FP32 || (which != RT_SWEEP_COLUMNS && which != RT_SWEEP_ROWS)) return RT_EINVAL;
+    DeviceGuard dg(h->device);
+    float2 *E = static_cast<float2 *>(h->E);
+    const float2 *tw = static_cast<const float2 *>(h->tw), *hh = static_cast<const float2 *>(h->h);
+    if (which == RT_SWEEP_COLUMNS) {
+        RT_TRY(launch_col_diffract32(h->logn, h->colC, E, tw, hh, h->stream));
+    } else {
+        RT_TRY(launch_row_diffract_gain32(h->logn, E, static_cast<float *>(h->N), tw, hh, gain_params<float>(h),
+                                          stat_params(h), h->stream));
+        h->bounces += 1;
+    }
+    return RT_OK;
+}
+
+rt_status rt_sync(rt_handle *h)
+{
+    if (!h) return RT_EINVAL;
+    DeviceGuard dg(h->device);
+    return check_device_error(h);
+}
+
+static rt_status copy_out(rt_handle *h, void *dst, const void *src, size_t bytes, size_t want)
+{
+    if (!h || !dst) return RT_EINVAL;
+    if (bytes != want) return RT_EINVAL;
+    DeviceGuard dg(h->device);
+    RT_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, h->stream));
+    return check_device_error(h);
+}
+
+rt_status rt_read_field(rt_handle *h, void *dst, size_t bytes)
+{
+    if (!h) return RT_EINVAL;
+    return copy_out(h, dst, h->E, bytes, h->points() * h->esz());
+}
+
+rt_status rt_read_inversion(rt_handle *h, void *dst, size_t bytes)
+{
+    if (!h) return RT_EINVAL;
+    return copy_out(h, dst, h->N, bytes, h->points() * h->rsz());
+}
+
+static rt_status copy_in(rt_handle *h, void *dst, const void *src, size_t bytes, size_t want)
+{
+    if (!h || !src) return RT_EINVAL;
+    if (bytes != want) return RT_EINVAL;
+    DeviceGuard dg(h->device);
+    RT_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, h->stream));
+    return RT_OK;
+}
+
+rt_status rt_write_field(rt_handle *h, const void *src, size_t bytes)
+{
+    if (!h) return RT_EINVAL;
+    return copy_in(h, h->E, src, bytes, h->points() * h->esz());
+}
+
+rt_status rt_write_inversion(rt_handle *h, const void *src, size_t bytes)
+{
+    if (!h) return RT_EINVAL;
+    return copy_in(h, h->N, src, bytes, h->points() * h->rsz());
+}
+
+rt_status rt_set_bounces(rt_handle *h, long long bounces)
+{
+    if (!h || bounces < 0) return RT_EINVAL;
+    DeviceGuard dg(h->device);
+    RT_TRY(cudaStreamSynchronize(h->stream));
+    RT_TRY(cudaMemcpy(&h->ctl->bounce, &bounces, sizeof(bounces), cudaMemcpyHostToDevice));
+    h->bounces = bounces;
+    return RT_OK;
+}
+
+rt_status rt_stats(rt_handle *h, rt_stats_t *out)
+{
+    if (!h || !out) return RT_EINVAL;
+    DeviceGuard dg(h->device);
+    Ctl c;
+    RT_TRY(cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
+    RT_TRY(cudaStreamSynchronize(h->stream));
+    std::memset(out, 0, sizeof(*out));
+    out->bounces = c.bounce;
+    out->mean_intensity = c.last_mean;
+    out->alpha = h->alpha;
+    out->n = h->n;
+    out->precision = h->precision;
+    out->last_error = c.err;
+    const long long cap = h->opts.history_cap;
+    out->history_len = cap > 0 ? (c.bounce < cap ? c.bounce : cap) : 0;
+    return RT_OK;
+}
+
+rt_status rt_read_history(rt_handle *h, double *dst, long long max, long long *got)
+{
+    if (!h || !got || max < 0 || (max > 0 && !dst)) return RT_EINVAL;
+    *got = 0;
+    rt_stats_t s;
+    rt_status st = rt_stats(h, &s);
+    if (st != RT_OK) return st;
+    const long long cap = h->opts.history_cap;
+    long long len = s.history_len < max ? s.history_len : max;
+    if (len <= 0 || cap <= 0) return RT_OK;
+    DeviceGuard dg(h->device);
+    // the last `len` bounces: b = total-len .. total-1, slot b % cap
+    const long long first = s.bounces - len;
+    long long done = 0;
+    while (done < len) {
+        const long long slot = (first + done) % cap;
+        long long run = cap - slot;
+        if (run > len - done) run = len - done;
+        RT_TRY(cudaMemcpy(dst + done, h->hist + slot, sizeof(double) * (size_t)run, cudaMemcpyDeviceToHost));
+        done += run;
+    }
+    *got = len;
+    return RT_OK;
+}
+
+rt_status rt_read_spectrum(rt_handle *h, void *dst, size_t bytes)
+{
+    if (!h || !dst) return RT_EINVAL;
+    if (bytes != h->points() * h->rsz()) return RT_EINVAL;
+    DeviceGuard dg(h->device);
+    rt_status st = compute_spectrum(h);
+    if (st != RT_OK) return st;
+    RT_TRY(cudaMemcpyAsync(dst, h->S, bytes, cudaMemcpyDefault, h->stream));
+    return check_device_error(h);
+}
+
+rt_status rt_spectrum_peak(rt_handle *h, int ring, int *mx, int *my, double *power)
+{
+    if (!h || !mx || !my || !power || ring < 0) return RT_EINVAL;
+    DeviceGuard dg(h->device);
+    rt_status st = compute_spectrum(h);
+    if (st != RT_OK) return st;
+    PeakResult *d_out = &h->ctl->peak;
+    unsigned int *cnt = &h->ctl->peak_count;
+    if (h->precision == RT_FP32)
+        RT_TRY(launch_peak32(h->n, ring, static_cast<const float *>(h->S), h->peak_val, h->peak_idx, cnt, d_out, h->stream));
+    else
+        RT_TRY(launch_peak64(h->n, ring, static_cast<const double *>(h->S), h->peak_val, h->peak_idx, cnt, d_out, h->stream));
+    PeakResult r;
+    RT_TRY(cudaMemcpyAsync(&r, d_out, sizeof(r), cudaMemcpyDeviceToHost, h->stream));
+    st = check_device_error(h);
+    if (st != RT_OK) return st;
+    if (r.value < 0.0) {
+        *mx = 0;
+        *my = 0;
+        *power = 0.0;
+        return RT_OK;
+    }
+    const int n = h->n;
+    const int kx = (int)(r.index % n), ky = (int)(r.index / n);
+    *mx = kx < n / 2 ? kx : kx - n;
+    *my = ky < n / 2 ? ky : ky - n;
+    *power = r.value;
+    return RT_OK;
+}
+
+rt_status rt_destroy(rt_handle *h)
+{
+    if (!h) return RT_OK;
+    DeviceGuard dg(h->device);
+    cudaStreamSynchronize(h->stream);
+    release(h);
+    delete h;
+    return RT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,91 @@
+// Internal declarations shared by the library's translation units: kernel
+// parameter blocks and the host-side launchers that dispatch on log2(n).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rtk {
+
+enum PumpKind { PUMP_SUPERGAUSS = 0, PUMP_UNIFORM = 1, PUMP_ARRAY = 2 };
+
+// Local map parameters: E <- sqrtR * A * exp(N/2) * E',
+// N <- N + (N0 - N (1 + I invIsat)) invT1, N0 = g0 * P(x, y).
+template <typename R>
+struct GainParams {
+    R sqrtR, invT1, invIsat, g0;
+    R inv_rp2;          // 1 / r_p^2 (super-Gaussian)
+    R half_order;       // order / 2
+    int int_half_order; // > 0 when order/2 is that integer (product form)
+    int edge;
+    int pump_kind;
+    const R *pump_tab;  // n*n N0 values when pump_kind == PUMP_ARRAY
+};
+
+// Per-bounce mean intensity: block partials, reduced by the last block to
+// arrive (fixed order, so the result is deterministic).
+struct StatParams {
+    double *part;          // one partial per block of the reducing kernel
+    unsigned int *count;   // arrival counter, reset by the last block
+    double *hist;          // ring of hist_cap means (may be null when hist_cap == 0)
+    long long hist_cap;
+    long long *bounce;     // device bounce counter (slot index for hist)
+    double *last_mean;     // mean intensity after the last bounce
+    int *err;              // sticky error word (0 or RT_ENUMERIC)
+};
+
+struct PeakResult {
+    double value;
+    long long index;
+};
+
+// ---- FP32 fused path: two sweeps per bounce --------------------------------
+// Column sweep: per column, forward FFT, x h(my), inverse FFT (in place).
+cudaError_t launch_col_diffract32(int logn, int colC, float2 *E, const float2 *tw, const float2 *h,
+                                  cudaStream_t s);
+// Row sweep: per row, forward FFT, x h(mx), inverse FFT, then the local map
+// (gain, mirror, edge, inversion update) and the mean-intensity reduction.
+cudaError_t launch_row_diffract_gain32(int logn, float2 *E, float *N, const float2 *tw, const float2 *h,
+                                       const GainParams<float> &g, const StatParams &st, cudaStream_t s);
+int row_blocks32(int logn);            // blocks of the row sweep (size of StatParams::part)
+// Set kernel attributes (shared-memory opt-in) of a bounce's kernels on the
+// current device; done before capturing a bounce into a CUDA graph.
+cudaError_t prepare_bounce32(int logn, int colC);
+cudaError_t prepare_bounce64(int logn);
+int col_tile_ok32(int logn, int colC); // 1 if that column tile width is instantiated and fits
+
+// Forward 2-D transform helpers (spectrum readout), FP32: rows out of place, columns in place.
+cudaError_t launch_row_fft32(int logn, const float2 *in, float2 *out, const float2 *tw, int dir, cudaStream_t s);
+cudaError_t launch_col_fft32(int logn, float2 *X, const float2 *tw, int dir, cudaStream_t s);
+
+// ---- FP64 plain path: six unfused sweeps per bounce --------------------------
+cudaError_t launch_row_fft64(int logn, const double2 *in, double2 *out, const double2 *tw, int dir,
+                             cudaStream_t s);
+cudaError_t launch_col_fft64(int logn, double2 *X, const double2 *tw, int dir, cudaStream_t s);
+cudaError_t launch_mul_h64(int n, double2 *E, const double2 *h, cudaStream_t s);
+cudaError_t launch_gain64(int n, double2 *E, double *N, const GainParams<double> &g, const StatParams &st,
+                          cudaStream_t s);
+int gain_blocks64(int n);
+
+// ---- set-up kernels (FP64 arithmetic, stored in the path's precision) -------
+cudaError_t launch_tables32(int n, double alpha, float2 *tw, float2 *h, cudaStream_t s);
+cudaError_t launch_tables64(int n, double alpha, double2 *tw, double2 *h, cudaStream_t s);
+cudaError_t launch_noise32(int n, unsigned long long seed, double amp, float2 *E, cudaStream_t s);
+cudaError_t launch_noise64(int n, unsigned long long seed, double amp, double2 *E, cudaStream_t s);
+// N0 = g0 * P in FP64 (profile: device array of n*n doubles or null), stored as R.
+cudaError_t launch_pump32(int n, int kind, double g0, double order, double radius, const double *profile,
+                          float *out, cudaStream_t s);
+cudaError_t launch_pump64(int n, int kind, double g0, double order, double radius, const double *profile,
+                          double *out, cudaStream_t s);
+
+// ---- spectrum readout ----------------------------------------------------------
+cudaError_t launch_power32(int n, const float2 *X, float *S, cudaStream_t s);
+cudaError_t launch_power64(int n, const double2 *X, double *S, cudaStream_t s);
+// Folded-power argmax over a power spectrum S (float or double).
+cudaError_t launch_peak32(int n, int ring, const float *S, double *part_val, long long *part_idx,
+                          unsigned int *count, PeakResult *out, cudaStream_t s);
+cudaError_t launch_peak64(int n, int ring, const double *S, double *part_val, long long *part_idx,
+                          unsigned int *count, PeakResult *out, cudaStream_t s);
+int peak_blocks(int n);
+
+}  // namespace rtk

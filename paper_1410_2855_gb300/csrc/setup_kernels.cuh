@@ -1,0 +1,174 @@
+// Set-up and readout kernels, generic over the storage precision.  All of
+// their arithmetic is FP64 (tables, noise, pump); results are stored in the
+// path's precision.
+#pragma once
+
+#include <climits>
+
+#include "fft_core.cuh"
+#include "rt_internal.h"
+
+namespace rtk {
+
+// Forward twiddles tw[k] = exp(-2 pi i k / n) and the per-axis propagator
+// h[k] = exp(-i pi alpha m^2) / n, m the signed frequency of bin k (the 1-D
+// factor of the transfer function of eq. limit_of_operators_renorm_final;
+// the 1/n carries the inverse transform's normalisation for that axis).
+// alpha*m^2 is split into a rounded product and its exact FMA residual, the
+// product is reduced modulo 2 exactly (fmod), and sincospi evaluates
+// exp(-i pi t) on the reduced argument, so phases of thousands of radians
+// keep full FP64 accuracy.
+template <typename V>
+__global__ void k_tables(int n, double alpha, V *tw, V *h)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    double s, c;
+    sincospi(2.0 * (double)k / (double)n, &s, &c);
+    tw[k] = cmk<V>(c, -s);
+    const long long m = k < n / 2 ? k : (long long)k - n;
+    const double m2 = (double)(m * m);
+    const double hi = alpha * m2;
+    const double lo = fma(alpha, m2, -hi);
+    const double t = fmod(hi, 2.0) + lo;
+    double sp, cp;
+    sincospi(t, &sp, &cp);
+    const double inv = 1.0 / (double)n;
+    h[k] = cmk<V>(cp * inv, -sp * inv);
+}
+
+// splitmix64 (Steele, Lea & Flood 2014) as a counter-based stream: output c
+// of the stream whose state starts at seed.
+__device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed, unsigned long long c)
+{
+    unsigned long long z = seed + (c + 1ull) * 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+// Complex Gaussian noise by Box-Muller on two uniforms per point:
+// E = amp/sqrt(2) * sqrt(-2 ln(1 - u1)) * exp(2 pi i u2).
+template <typename V>
+__global__ void k_noise(int n, unsigned long long seed, double amp, V *E)
+{
+    const size_t P = (size_t)n * n;
+    const double sigma = amp * 0.70710678118654752440;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < P; i += (size_t)gridDim.x * blockDim.x) {
+        const double u1 = (double)(splitmix64_at(seed, 2ull * i) >> 11) * 0x1.0p-53;
+        const double u2 = (double)(splitmix64_at(seed, 2ull * i + 1ull) >> 11) * 0x1.0p-53;
+        const double rho = sigma * sqrt(-2.0 * log(1.0 - u1));
+        double s, c;
+        sincospi(2.0 * u2, &s, &c);
+        E[i] = cmk<V>(rho * c, rho * s);
+    }
+}
+
+// Unsaturated inversion N0 = g0 * P(x, y) in FP64.
+template <typename R>
+__global__ void k_pump(int n, int kind, double g0, double order, double radius, const double *profile, R *out)
+{
+    const size_t P = (size_t)n * n;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < P; i += (size_t)gridDim.x * blockDim.x) {
+        double v;
+        if (kind == PUMP_UNIFORM) {
+            v = g0;
+        } else if (kind == PUMP_ARRAY) {
+            v = g0 * profile[i];
+        } else {
+            const int x = (int)(i % n), y = (int)(i / n);
+            const double xc = (double)(x - n / 2) / (double)(n / 2);
+            const double yc = (double)(y - n / 2) / (double)(n / 2);
+            const double q = (xc * xc + yc * yc) / (radius * radius);
+            v = g0 * exp(-(q > 0.0 ? pow(q, 0.5 * order) : 0.0));
+        }
+        out[i] = (R)v;
+    }
+}
+
+template <typename V, typename R>
+__global__ void k_power(size_t P, const V *X, R *S)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < P; i += (size_t)gridDim.x * blockDim.x) {
+        const V x = X[i];
+        S[i] = x.x * x.x + x.y * x.y;
+    }
+}
+
+// Folded-power argmax (see rt_spectrum_peak): bin k and its mirror -k form
+// one peak filed under the smaller flat index; ties to the smaller index.
+__device__ __forceinline__ bool peak_better(double v, long long k, double bv, long long bk)
+{
+    return v > bv || (v == bv && k < bk);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_peak(int n, int ring, const R *S, double *part_val, long long *part_idx,
+                                              unsigned int *count, PeakResult *out)
+{
+    __shared__ double sv[256];
+    __shared__ long long sk[256];
+    __shared__ int is_last;
+    const long long P = (long long)n * n;
+    double bv = -1.0;
+    long long bk = LLONG_MAX;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < P; k += (long long)gridDim.x * blockDim.x) {
+        const int ky = (int)(k / n), kx = (int)(k % n);
+        const long long kp = (long long)((n - ky) % n) * n + (n - kx) % n;
+        if (kp < k) continue;
+        const int mx = kx < n / 2 ? kx : kx - n, my = ky < n / 2 ? ky : ky - n;
+        const int amx = mx < 0 ? -mx : mx, amy = my < 0 ? -my : my;
+        if ((amx > amy ? amx : amy) < ring) continue;
+        const double v = (kp == k) ? (double)S[k] : (double)S[k] + (double)S[kp];
+        if (peak_better(v, k, bv, bk)) { bv = v; bk = k; }
+    }
+    sv[threadIdx.x] = bv;
+    sk[threadIdx.x] = bk;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o && peak_better(sv[threadIdx.x + o], sk[threadIdx.x + o], sv[threadIdx.x], sk[threadIdx.x])) {
+            sv[threadIdx.x] = sv[threadIdx.x + o];
+            sk[threadIdx.x] = sk[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part_val[blockIdx.x] = sv[0];
+        part_idx[blockIdx.x] = sk[0];
+        __threadfence();
+        is_last = (atomicAdd(count, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    bv = -1.0;
+    bk = LLONG_MAX;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += 256) {
+        const double v = __ldcg(part_val + i);
+        const long long k = __ldcg(part_idx + i);
+        if (peak_better(v, k, bv, bk)) { bv = v; bk = k; }
+    }
+    sv[threadIdx.x] = bv;
+    sk[threadIdx.x] = bk;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o && peak_better(sv[threadIdx.x + o], sk[threadIdx.x + o], sv[threadIdx.x], sk[threadIdx.x])) {
+            sv[threadIdx.x] = sv[threadIdx.x + o];
+            sk[threadIdx.x] = sk[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out->value = sv[0];
+        out->index = sk[0];
+        *count = 0u;
+    }
+}
+
+inline int grid_for(size_t P, int threads, int cap)
+{
+    size_t b = (P + threads - 1) / threads;
+    return (int)(b < (size_t)cap ? (b > 0 ? b : 1) : cap);
+}
+
+}  // namespace rtk

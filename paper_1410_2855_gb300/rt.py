@@ -1,0 +1,288 @@
+"""Thin ctypes binding of the C ABI declared in include/rt.h.
+
+Functions carry the C names and only marshal arguments; every step of the
+bounce map runs in the CUDA library.  Loading fails loudly if the library has
+not been built: there is no CPU fallback.  A non-OK status raises RtError.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import platform
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", f"libbouncemap_{platform.machine()}.so")
+
+RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENUMERIC, RT_ETIMEOUT, RT_EBUSY = 0, -1, -2, -3, -4, -5, -6
+RT_PUMP_SUPERGAUSS, RT_PUMP_UNIFORM, RT_PUMP_ARRAY = 0, 1, 2
+RT_FP32, RT_FP64 = 0, 1
+
+
+class RtError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+class rt_pump(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("order", ctypes.c_double), ("radius", ctypes.c_double),
+                ("profile", ctypes.c_void_p)]
+
+
+class rt_opts(ctypes.Structure):
+    _fields_ = [("Isat", ctypes.c_double), ("edge_px", ctypes.c_int), ("precision", ctypes.c_int),
+                ("seed", ctypes.c_ulonglong), ("noise_amp", ctypes.c_double),
+                ("pump_diam_over_window", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
+                ("history_cap", ctypes.c_longlong), ("chunk", ctypes.c_int)]
+
+
+class rt_stats_t(ctypes.Structure):
+    _fields_ = [("bounces", ctypes.c_longlong), ("mean_intensity", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("n", ctypes.c_int), ("precision", ctypes.c_int), ("last_error", ctypes.c_int),
+                ("history_len", ctypes.c_longlong)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library (raises ImportError if it was never built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"bounce-map CUDA library missing at {LIB_PATH}; build it with "
+                              "paper_1410_2855_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, d, ll, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong, ctypes.c_size_t
+        sig = {
+            "rt_opts_default": [ctypes.POINTER(rt_opts)],
+            "rt_create": [i, d, ctypes.POINTER(rt_pump), d, d, d, ctypes.POINTER(rt_opts), ctypes.POINTER(vp)],
+            "rt_step": [vp, ll],
+            "rt_sync": [vp],
+            "rt_sweep": [vp, i],
+            "rt_read_field": [vp, vp, sz],
+            "rt_read_inversion": [vp, vp, sz],
+            "rt_write_field": [vp, vp, sz],
+            "rt_write_inversion": [vp, vp, sz],
+            "rt_set_bounces": [vp, ll],
+            "rt_stats": [vp, ctypes.POINTER(rt_stats_t)],
+            "rt_read_history": [vp, vp, ll, ctypes.POINTER(ll)],
+            "rt_read_spectrum": [vp, vp, sz],
+            "rt_spectrum_peak": [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(d)],
+            "rt_destroy": [vp],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.rt_status_string.argtypes = [ctypes.c_int]
+        L.rt_status_string.restype = ctypes.c_char_p
+        L.rt_version.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def status_string(s: int) -> str:
+    try:
+        return lib().rt_status_string(s).decode()
+    except ImportError:
+        return "library not loaded"
+
+
+def _check(status: int, where: str):
+    if status != RT_OK:
+        raise RtError(status, where)
+
+
+def _ptr(a) -> int:
+    """Address of a numpy array or torch tensor (host or device)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def _nbytes(a) -> int:
+    return a.nbytes if isinstance(a, np.ndarray) else a.numel() * a.element_size()
+
+
+# ----------------------------------------------------------------- C-named API
+
+def rt_version() -> int:
+    return lib().rt_version()
+
+
+def rt_opts_default() -> rt_opts:
+    o = rt_opts()
+    _check(lib().rt_opts_default(ctypes.byref(o)), "rt_opts_default")
+    return o
+
+
+def rt_create(n: int, fresnel: float, pump: rt_pump | None, g0: float, T1: float, R: float,
+              opts: rt_opts | None = None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().rt_create(n, fresnel, ctypes.byref(pump) if pump is not None else None, g0, T1, R,
+                           ctypes.byref(opts) if opts is not None else None, ctypes.byref(h)), "rt_create")
+    return h
+
+
+def rt_step(h, n_bounces: int):
+    _check(lib().rt_step(h, int(n_bounces)), "rt_step")
+
+
+def rt_sync(h):
+    _check(lib().rt_sync(h), "rt_sync")
+
+
+RT_SWEEP_COLUMNS, RT_SWEEP_ROWS = 0, 1
+
+
+def rt_sweep(h, which: int):
+    _check(lib().rt_sweep(h, which), "rt_sweep")
+
+
+def rt_read_field(h, dst):
+    _check(lib().rt_read_field(h, _ptr(dst), _nbytes(dst)), "rt_read_field")
+    return dst
+
+
+def rt_read_inversion(h, dst):
+    _check(lib().rt_read_inversion(h, _ptr(dst), _nbytes(dst)), "rt_read_inversion")
+    return dst
+
+
+def rt_write_field(h, src):
+    _check(lib().rt_write_field(h, _ptr(src), _nbytes(src)), "rt_write_field")
+
+
+def rt_write_inversion(h, src):
+    _check(lib().rt_write_inversion(h, _ptr(src), _nbytes(src)), "rt_write_inversion")
+
+
+def rt_set_bounces(h, bounces: int):
+    _check(lib().rt_set_bounces(h, int(bounces)), "rt_set_bounces")
+
+
+def rt_stats(h) -> rt_stats_t:
+    s = rt_stats_t()
+    _check(lib().rt_stats(h, ctypes.byref(s)), "rt_stats")
+    return s
+
+
+def rt_read_history(h, max_values: int) -> np.ndarray:
+    out = np.zeros(max(int(max_values), 0), np.float64)
+    got = ctypes.c_longlong()
+    _check(lib().rt_read_history(h, out.ctypes.data if out.size else None, out.size, ctypes.byref(got)),
+           "rt_read_history")
+    return out[: got.value]
+
+
+def rt_read_spectrum(h, dst):
+    _check(lib().rt_read_spectrum(h, _ptr(dst), _nbytes(dst)), "rt_read_spectrum")
+    return dst
+
+
+def rt_spectrum_peak(h, ring: int = 0):
+    mx, my, pw = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().rt_spectrum_peak(h, ring, ctypes.byref(mx), ctypes.byref(my), ctypes.byref(pw)),
+           "rt_spectrum_peak")
+    return mx.value, my.value, pw.value
+
+
+def rt_destroy(h):
+    _check(lib().rt_destroy(h), "rt_destroy")
+
+
+# --------------------------------------------------------- convenience wrapper
+
+class Resonator:
+    """One resonator handle with numpy-returning readouts.
+
+    ``Resonator(n, fresnel, g0, T1, R, precision=RT_FP32, **opts)``; keyword
+    options are the rt_opts fields (Isat, edge_px, seed, noise_amp,
+    pump_diam_over_window, cuda_stream, history_cap, chunk) plus pump_kind,
+    pump_order, pump_radius, pump_profile.
+    """
+
+    def __init__(self, n, fresnel, g0, T1, R, precision=RT_FP32, pump_kind=RT_PUMP_SUPERGAUSS,
+                 pump_order=10.0, pump_radius=0.8, pump_profile=None, **opts):
+        o = rt_opts_default()
+        o.precision = precision
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
+        self._profile = None
+        p = rt_pump(kind=pump_kind, order=pump_order, radius=pump_radius, profile=None)
+        if pump_kind == RT_PUMP_ARRAY:
+            self._profile = np.ascontiguousarray(pump_profile, np.float64).reshape(n, n)
+            p.profile = self._profile.ctypes.data
+        self.n = n
+        self.precision = precision
+        self.cdtype = np.complex128 if precision == RT_FP64 else np.complex64
+        self.rdtype = np.float64 if precision == RT_FP64 else np.float32
+        self.h = rt_create(n, fresnel, p, g0, T1, R, o)
+
+    @classmethod
+    def from_params(cls, p, precision=RT_FP32, **opts):
+        """From a workloads.Resonator parameter record."""
+        return cls(p.n, p.fresnel, p.g0, p.T1, p.R, precision=precision, pump_order=p.pump_order,
+                   pump_radius=p.pump_radius, Isat=p.Isat, edge_px=p.edge, seed=p.seed, noise_amp=p.noise_amp,
+                   pump_diam_over_window=p.d_over_w, **opts)
+
+    def step(self, n_bounces: int):
+        rt_step(self.h, n_bounces)
+        return self
+
+    def sync(self):
+        rt_sync(self.h)
+
+    def field(self) -> np.ndarray:
+        return rt_read_field(self.h, np.empty((self.n, self.n), self.cdtype))
+
+    def inversion(self) -> np.ndarray:
+        return rt_read_inversion(self.h, np.empty((self.n, self.n), self.rdtype))
+
+    def set_field(self, E):
+        rt_write_field(self.h, np.ascontiguousarray(E, self.cdtype))
+        rt_sync(self.h)
+
+    def set_inversion(self, N):
+        rt_write_inversion(self.h, np.ascontiguousarray(N, self.rdtype))
+        rt_sync(self.h)
+
+    def spectrum(self) -> np.ndarray:
+        return rt_read_spectrum(self.h, np.empty((self.n, self.n), self.rdtype))
+
+    def peak(self, ring: int = 0):
+        return rt_spectrum_peak(self.h, ring)
+
+    def stats(self) -> rt_stats_t:
+        return rt_stats(self.h)
+
+    def history(self, max_values: int) -> np.ndarray:
+        return rt_read_history(self.h, max_values)
+
+    def close(self):
+        if self.h:
+            rt_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,101 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, exports every
+function include/rt.h declares, and its structures have the layout the
+Python binding assumes.  Only host-side logic is exercised (no compute)."""
+import ctypes
+import os
+import re
+import subprocess
+import textwrap
+
+import pytest
+
+from paper_1410_2855_gb300 import build, rt
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rt.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return rt.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rt_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["rt_create", "rt_step", "rt_read_field", "rt_read_inversion", "rt_destroy",
+                     "rt_write_field", "rt_write_inversion", "rt_stats", "rt_status_string"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_and_version(lib):
+    assert rt.status_string(0) == "ok"
+    assert rt.status_string(-1) == "invalid argument"
+    assert rt.status_string(-4) == "non-finite field intensity"
+    assert rt.rt_version() >= 100
+
+
+def test_default_options(lib):
+    o = rt.rt_opts_default()
+    assert (o.Isat, o.edge_px, o.precision, o.seed, o.noise_amp) == (1.0, 8, 0, 14102855, 1e-6)
+    assert o.pump_diam_over_window == 0.8 and o.history_cap == 65536 and o.chunk == 500
+
+
+@pytest.mark.parametrize("args", [
+    dict(n=100), dict(n=16), dict(n=8192), dict(fresnel=0.0), dict(fresnel=float("nan")),
+    dict(g0=-0.1), dict(T1=0.5), dict(R=0.0), dict(R=1.5),
+])
+def test_create_rejects_bad_arguments_before_touching_the_device(lib, args):
+    p = dict(n=64, fresnel=100.0, g0=0.2, T1=1000.0, R=0.95)
+    p.update(args)
+    h = ctypes.c_void_p()
+    st = lib.rt_create(p["n"], p["fresnel"], None, p["g0"], p["T1"], p["R"], None, ctypes.byref(h))
+    assert st == rt.RT_EINVAL and not h.value
+
+
+def test_create_rejects_bad_options(lib):
+    h = ctypes.c_void_p()
+    for field, value in [("precision", 3), ("edge_px", -1), ("Isat", 0.0), ("history_cap", -5), ("chunk", -1)]:
+        o = rt.rt_opts_default()
+        setattr(o, field, value)
+        assert lib.rt_create(64, 100.0, None, 0.2, 1000.0, 0.95, ctypes.byref(o), ctypes.byref(h)) == rt.RT_EINVAL
+    p = rt.rt_pump(kind=rt.RT_PUMP_ARRAY, order=10.0, radius=0.8, profile=None)
+    assert lib.rt_create(64, 100.0, ctypes.byref(p), 0.2, 1000.0, 0.95, None, ctypes.byref(h)) == rt.RT_EINVAL
+
+
+def test_null_handles_are_rejected(lib):
+    assert lib.rt_step(None, 1) == rt.RT_EINVAL
+    assert lib.rt_sync(None) == rt.RT_EINVAL
+    assert lib.rt_read_field(None, None, 0) == rt.RT_EINVAL
+    assert lib.rt_destroy(None) == rt.RT_OK
+
+
+def test_struct_layouts_match_the_header(tmp_path, lib):
+    src = tmp_path / "sizes.c"
+    src.write_text(textwrap.dedent("""
+        #include <stdio.h>
+        #include <stddef.h>
+        #include "rt.h"
+        int main(void) {
+            printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(rt_opts), sizeof(rt_pump), sizeof(rt_stats_t),
+                   offsetof(rt_opts, chunk), offsetof(rt_stats_t, history_len), offsetof(rt_opts, cuda_stream));
+            return 0;
+        }
+    """))
+    exe = tmp_path / "sizes"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()))
+    want = [ctypes.sizeof(rt.rt_opts), ctypes.sizeof(rt.rt_pump), ctypes.sizeof(rt.rt_stats_t),
+            rt.rt_opts.chunk.offset, rt.rt_stats_t.history_len.offset, rt.rt_opts.cuda_stream.offset]
+    assert got == want
