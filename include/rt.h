@@ -86,6 +86,7 @@ typedef struct {
     void *cuda_stream;            /* cudaStream_t to run on; NULL = the legacy default stream */
     long long history_cap;        /* >0: keep the mean intensity of the last history_cap bounces (65536) */
     int chunk;                    /* bounces per captured CUDA graph in rt_step; 0 = no graphs (500) */
+    int col_tile;                 /* FP32 column-sweep tile width in columns (2, 4, 8 or 16); 0 = library choice (0) */
 } rt_opts;
 
 rt_status rt_opts_default(rt_opts *opts);
@@ -101,7 +102,7 @@ typedef struct {
     long long history_len;    /* bounces currently held in the history ring */
 } rt_stats_t;
 
-/* Create a resonator of side n (power of two, 16 <= n <= 4096) with Fresnel
+/* Create a resonator of side n (power of two, 32 <= n <= 4096) with Fresnel
  * number `fresnel` (> 0), pump `pump`, small-signal gain g0 (intensity gain
  * exponent per pass, >= 0), inversion relaxation time T1 (in bounces, >= 1)
  * and mirror reflectivity R (0 < R <= 1).  Allocates the field, inversion and

@@ -47,19 +47,23 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+def build(force: bool = False, verbose: bool = False, extra_flags=(), tag: str = "") -> str:
     """Compile and link the library if any source is newer than it.  Returns
-    the path of the shared library."""
-    os.makedirs(BUILD_DIR, exist_ok=True)
+    the path of the shared library.  A non-empty `tag` builds a variant
+    (e.g. with extra -D flags) into its own object directory and library
+    file, leaving the default build untouched."""
+    build_dir = BUILD_DIR + (f"_{tag}" if tag else "")
+    lib_path = LIB_PATH if not tag else os.path.join(LIB_DIR, f"libbouncemap_{platform.machine()}_{tag}.so")
+    os.makedirs(build_dir, exist_ok=True)
     os.makedirs(LIB_DIR, exist_ok=True)
     deps = _deps()
-    if not force and not _stale(LIB_PATH, deps):
-        return LIB_PATH
+    if not force and not _stale(lib_path, deps):
+        return lib_path
     exe = nvcc()
     headers = [d for d in deps if not d.endswith(".cu")]
 
     def compile_one(src):
-        obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src) + ".o")
         if force or _stale(obj, [src] + headers):
             cmd = [exe, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
             r = subprocess.run(cmd, capture_output=True, text=True)
@@ -72,13 +76,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB_PATH + ".tmp"
+    tmp = lib_path + ".tmp"
     cmd = [exe, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr[-4000:]}")
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

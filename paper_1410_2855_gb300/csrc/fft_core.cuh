@@ -11,6 +11,11 @@
 // inverse transform follow each other with no data movement in between
 // (the diffraction operator of eq. limit_of_operators_renorm_final is
 // diagonal in the Fourier basis).
+//
+// Twiddles come from a pass-major table (see Plan::tw_size): for the pass
+// with span Ns and radix R, entry [(r-1)*Ns + j] = exp(-2 pi i r j / (Ns R)),
+// so the R-1 loads of a thread are each coalesced across the threads of a
+// warp.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -40,6 +45,11 @@ template <typename V> __device__ __forceinline__ V csub(V a, V b) { return cmk<V
 template <typename V> __device__ __forceinline__ V cmul(V a, V b)
 {
     return cmk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename V> __device__ __forceinline__ V cmulc(V a, V b)
+{
+    return cmk<V>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 template <typename V> __device__ __forceinline__ V cscale(V a, typename real_of<V>::type s)
 {
@@ -96,72 +106,108 @@ __device__ __forceinline__ void dft(V (&v)[RAD])
 
 // Shared-memory index with one pad element per 16: keeps the stride-16
 // writes of the first pass and the unit-stride reads conflict-free.
-__device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int padi(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int padded_len(int n) { return n + n / 16; }
 
 template <int LOGN> struct Plan {
-    static_assert(LOGN >= 4 && LOGN <= 12, "line length 16..4096");
+    static_assert(LOGN >= 5 && LOGN <= 12, "line length 32..4096");
     static constexpr int N = 1 << LOGN;
     static constexpr int T = N / 16;                 // threads per line
     static constexpr int P16 = LOGN / 4;             // radix-16 passes
     static constexpr int LASTLOG = LOGN % 4;         // log2 of the trailing radix (0: none)
     static constexpr int LASTR = 1 << LASTLOG;
+    // entries of the pass-major twiddle table
+    static constexpr int tw_size()
+    {
+        int s = 0, Ns = 16;
+        for (int p = 1; p < P16; ++p, Ns *= 16) s += 15 * Ns;
+        if (LASTLOG) s += (LASTR - 1) * Ns;
+        return s;
+    }
 };
 
-// Twiddle exp(DIR * 2 pi i k / N) from the forward table tw[k] = exp(-2 pi i k / N).
+// Twiddle from the forward table (exp(-...)), conjugated for the inverse.
 template <int DIR, typename V>
-__device__ __forceinline__ V twiddle(const V *__restrict__ tw, int k)
+__device__ __forceinline__ V twmul(V a, const V *__restrict__ tw, int k)
 {
-    V w = __ldg(tw + k);
-    if (DIR > 0) w.y = -w.y;
-    return w;
+    const V w = __ldg(tw + k);
+    return DIR > 0 ? cmulc(a, w) : cmul(a, w);
 }
+
+// Element i of a padded line with element stride CS (1 for a row buffer; C
+// for the [row][column] tile of the column sweep).
+template <int CS, typename V> __device__ __forceinline__ V &sm_at(V *line, int i) { return line[padi(i) * CS]; }
 
 // One Stockham FFT of a line.  On entry v[s] = x[t + T s]; on exit
 // v[s] = X[t + T s], X[k] = sum_j x[j] exp(DIR 2 pi i jk / N) (unnormalised).
-// S(i) returns a reference to shared element i of this line (already padded
-// by the caller's accessor); sync() is a barrier over every thread that
-// shares the shared buffer.  Each exchange is barrier, write, barrier, read.
-template <int LOGN, int DIR, typename V, typename SmemF, typename SyncF>
-__device__ __forceinline__ void fft_line(V (&v)[16], int t, SmemF S, const V *__restrict__ tw, SyncF sync)
+// `line` is this line's padded shared buffer (element stride CS); sync() is a
+// barrier over every thread that shares the buffer.  Each exchange is
+// barrier, write, barrier, read.  Shared addresses are a per-thread base plus
+// compile-time offsets: spans and T are multiples of 16 wherever the pad
+// arithmetic allows it.
+template <int LOGN, int DIR, int CS, typename V, typename SyncF>
+__device__ __forceinline__ void fft_line(V (&v)[16], const int t, V *line, const V *__restrict__ tw, SyncF sync)
 {
     using P = Plan<LOGN>;
     constexpr int N = P::N, T = P::T;
-    // pass 0: radix 16, Ns = 1 (no twiddles)
+    constexpr bool T16 = (T % 16) == 0;
+    V *rd_base = line + padi(t) * CS;  // element t of the line (valid base when T16)
     dft<16, DIR>(v);
-    int Ns = 1;
+    int off = 0;
 #pragma unroll
     for (int p = 1; p < P::P16; ++p) {
-        const int idxD = (t / Ns) * Ns * 16 + (t % Ns);
+        const int NsPrev = 1 << (4 * (p - 1));
+        const int Ns = NsPrev * 16;
         sync();
+        if (NsPrev == 1) {
+            V *w = line + 17 * t * CS;
 #pragma unroll
-        for (int r = 0; r < 16; ++r) S(idxD + r * Ns) = v[r];
+            for (int r = 0; r < 16; ++r) w[r * CS] = v[r];
+        } else {
+            const int idxD = (t / NsPrev) * NsPrev * 16 + (t % NsPrev);
+            V *w = line + padi(idxD) * CS;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) w[r * (17 * NsPrev / 16) * CS] = v[r];
+        }
         sync();
-        Ns *= 16;
+        if constexpr (T16) {
 #pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = S(t + r * T);
-        const int e = (t % Ns) * (N / (16 * Ns));
+            for (int r = 0; r < 16; ++r) v[r] = rd_base[r * (17 * T / 16) * CS];
+        } else {
 #pragma unroll
-        for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], twiddle<DIR>(tw, r * e));
+            for (int r = 0; r < 16; ++r) v[r] = sm_at<CS>(line, t + r * T);
+        }
+        const V *twp = tw + off + (t & (Ns - 1));
+#pragma unroll
+        for (int r = 1; r < 16; ++r) v[r] = twmul<DIR>(v[r], twp, (r - 1) * Ns);
+        off += 15 * Ns;
         dft<16, DIR>(v);
     }
     if constexpr (P::LASTLOG > 0) {
         constexpr int RL = P::LASTR, NB = 16 / RL, NsL = N / RL;
-        {
-            const int idxD = (t / Ns) * Ns * 16 + (t % Ns);
-            sync();
+        constexpr int NsPrev = NsL / 16;
+        sync();
+        if constexpr (NsPrev == 1) {
+            V *w = line + 17 * t * CS;
 #pragma unroll
-            for (int r = 0; r < 16; ++r) S(idxD + r * Ns) = v[r];
-            sync();
+            for (int r = 0; r < 16; ++r) w[r * CS] = v[r];
+        } else {
+            const int idxD = (t / NsPrev) * NsPrev * 16 + (t % NsPrev);
+            V *w = line + padi(idxD) * CS;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) w[r * (17 * NsPrev / 16) * CS] = v[r];
         }
+        sync();
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
             const int j = t + i * T;
+            V *rb = T16 ? rd_base + i * (17 * T / 16) * CS : line + padi(j) * CS;
             V u[RL];
 #pragma unroll
-            for (int r = 0; r < RL; ++r) u[r] = S(j + r * NsL);
+            for (int r = 0; r < RL; ++r) u[r] = rb[r * (17 * NsL / 16) * CS];
+            const V *twp = tw + off + j;
 #pragma unroll
-            for (int r = 1; r < RL; ++r) u[r] = cmul(u[r], twiddle<DIR>(tw, r * j));
+            for (int r = 1; r < RL; ++r) u[r] = twmul<DIR>(u[r], twp, (r - 1) * NsL);
             dft<RL, DIR>(u);
 #pragma unroll
             for (int r = 0; r < RL; ++r) v[i + r * NB] = u[r];

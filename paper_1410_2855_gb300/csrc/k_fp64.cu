@@ -29,12 +29,12 @@ static cudaError_t row_fft64(const double2 *in, double2 *out, const double2 *tw,
     const StatParams st{};
     if (dir < 0) {
         cudaError_t e = row_attr<double, LOGN, MODE_FWD>();
-        auto k = k_row<double, LOGN, MODE_FWD>;
+        auto k = k_row<double, LOGN, MODE_FWD, PE_SG10>;
         if (e != cudaSuccess) return e;
         k<<<(1 << LOGN) / LPC, LPC * Plan<LOGN>::T, sm, s>>>(in, out, nullptr, tw, nullptr, g, st);
     } else {
         cudaError_t e = row_attr<double, LOGN, MODE_INV>();
-        auto k = k_row<double, LOGN, MODE_INV>;
+        auto k = k_row<double, LOGN, MODE_INV, PE_SG10>;
         if (e != cudaSuccess) return e;
         k<<<(1 << LOGN) / LPC, LPC * Plan<LOGN>::T, sm, s>>>(in, out, nullptr, tw, nullptr, g, st);
     }
@@ -126,7 +126,11 @@ cudaError_t launch_gain64(int n, double2 *E, double *N, const GainParams<double>
 
 cudaError_t launch_tables64(int n, double alpha, double2 *tw, double2 *h, cudaStream_t s)
 {
-    k_tables<double2><<<(n + 255) / 256, 256, 0, s>>>(n, alpha, tw, h);
+    int logn = 0;
+    while ((1 << logn) < n) ++logn;
+    const int total = twiddle_count(logn);
+    k_prop_table<double2><<<(n + 255) / 256, 256, 0, s>>>(n, alpha, h);
+    if (total > 0) k_twiddles<double2><<<(total + 255) / 256, 256, 0, s>>>(logn, total, tw);
     return cudaGetLastError();
 }
 

@@ -81,6 +81,7 @@ struct rt_handle {
     Ctl *ctl = nullptr;
     long long bounces = 0;
     int colC = 4;
+    int pe = 0;                   // pump evaluation of the FP32 row sweep (PumpEval)
     std::map<long long, cudaGraphExec_t> graphs;
     size_t esz() const { return precision == RT_FP64 ? 16 : 8; }
     size_t rsz() const { return precision == RT_FP64 ? 8 : 4; }
@@ -114,7 +115,7 @@ GainParams<R> gain_params(rt_handle *h)
     g.inv_rp2 = (R)(1.0 / (r * r));
     const double half = 0.5 * h->pump.order;
     g.half_order = (R)half;
-    g.int_half_order = (half == std::floor(half) && half >= 1 && half <= 16) ? (int)half : 0;
+    g.int_half_order = (h->pump.kind == RT_PUMP_SUPERGAUSS && half == 5.0) ? 5 : 0;
     g.edge = h->opts.edge_px;
     g.pump_kind = h->pump.kind;
     g.pump_tab = reinterpret_cast<const R *>(h->pump_tab);
@@ -138,7 +139,8 @@ cudaError_t enqueue_bounce(rt_handle *h, cudaStream_t s)
         const float2 *tw = static_cast<const float2 *>(h->tw), *hh = static_cast<const float2 *>(h->h);
         cudaError_t e = launch_col_diffract32(h->logn, h->colC, E, tw, hh, s);
         if (e != cudaSuccess) return e;
-        return launch_row_diffract_gain32(h->logn, E, static_cast<float *>(h->N), tw, hh, gain_params<float>(h), st, s);
+        return launch_row_diffract_gain32(h->logn, h->pe, E, static_cast<float *>(h->N), tw, hh, gain_params<float>(h), st,
+                                          s);
     }
     double2 *E = static_cast<double2 *>(h->E);
     const double2 *tw = static_cast<const double2 *>(h->tw), *hh = static_cast<const double2 *>(h->h);
@@ -158,7 +160,7 @@ cudaError_t get_graph(rt_handle *h, long long k, cudaGraphExec_t *out)
         *out = it->second;
         return cudaSuccess;
     }
-    cudaError_t e = h->precision == RT_FP32 ? prepare_bounce32(h->logn, h->colC) : prepare_bounce64(h->logn);
+    cudaError_t e = h->precision == RT_FP32 ? prepare_bounce32(h->logn, h->colC, h->pe) : prepare_bounce64(h->logn);
     if (e != cudaSuccess) return e;
     e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
@@ -285,6 +287,7 @@ rt_status rt_create(int n, double fresnel, const rt_pump *pump, double g0, doubl
     if (o.precision != RT_FP32 && o.precision != RT_FP64) return RT_EINVAL;
     if (!std::isfinite(o.noise_amp) || o.noise_amp < 0.0 || !finite_pos(o.pump_diam_over_window)) return RT_EINVAL;
     if (o.history_cap < 0 || o.chunk < 0) return RT_EINVAL;
+    if (o.col_tile != 0 && (o.precision != RT_FP32 || !col_tile_ok32(ilog2(n), o.col_tile))) return RT_EINVAL;
     if (p.kind == RT_PUMP_SUPERGAUSS && (!finite_pos(p.order) || !finite_pos(p.radius))) return RT_EINVAL;
     if (p.kind == RT_PUMP_ARRAY && !p.profile) return RT_EINVAL;
     if (p.kind < RT_PUMP_SUPERGAUSS || p.kind > RT_PUMP_ARRAY) return RT_EINVAL;
@@ -303,7 +306,9 @@ rt_status rt_create(int n, double fresnel, const rt_pump *pump, double g0, doubl
     h->pump = p;
     h->pump.profile = nullptr;
     h->stream = static_cast<cudaStream_t>(o.cuda_stream);
-    h->colC = default_col_c(h->logn);
+    h->colC = o.col_tile ? o.col_tile : default_col_c(h->logn);
+    // N0 on the fly for the order-10 super-Gaussian and the uniform pump, else from a table
+    h->pe = p.kind == RT_PUMP_UNIFORM ? 1 : ((p.kind == RT_PUMP_SUPERGAUSS && p.order == 10.0) ? 0 : 2);
     cudaGetDevice(&h->device);
 
     auto fail = [&](rt_status s) {
@@ -321,7 +326,7 @@ rt_status rt_create(int n, double fresnel, const rt_pump *pump, double g0, doubl
     RT_CREATE_TRY(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
     RT_CREATE_TRY(cudaMalloc(&h->E, P * h->esz()));
     RT_CREATE_TRY(cudaMalloc(&h->N, P * h->rsz()));
-    RT_CREATE_TRY(cudaMalloc(&h->tw, (size_t)n * h->esz()));
+    RT_CREATE_TRY(cudaMalloc(&h->tw, (size_t)(twiddle_entries(h->logn) + 1) * h->esz()));
     RT_CREATE_TRY(cudaMalloc(&h->h, (size_t)n * h->esz()));
     RT_CREATE_TRY(cudaMalloc(&h->part, sizeof(double) * kMaxPart));
     RT_CREATE_TRY(cudaMalloc(reinterpret_cast<void **>(&h->ctl), sizeof(Ctl)));
@@ -336,7 +341,7 @@ rt_status rt_create(int n, double fresnel, const rt_pump *pump, double g0, doubl
         RT_CREATE_TRY(launch_tables32(n, h->alpha, static_cast<float2 *>(h->tw), static_cast<float2 *>(h->h), h->stream));
         RT_CREATE_TRY(launch_noise32(n, o.seed, o.noise_amp, static_cast<float2 *>(h->E), h->stream));
         RT_CREATE_TRY(launch_pump32(n, p.kind, g0, p.order, p.radius, h->profile, static_cast<float *>(h->N), h->stream));
-        if (p.kind == RT_PUMP_ARRAY) {
+        if (h->pe == 2) {
             RT_CREATE_TRY(cudaMalloc(&h->pump_tab, sizeof(float) * P));
             RT_CREATE_TRY(cudaMemcpyAsync(h->pump_tab, h->N, sizeof(float) * P, cudaMemcpyDeviceToDevice, h->stream));
         }
@@ -344,7 +349,7 @@ rt_status rt_create(int n, double fresnel, const rt_pump *pump, double g0, doubl
         RT_CREATE_TRY(launch_tables64(n, h->alpha, static_cast<double2 *>(h->tw), static_cast<double2 *>(h->h), h->stream));
         RT_CREATE_TRY(launch_noise64(n, o.seed, o.noise_amp, static_cast<double2 *>(h->E), h->stream));
         RT_CREATE_TRY(launch_pump64(n, p.kind, g0, p.order, p.radius, h->profile, static_cast<double *>(h->N), h->stream));
-        if (p.kind == RT_PUMP_ARRAY) {
+        if (h->pe == 2) {
             RT_CREATE_TRY(cudaMalloc(&h->pump_tab, sizeof(double) * P));
             RT_CREATE_TRY(cudaMemcpyAsync(h->pump_tab, h->N, sizeof(double) * P, cudaMemcpyDeviceToDevice, h->stream));
         }
@@ -381,7 +386,7 @@ rt_status rt_sweep(rt_handle *h, int which)
     if (which == RT_SWEEP_COLUMNS) {
         RT_TRY(launch_col_diffract32(h->logn, h->colC, E, tw, hh, h->stream));
     } else {
-        RT_TRY(launch_row_diffract_gain32(h->logn, E, static_cast<float *>(h->N), tw, hh, gain_params<float>(h),
+        RT_TRY(launch_row_diffract_gain32(h->logn, h->pe, E, static_cast<float *>(h->N), tw, hh, gain_params<float>(h),
                                           stat_params(h), h->stream));
         h->bounces += 1;
     }

@@ -45,12 +45,14 @@ cudaError_t launch_col_diffract32(int logn, int colC, float2 *E, const float2 *t
                                   cudaStream_t s);
 // Row sweep: per row, forward FFT, x h(mx), inverse FFT, then the local map
 // (gain, mirror, edge, inversion update) and the mean-intensity reduction.
-cudaError_t launch_row_diffract_gain32(int logn, float2 *E, float *N, const float2 *tw, const float2 *h,
+// pe selects how N0 is evaluated: 0 super-Gaussian of order 10 on the fly,
+// 1 uniform, 2 from GainParams::pump_tab.
+cudaError_t launch_row_diffract_gain32(int logn, int pe, float2 *E, float *N, const float2 *tw, const float2 *h,
                                        const GainParams<float> &g, const StatParams &st, cudaStream_t s);
 int row_blocks32(int logn);            // blocks of the row sweep (size of StatParams::part)
 // Set kernel attributes (shared-memory opt-in) of a bounce's kernels on the
 // current device; done before capturing a bounce into a CUDA graph.
-cudaError_t prepare_bounce32(int logn, int colC);
+cudaError_t prepare_bounce32(int logn, int colC, int pe);
 cudaError_t prepare_bounce64(int logn);
 int col_tile_ok32(int logn, int colC); // 1 if that column tile width is instantiated and fits
 
@@ -68,6 +70,9 @@ cudaError_t launch_gain64(int n, double2 *E, double *N, const GainParams<double>
 int gain_blocks64(int n);
 
 // ---- set-up kernels (FP64 arithmetic, stored in the path's precision) -------
+// Entries of the pass-major twiddle table of a line FFT of length 2^logn.
+int twiddle_entries(int logn);
+// tw: pass-major twiddles (twiddle_entries(log2 n) entries); h: n per-axis propagator values.
 cudaError_t launch_tables32(int n, double alpha, float2 *tw, float2 *h, cudaStream_t s);
 cudaError_t launch_tables64(int n, double alpha, double2 *tw, double2 *h, cudaStream_t s);
 cudaError_t launch_noise32(int n, unsigned long long seed, double amp, float2 *E, cudaStream_t s);

@@ -10,22 +10,18 @@
 
 namespace rtk {
 
-// Forward twiddles tw[k] = exp(-2 pi i k / n) and the per-axis propagator
-// h[k] = exp(-i pi alpha m^2) / n, m the signed frequency of bin k (the 1-D
-// factor of the transfer function of eq. limit_of_operators_renorm_final;
-// the 1/n carries the inverse transform's normalisation for that axis).
-// alpha*m^2 is split into a rounded product and its exact FMA residual, the
-// product is reduced modulo 2 exactly (fmod), and sincospi evaluates
-// exp(-i pi t) on the reduced argument, so phases of thousands of radians
-// keep full FP64 accuracy.
+// Per-axis propagator h[k] = exp(-i pi alpha m^2) / n, m the signed
+// frequency of bin k (the 1-D factor of the transfer function of eq.
+// limit_of_operators_renorm_final; the 1/n carries the inverse transform's
+// normalisation for that axis).  alpha*m^2 is split into a rounded product
+// and its exact FMA residual, the product is reduced modulo 2 exactly
+// (fmod), and sincospi evaluates exp(-i pi t) on the reduced argument, so
+// phases of thousands of radians keep full FP64 accuracy.
 template <typename V>
-__global__ void k_tables(int n, double alpha, V *tw, V *h)
+__global__ void k_prop_table(int n, double alpha, V *h)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    double s, c;
-    sincospi(2.0 * (double)k / (double)n, &s, &c);
-    tw[k] = cmk<V>(c, -s);
     const long long m = k < n / 2 ? k : (long long)k - n;
     const double m2 = (double)(m * m);
     const double hi = alpha * m2;
@@ -35,6 +31,41 @@ __global__ void k_tables(int n, double alpha, V *tw, V *h)
     sincospi(t, &sp, &cp);
     const double inv = 1.0 / (double)n;
     h[k] = cmk<V>(cp * inv, -sp * inv);
+}
+
+// Pass-major twiddle table of the line FFT of length 2^logn (layout in
+// fft_core.cuh): for each pass after the first, with span Ns and radix R,
+// entry (r-1)*Ns + j holds exp(-2 pi i r j / (Ns R)).  FP64 sincospi on the
+// exact rational argument 2 r j / (Ns R).
+template <typename V>
+__global__ void k_twiddles(int logn, int total, V *tw)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int p16 = logn / 4, lastlog = logn % 4;
+    int base = 0, Ns = 16;
+    int R = 16;
+    for (int p = 1;; ++p) {
+        const bool trailing = p >= p16;
+        R = trailing ? (1 << lastlog) : 16;
+        const int size = (R - 1) * Ns;
+        if (e < base + size) break;
+        base += size;
+        Ns *= 16;
+    }
+    const int local = e - base;
+    const int r = local / Ns + 1, j = local % Ns;
+    double s, c;
+    sincospi(2.0 * (double)((long long)r * j) / ((double)Ns * R), &s, &c);
+    tw[e] = cmk<V>(c, -s);
+}
+
+__host__ __device__ inline int twiddle_count(int logn)
+{
+    int s = 0, Ns = 16;
+    for (int p = 1; p < logn / 4; ++p, Ns *= 16) s += 15 * Ns;
+    if (logn % 4) s += ((1 << (logn % 4)) - 1) * Ns;
+    return s;
 }
 
 // splitmix64 (Steele, Lea & Flood 2014) as a counter-based stream: output c

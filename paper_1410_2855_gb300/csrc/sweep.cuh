@@ -21,33 +21,42 @@ namespace rtk {
 
 enum SweepMode { MODE_FWD = 0, MODE_INV = 1, MODE_DIFF = 2, MODE_DIFF_GAIN = 3 };
 
+// Pump evaluation inside the row sweep: super-Gaussian of order 10 computed
+// on the fly, uniform, or a precomputed N0 table (array pumps and any other
+// super-Gaussian order).
+enum PumpEval { PE_SG10 = 0, PE_UNIFORM = 1, PE_TABLE = 2 };
+
 // Lines per block of a row sweep: about 256 threads.
 template <int LOGN> constexpr int row_lpc()
 {
     return Plan<LOGN>::T >= 256 ? 1 : ((256 / Plan<LOGN>::T) > (1 << LOGN) ? (1 << LOGN) : 256 / Plan<LOGN>::T);
 }
+// Register budget per thread of the sweeps (build-time knob); the launch
+// bounds ask the compiler for as many resident blocks as that budget allows.
+#ifndef RTK_REGS
+#define RTK_REGS 128
+#endif
+constexpr int min_blocks(int threads)
+{
+    return 65536 / (threads * RTK_REGS) > 0 ? 65536 / (threads * RTK_REGS) : 1;
+}
 
-__device__ __forceinline__ float rexp(float x) { return expf(x); }
-__device__ __forceinline__ double rexp(double x) { return exp(x); }
-__device__ __forceinline__ float rpow(float x, float y) { return powf(x, y); }
-__device__ __forceinline__ double rpow(double x, double y) { return pow(x, y); }
+// exp for the FP32 local map: ex2.approx of a prescaled argument (relative
+// error ~2e-7 for the small arguments here); FP64 keeps the library exp.
+__device__ __forceinline__ float fexp(float x) { return __expf(x); }
+__device__ __forceinline__ double fexp(double x) { return exp(x); }
+__device__ __forceinline__ double dpow(double x, double y) { return pow(x, y); }
 
-// Unsaturated inversion N0 at pixel (x, y); yc2 = y-coordinate squared.
+// Unsaturated inversion N0 for the plain FP64 gain kernel (runtime pump kind).
 template <typename R>
 __device__ __forceinline__ R pump_value(const GainParams<R> &g, int x, int y, int n, R yc2)
 {
     if (g.pump_kind == PUMP_UNIFORM) return g.g0;
-    if (g.pump_kind == PUMP_ARRAY) return __ldg(g.pump_tab + (size_t)y * n + x);
+    if (g.pump_kind == PUMP_ARRAY || g.int_half_order != 5) return __ldg(g.pump_tab + (size_t)y * n + x);
     const R xc = R(x - n / 2) * (R(2) / R(n));
     const R q = (xc * xc + yc2) * g.inv_rp2;
-    R qp;
-    if (g.int_half_order > 0) {
-        qp = q;
-        for (int i = 1; i < g.int_half_order; ++i) qp *= q;
-    } else {
-        qp = q > R(0) ? rpow(q, g.half_order) : R(0);
-    }
-    return g.g0 * rexp(-qp);
+    const R q2 = q * q;
+    return g.g0 * fexp(-(q2 * q2 * q));
 }
 
 // Block sum of v, then the last block to arrive sums the block partials in a
@@ -95,8 +104,8 @@ __device__ __forceinline__ void finish_mean(double v, const StatParams &st, doub
 
 // Row sweep.  Each group of T threads owns one row.  `in` and `out` may alias
 // (in-place): a block reads all its rows before it writes any.
-template <typename R, int LOGN, int MODE>
-__global__ void __launch_bounds__(row_lpc<LOGN>() * Plan<LOGN>::T)
+template <typename R, int LOGN, int MODE, int PE>
+__global__ void __launch_bounds__(row_lpc<LOGN>() * Plan<LOGN>::T, min_blocks(row_lpc<LOGN>() * Plan<LOGN>::T))
 k_row(const cv<R> *in, cv<R> *out, R *__restrict__ Nv, const cv<R> *__restrict__ tw,
       const cv<R> *__restrict__ h, GainParams<R> g, StatParams st)
 {
@@ -104,55 +113,63 @@ k_row(const cv<R> *in, cv<R> *out, R *__restrict__ Nv, const cv<R> *__restrict__
     using P = Plan<LOGN>;
     constexpr int N = P::N, T = P::T, LPC = row_lpc<LOGN>(), NT = LPC * T, LS = padded_len(N);
     extern __shared__ __align__(16) unsigned char smraw[];
-    V *S = reinterpret_cast<V *>(smraw) + (threadIdx.x / T) * LS;
+    V *line = reinterpret_cast<V *>(smraw) + (threadIdx.x / T) * LS;
     const int t = threadIdx.x % T;
     const int row = blockIdx.x * LPC + threadIdx.x / T;
-    auto smem = [S](int i) -> V & { return S[padi(i)]; };
     auto sync = []() { __syncthreads(); };
 
-    const V *src = in + (size_t)row * N;
+    const V *src = in + (size_t)row * N + t;
     V v[16];
 #pragma unroll
-    for (int s = 0; s < 16; ++s) v[s] = src[t + s * T];
+    for (int s = 0; s < 16; ++s) v[s] = src[s * T];
 
     if constexpr (MODE == MODE_INV) {
-        fft_line<LOGN, +1>(v, t, smem, tw, sync);
+        fft_line<LOGN, +1, 1>(v, t, line, tw, sync);
     } else {
-        fft_line<LOGN, -1>(v, t, smem, tw, sync);
+        fft_line<LOGN, -1, 1>(v, t, line, tw, sync);
     }
     if constexpr (MODE >= MODE_DIFF) {
+        const V *hp = h + t;
 #pragma unroll
-        for (int s = 0; s < 16; ++s) v[s] = cmul(v[s], __ldg(h + t + s * T));
-        fft_line<LOGN, +1>(v, t, smem, tw, sync);
+        for (int s = 0; s < 16; ++s) v[s] = cmul(v[s], __ldg(hp + s * T));
+        fft_line<LOGN, +1, 1>(v, t, line, tw, sync);
     }
+    V *dst = out + (size_t)row * N + t;
     if constexpr (MODE == MODE_DIFF_GAIN) {
-        const R yc = R(row - N / 2) * (R(2) / R(N));
-        const R yc2 = yc * yc;
+        const R step = R(2) / R(N);
+        const R yc = R(row - N / 2) * step;
+        const R yq = yc * yc * g.inv_rp2;
+        const R xc0 = R(t - N / 2) * step;
         const bool row_in = row >= g.edge && row < N - g.edge;
-        R *Nrow = Nv + (size_t)row * N;
+        R *Nrow = Nv + (size_t)row * N + t;
         R acc = R(0);
 #pragma unroll
         for (int s = 0; s < 16; ++s) {
             const int x = t + s * T;
-            const R nn = Nrow[x];
+            const R nn = Nrow[s * T];
             V e = v[s];
             const R inten = e.x * e.x + e.y * e.y;
             const bool inside = row_in && x >= g.edge && x < N - g.edge;
-            const R gain = inside ? g.sqrtR * rexp(R(0.5) * nn) : R(0);
-            e = cscale(e, gain);
-            const R n0 = pump_value(g, x, row, N, yc2);
-            Nrow[x] = nn + (n0 - nn * (R(1) + inten * g.invIsat)) * g.invT1;
-            v[s] = e;
+            e = cscale(e, inside ? g.sqrtR * fexp(R(0.5) * nn) : R(0));
+            R n0;
+            if constexpr (PE == PE_UNIFORM) {
+                n0 = g.g0;
+            } else if constexpr (PE == PE_TABLE) {
+                n0 = __ldg(g.pump_tab + (size_t)row * N + x);
+            } else {
+                const R xc = xc0 + R(s * T) * step;
+                const R q = xc * xc * g.inv_rp2 + yq;
+                const R q2 = q * q;
+                n0 = g.g0 * fexp(-(q2 * q2 * q));
+            }
+            Nrow[s * T] = nn + (n0 - nn * (R(1) + inten * g.invIsat)) * g.invT1;
+            dst[s * T] = e;
             acc += e.x * e.x + e.y * e.y;
         }
-        V *dst = out + (size_t)row * N;
-#pragma unroll
-        for (int s = 0; s < 16; ++s) dst[t + s * T] = v[s];
         finish_mean<NT>((double)acc, st, 1.0 / ((double)N * (double)N));
     } else {
-        V *dst = out + (size_t)row * N;
 #pragma unroll
-        for (int s = 0; s < 16; ++s) dst[t + s * T] = v[s];
+        for (int s = 0; s < 16; ++s) dst[s * T] = v[s];
     }
 }
 
@@ -160,34 +177,34 @@ k_row(const cv<R> *in, cv<R> *out, R *__restrict__ Nv, const cv<R> *__restrict__
 // fast index, so a warp reads C*sizeof(V) contiguous bytes from each of
 // 32/C rows.  Shared layout [padded row][c].  In place.
 template <typename R, int LOGN, int C, int MODE>
-__global__ void __launch_bounds__(C * Plan<LOGN>::T)
+__global__ void __launch_bounds__(C * Plan<LOGN>::T, min_blocks(C * Plan<LOGN>::T))
 k_col(cv<R> *X, const cv<R> *__restrict__ tw, const cv<R> *__restrict__ h)
 {
     using V = cv<R>;
     using P = Plan<LOGN>;
     constexpr int N = P::N, T = P::T;
     extern __shared__ __align__(16) unsigned char smraw[];
-    V *sm = reinterpret_cast<V *>(smraw);
     const int c = threadIdx.x % C, t = threadIdx.x / C;
-    const int col = blockIdx.x * C + c;
-    auto smem = [sm, c](int i) -> V & { return sm[padi(i) * C + c]; };
+    V *line = reinterpret_cast<V *>(smraw) + c;
     auto sync = []() { __syncthreads(); };
+    V *col = X + (size_t)t * N + blockIdx.x * C + c;
 
     V v[16];
 #pragma unroll
-    for (int s = 0; s < 16; ++s) v[s] = X[(size_t)(t + s * T) * N + col];
+    for (int s = 0; s < 16; ++s) v[s] = col[(size_t)s * T * N];
     if constexpr (MODE == MODE_INV) {
-        fft_line<LOGN, +1>(v, t, smem, tw, sync);
+        fft_line<LOGN, +1, C>(v, t, line, tw, sync);
     } else {
-        fft_line<LOGN, -1>(v, t, smem, tw, sync);
+        fft_line<LOGN, -1, C>(v, t, line, tw, sync);
     }
     if constexpr (MODE >= MODE_DIFF) {
+        const V *hp = h + t;
 #pragma unroll
-        for (int s = 0; s < 16; ++s) v[s] = cmul(v[s], __ldg(h + t + s * T));
-        fft_line<LOGN, +1>(v, t, smem, tw, sync);
+        for (int s = 0; s < 16; ++s) v[s] = cmul(v[s], __ldg(hp + s * T));
+        fft_line<LOGN, +1, C>(v, t, line, tw, sync);
     }
 #pragma unroll
-    for (int s = 0; s < 16; ++s) X[(size_t)(t + s * T) * N + col] = v[s];
+    for (int s = 0; s < 16; ++s) col[(size_t)s * T * N] = v[s];
 }
 
 template <typename R, int LOGN> constexpr size_t row_smem_bytes()
@@ -215,11 +232,11 @@ inline cudaError_t ensure_smem(K kernel, size_t bytes, std::atomic<unsigned long
     return e;
 }
 
-template <typename R, int LOGN, int MODE>
+template <typename R, int LOGN, int MODE, int PE = PE_SG10>
 inline cudaError_t row_attr()
 {
     static std::atomic<unsigned long long> mask{0};
-    return ensure_smem(k_row<R, LOGN, MODE>, row_smem_bytes<R, LOGN>(), mask);
+    return ensure_smem(k_row<R, LOGN, MODE, PE>, row_smem_bytes<R, LOGN>(), mask);
 }
 
 template <typename R, int LOGN, int C, int MODE>

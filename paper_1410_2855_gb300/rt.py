@@ -13,7 +13,7 @@ import platform
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_lib", f"libbouncemap_{platform.machine()}.so")
+LIB_PATH = os.environ.get("RT_LIBRARY") or os.path.join(HERE, "_lib", f"libbouncemap_{platform.machine()}.so")
 
 RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENUMERIC, RT_ETIMEOUT, RT_EBUSY = 0, -1, -2, -3, -4, -5, -6
 RT_PUMP_SUPERGAUSS, RT_PUMP_UNIFORM, RT_PUMP_ARRAY = 0, 1, 2
@@ -35,7 +35,7 @@ class rt_opts(ctypes.Structure):
     _fields_ = [("Isat", ctypes.c_double), ("edge_px", ctypes.c_int), ("precision", ctypes.c_int),
                 ("seed", ctypes.c_ulonglong), ("noise_amp", ctypes.c_double),
                 ("pump_diam_over_window", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
-                ("history_cap", ctypes.c_longlong), ("chunk", ctypes.c_int)]
+                ("history_cap", ctypes.c_longlong), ("chunk", ctypes.c_int), ("col_tile", ctypes.c_int)]
 
 
 class rt_stats_t(ctypes.Structure):
