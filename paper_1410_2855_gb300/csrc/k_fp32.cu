@@ -1,7 +1,15 @@
 // FP32 fused path: launchers and instantiations of the two bounce sweeps and
 // of the FP32 set-up and spectrum kernels.
+#include <cudaTypedefs.h>
+
 #include "setup_kernels.cuh"
 #include "sweep.cuh"
+#include "sweep_tma.cuh"
+
+// 1: persistent copy-engine-fed sweeps (default); 0: one block per line group.
+#ifndef RTK_PERSISTENT
+#define RTK_PERSISTENT 1
+#endif
 
 namespace rtk {
 
@@ -23,13 +31,92 @@ template <int LOGN, int C> constexpr bool col_fits32()
     return C <= (1 << LOGN) && C * Plan<LOGN>::T <= 1024 && col_smem_bytes<float, LOGN, C>() <= 227 * 1024;
 }
 
+// ---- persistent launch geometry -------------------------------------------------
+
+static int sm_count()
+{
+    static std::atomic<int> cached{0};
+    int v = cached.load();
+    if (v > 0) return v;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+    cached.store(v);
+    return v;
+}
+
+// Blocks of a persistent launch: resident blocks per SM x SMs, capped by the work.
+template <typename K>
+static int persistent_grid(K kernel, int threads, size_t smem, int work, std::atomic<int> &per_sm)
+{
+    int b = per_sm.load();
+    if (b <= 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, smem) != cudaSuccess || b <= 0) b = 1;
+        per_sm.store(b);
+    }
+    const int g = b * sm_count();
+    return g < work ? g : work;
+}
+
+template <int LOGN> constexpr int tma_lpc() { return Plan<LOGN>::T >= 64 ? 1 : 64 / Plan<LOGN>::T; }
+
+template <int LOGN, int C> constexpr bool col_tma_fits()
+{
+    return col_fits32<LOGN, C>() && C >= 2 && ColStage<LOGN, C>::total <= 227 * 1024;
+}
+
+// Tensor map over the complex64 field viewed as an n x 2n float matrix; one
+// box is BR rows x C complex columns (2C floats, >= 16 bytes for C >= 2).
+cudaError_t make_col_tensor_map(void *map, float2 *E, int n, int colC)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)2 * n, (cuuint64_t)n};
+    const cuuint64_t strides[1] = {(cuuint64_t)2 * n * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)(2 * colC), (cuuint32_t)(n < 256 ? n : 256)};
+    const cuuint32_t es[2] = {1, 1};
+    CUresult r = encode(static_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, E, dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 // ---- column sweep ---------------------------------------------------------------
 
 template <int LOGN, int C>
-static cudaError_t col_diff32_c(float2 *E, const float2 *tw, const float2 *h, cudaStream_t s)
+static cudaError_t col_tma32_c(float2 *E, const float2 *tw, const float2 *h, const void *tmap, int *err,
+                               cudaStream_t s)
+{
+    if constexpr (!col_tma_fits<LOGN, C>()) {
+        return cudaErrorInvalidValue;
+    } else {
+        using L = ColStage<LOGN, C>;
+        auto k = k_col_tma<LOGN, C>;
+        static std::atomic<unsigned long long> mask{0};
+        static std::atomic<int> per_sm{0};
+        cudaError_t e = ensure_smem(k, L::total, mask);
+        if (e != cudaSuccess) return e;
+        const int ntiles = (1 << LOGN) / C;
+        const int grid = persistent_grid(k, C * Plan<LOGN>::T, L::total, ntiles, per_sm);
+        k<<<grid, C * Plan<LOGN>::T, L::total, s>>>(E, tw, h, *static_cast<const CUtensorMap *>(tmap), ntiles, err);
+        return cudaGetLastError();
+    }
+}
+
+template <int LOGN, int C>
+static cudaError_t col_diff32_c(float2 *E, const float2 *tw, const float2 *h, const void *tmap, int *err,
+                                cudaStream_t s)
 {
     if constexpr (!col_fits32<LOGN, C>()) {
         return cudaErrorInvalidValue;
+    } else if constexpr (RTK_PERSISTENT && col_tma_fits<LOGN, C>()) {
+        return col_tma32_c<LOGN, C>(E, tw, h, tmap, err, s);
     } else {
         cudaError_t e = col_attr<float, LOGN, C, MODE_DIFF>();
         if (e != cudaSuccess) return e;
@@ -40,20 +127,22 @@ static cudaError_t col_diff32_c(float2 *E, const float2 *tw, const float2 *h, cu
 }
 
 template <int LOGN>
-static cudaError_t col_diff32(int colC, float2 *E, const float2 *tw, const float2 *h, cudaStream_t s)
+static cudaError_t col_diff32(int colC, float2 *E, const float2 *tw, const float2 *h, const void *tmap, int *err,
+                              cudaStream_t s)
 {
     switch (colC) {
-    case 2: return col_diff32_c<LOGN, 2>(E, tw, h, s);
-    case 4: return col_diff32_c<LOGN, 4>(E, tw, h, s);
-    case 8: return col_diff32_c<LOGN, 8>(E, tw, h, s);
-    case 16: return col_diff32_c<LOGN, 16>(E, tw, h, s);
+    case 2: return col_diff32_c<LOGN, 2>(E, tw, h, tmap, err, s);
+    case 4: return col_diff32_c<LOGN, 4>(E, tw, h, tmap, err, s);
+    case 8: return col_diff32_c<LOGN, 8>(E, tw, h, tmap, err, s);
+    case 16: return col_diff32_c<LOGN, 16>(E, tw, h, tmap, err, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_col_diffract32(int logn, int colC, float2 *E, const float2 *tw, const float2 *h, cudaStream_t s)
+cudaError_t launch_col_diffract32(int logn, int colC, float2 *E, const float2 *tw, const float2 *h, const void *tmap,
+                                  int *err, cudaStream_t s)
 {
-    RTK_LOGN_CASES(col_diff32, colC, E, tw, h, s)
+    RTK_LOGN_CASES(col_diff32, colC, E, tw, h, tmap, err, s)
 }
 
 template <int LOGN> static int col_ok32(int colC)
@@ -72,9 +161,27 @@ int col_tile_ok32(int logn, int colC) { RTK_LOGN_CASES(col_ok32, colC) }
 // ---- row sweep (diffraction along x + local map) --------------------------------
 
 template <int LOGN, int PE>
+static cudaError_t row_tma32_pe(float2 *E, float *N, const float2 *tw, const float2 *h, const GainParams<float> &g,
+                                const StatParams &st, cudaStream_t s)
+{
+    constexpr int LPC = tma_lpc<LOGN>();
+    using L = RowStage<LOGN, LPC>;
+    auto k = k_row_tma<LOGN, LPC, PE>;
+    static std::atomic<unsigned long long> mask{0};
+    static std::atomic<int> per_sm{0};
+    cudaError_t e = ensure_smem(k, L::total, mask);
+    if (e != cudaSuccess) return e;
+    const int ngroups = (1 << LOGN) / LPC;
+    const int grid = persistent_grid(k, LPC * Plan<LOGN>::T, L::total, ngroups, per_sm);
+    k<<<grid, LPC * Plan<LOGN>::T, L::total, s>>>(E, N, tw, h, g, st, ngroups);
+    return cudaGetLastError();
+}
+
+template <int LOGN, int PE>
 static cudaError_t row_dg32_pe(float2 *E, float *N, const float2 *tw, const float2 *h, const GainParams<float> &g,
                                const StatParams &st, cudaStream_t s)
 {
+    if constexpr (RTK_PERSISTENT) return row_tma32_pe<LOGN, PE>(E, N, tw, h, g, st, s);
     cudaError_t e = row_attr<float, LOGN, MODE_DIFF_GAIN, PE>();
     if (e != cudaSuccess) return e;
     constexpr int LPC = row_lpc<LOGN>();
@@ -159,17 +266,33 @@ cudaError_t launch_col_fft32(int logn, float2 *X, const float2 *tw, int dir, cud
 
 template <int LOGN, int C> static cudaError_t col_prep32_c()
 {
-    if constexpr (!col_fits32<LOGN, C>()) return cudaErrorInvalidValue;
-    else return col_attr<float, LOGN, C, MODE_DIFF>();
+    if constexpr (!col_fits32<LOGN, C>()) {
+        return cudaErrorInvalidValue;
+    } else if constexpr (RTK_PERSISTENT && col_tma_fits<LOGN, C>()) {
+        static std::atomic<unsigned long long> mask{0};
+        return ensure_smem(k_col_tma<LOGN, C>, ColStage<LOGN, C>::total, mask);
+    } else {
+        return col_attr<float, LOGN, C, MODE_DIFF>();
+    }
+}
+
+template <int LOGN, int PE> static cudaError_t row_prep32()
+{
+    if constexpr (RTK_PERSISTENT) {
+        static std::atomic<unsigned long long> mask{0};
+        return ensure_smem(k_row_tma<LOGN, tma_lpc<LOGN>(), PE>, RowStage<LOGN, tma_lpc<LOGN>()>::total, mask);
+    } else {
+        return row_attr<float, LOGN, MODE_DIFF_GAIN, PE>();
+    }
 }
 
 template <int LOGN> static cudaError_t prep32(int colC, int pe)
 {
     cudaError_t e;
     switch (pe) {
-    case PE_SG10: e = row_attr<float, LOGN, MODE_DIFF_GAIN, PE_SG10>(); break;
-    case PE_UNIFORM: e = row_attr<float, LOGN, MODE_DIFF_GAIN, PE_UNIFORM>(); break;
-    case PE_TABLE: e = row_attr<float, LOGN, MODE_DIFF_GAIN, PE_TABLE>(); break;
+    case PE_SG10: e = row_prep32<LOGN, PE_SG10>(); break;
+    case PE_UNIFORM: e = row_prep32<LOGN, PE_UNIFORM>(); break;
+    case PE_TABLE: e = row_prep32<LOGN, PE_TABLE>(); break;
     default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;

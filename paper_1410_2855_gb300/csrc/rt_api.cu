@@ -82,6 +82,7 @@ struct rt_handle {
     long long bounces = 0;
     int colC = 4;
     int pe = 0;                   // pump evaluation of the FP32 row sweep (PumpEval)
+    alignas(64) unsigned char tmap[128] = {};  // tensor map of E for the column sweep's tile loads
     std::map<long long, cudaGraphExec_t> graphs;
     size_t esz() const { return precision == RT_FP64 ? 16 : 8; }
     size_t rsz() const { return precision == RT_FP64 ? 8 : 4; }
@@ -137,7 +138,7 @@ cudaError_t enqueue_bounce(rt_handle *h, cudaStream_t s)
     if (h->precision == RT_FP32) {
         float2 *E = static_cast<float2 *>(h->E);
         const float2 *tw = static_cast<const float2 *>(h->tw), *hh = static_cast<const float2 *>(h->h);
-        cudaError_t e = launch_col_diffract32(h->logn, h->colC, E, tw, hh, s);
+        cudaError_t e = launch_col_diffract32(h->logn, h->colC, E, tw, hh, h->tmap, &h->ctl->err, s);
         if (e != cudaSuccess) return e;
         return launch_row_diffract_gain32(h->logn, h->pe, E, static_cast<float *>(h->N), tw, hh, gain_params<float>(h), st,
                                           s);
@@ -339,6 +340,7 @@ rt_status rt_create(int n, double fresnel, const rt_pump *pump, double g0, doubl
 
     if (h->precision == RT_FP32) {
         RT_CREATE_TRY(launch_tables32(n, h->alpha, static_cast<float2 *>(h->tw), static_cast<float2 *>(h->h), h->stream));
+        RT_CREATE_TRY(make_col_tensor_map(h->tmap, static_cast<float2 *>(h->E), n, h->colC));
         RT_CREATE_TRY(launch_noise32(n, o.seed, o.noise_amp, static_cast<float2 *>(h->E), h->stream));
         RT_CREATE_TRY(launch_pump32(n, p.kind, g0, p.order, p.radius, h->profile, static_cast<float *>(h->N), h->stream));
         if (h->pe == 2) {
@@ -384,7 +386,7 @@ rt_status rt_sweep(rt_handle *h, int which)
     float2 *E = static_cast<float2 *>(h->E);
     const float2 *tw = static_cast<const float2 *>(h->tw), *hh = static_cast<const float2 *>(h->h);
     if (which == RT_SWEEP_COLUMNS) {
-        RT_TRY(launch_col_diffract32(h->logn, h->colC, E, tw, hh, h->stream));
+        RT_TRY(launch_col_diffract32(h->logn, h->colC, E, tw, hh, h->tmap, &h->ctl->err, h->stream));
     } else {
         RT_TRY(launch_row_diffract_gain32(h->logn, h->pe, E, static_cast<float *>(h->N), tw, hh, gain_params<float>(h),
                                           stat_params(h), h->stream));

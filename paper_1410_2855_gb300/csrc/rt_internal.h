@@ -41,8 +41,13 @@ struct PeakResult {
 
 // ---- FP32 fused path: two sweeps per bounce --------------------------------
 // Column sweep: per column, forward FFT, x h(my), inverse FFT (in place).
-cudaError_t launch_col_diffract32(int logn, int colC, float2 *E, const float2 *tw, const float2 *h,
-                                  cudaStream_t s);
+// tmap: the field's column-tile tensor map (make_col_tensor_map); err: the
+// handle's sticky error word (set to RT_ETIMEOUT if a copy wait runs out).
+cudaError_t launch_col_diffract32(int logn, int colC, float2 *E, const float2 *tw, const float2 *h, const void *tmap,
+                                  int *err, cudaStream_t s);
+// Encode the 128-byte tensor map of an n x n complex64 field for column
+// tiles of colC columns (copy-engine loads of the column sweep).
+cudaError_t make_col_tensor_map(void *map, float2 *E, int n, int colC);
 // Row sweep: per row, forward FFT, x h(mx), inverse FFT, then the local map
 // (gain, mirror, edge, inversion update) and the mean-intensity reduction.
 // pe selects how N0 is evaluated: 0 super-Gaussian of order 10 on the fly,
