@@ -138,27 +138,46 @@ __device__ __forceinline__ V twmul(V a, const V *__restrict__ tw, int k)
 // for the [row][column] tile of the column sweep).
 template <int CS, typename V> __device__ __forceinline__ V &sm_at(V *line, int i) { return line[padi(i) * CS]; }
 
+// Exchange buffers of a line FFT.  With one buffer every exchange is
+// barrier, write, barrier, read.  With two (ping-pong) an exchange is write,
+// barrier, read into the buffer not used by the previous exchange: a thread
+// can only write a buffer again after passing the barrier of the exchange in
+// between, by which time every thread has finished reading it, so one
+// barrier per exchange suffices.  `next` selects the buffer of the next
+// exchange and carries across calls (forward then inverse transform).
+template <typename V, bool PP> struct LineBufs {
+    V *buf[2];
+    int next;
+    __device__ __forceinline__ V *take()
+    {
+        V *b = buf[PP ? next : 0];
+        if (PP) next ^= 1;
+        return b;
+    }
+};
+
 // One Stockham FFT of a line.  On entry v[s] = x[t + T s]; on exit
 // v[s] = X[t + T s], X[k] = sum_j x[j] exp(DIR 2 pi i jk / N) (unnormalised).
-// `line` is this line's padded shared buffer (element stride CS); sync() is a
-// barrier over every thread that shares the buffer.  Each exchange is
-// barrier, write, barrier, read.  Shared addresses are a per-thread base plus
-// compile-time offsets: spans and T are multiples of 16 wherever the pad
-// arithmetic allows it.
-template <int LOGN, int DIR, int CS, typename V, typename SyncF>
-__device__ __forceinline__ void fft_line(V (&v)[16], const int t, V *line, const V *__restrict__ tw, SyncF sync)
+// `lb` holds this line's padded shared buffer(s) (element stride CS); sync()
+// is a barrier over every thread that shares them.  Shared addresses are a
+// per-thread base plus compile-time offsets: spans and T are multiples of 16
+// wherever the pad arithmetic allows it.
+template <int LOGN, int DIR, int CS, bool PP, typename V, typename SyncF>
+__device__ __forceinline__ void fft_line(V (&v)[16], const int t, LineBufs<V, PP> &lb, const V *__restrict__ tw,
+                                         SyncF sync)
 {
     using P = Plan<LOGN>;
     constexpr int N = P::N, T = P::T;
     constexpr bool T16 = (T % 16) == 0;
-    V *rd_base = line + padi(t) * CS;  // element t of the line (valid base when T16)
     dft<16, DIR>(v);
     int off = 0;
 #pragma unroll
     for (int p = 1; p < P::P16; ++p) {
         const int NsPrev = 1 << (4 * (p - 1));
         const int Ns = NsPrev * 16;
-        sync();
+        V *line = lb.take();
+        V *rd_base = line + padi(t) * CS;
+        if (!PP) sync();
         if (NsPrev == 1) {
             V *w = line + 17 * t * CS;
 #pragma unroll
@@ -186,7 +205,9 @@ __device__ __forceinline__ void fft_line(V (&v)[16], const int t, V *line, const
     if constexpr (P::LASTLOG > 0) {
         constexpr int RL = P::LASTR, NB = 16 / RL, NsL = N / RL;
         constexpr int NsPrev = NsL / 16;
-        sync();
+        V *line = lb.take();
+        V *rd_base = line + padi(t) * CS;
+        if (!PP) sync();
         if constexpr (NsPrev == 1) {
             V *w = line + 17 * t * CS;
 #pragma unroll

@@ -62,7 +62,7 @@ template <int LOGN> constexpr int tma_lpc() { return Plan<LOGN>::T >= 64 ? 1 : 6
 
 template <int LOGN, int C> constexpr bool col_tma_fits()
 {
-    return col_fits32<LOGN, C>() && C >= 2 && ColStage<LOGN, C>::total <= 227 * 1024;
+    return col_fits32<LOGN, C>() && C >= 2 && ColStage<LOGN, C, RTK_COL_PP>::total <= 227 * 1024;
 }
 
 // Tensor map over the complex64 field viewed as an n x 2n float matrix; one
@@ -96,7 +96,7 @@ static cudaError_t col_tma32_c(float2 *E, const float2 *tw, const float2 *h, con
     if constexpr (!col_tma_fits<LOGN, C>()) {
         return cudaErrorInvalidValue;
     } else {
-        using L = ColStage<LOGN, C>;
+        using L = ColStage<LOGN, C, RTK_COL_PP>;
         auto k = k_col_tma<LOGN, C>;
         static std::atomic<unsigned long long> mask{0};
         static std::atomic<int> per_sm{0};
@@ -165,7 +165,7 @@ static cudaError_t row_tma32_pe(float2 *E, float *N, const float2 *tw, const flo
                                 const StatParams &st, cudaStream_t s)
 {
     constexpr int LPC = tma_lpc<LOGN>();
-    using L = RowStage<LOGN, LPC>;
+    using L = RowStage<LOGN, LPC, RTK_ROW_PP>;
     auto k = k_row_tma<LOGN, LPC, PE>;
     static std::atomic<unsigned long long> mask{0};
     static std::atomic<int> per_sm{0};
@@ -270,7 +270,7 @@ template <int LOGN, int C> static cudaError_t col_prep32_c()
         return cudaErrorInvalidValue;
     } else if constexpr (RTK_PERSISTENT && col_tma_fits<LOGN, C>()) {
         static std::atomic<unsigned long long> mask{0};
-        return ensure_smem(k_col_tma<LOGN, C>, ColStage<LOGN, C>::total, mask);
+        return ensure_smem(k_col_tma<LOGN, C>, ColStage<LOGN, C, RTK_COL_PP>::total, mask);
     } else {
         return col_attr<float, LOGN, C, MODE_DIFF>();
     }
@@ -280,7 +280,7 @@ template <int LOGN, int PE> static cudaError_t row_prep32()
 {
     if constexpr (RTK_PERSISTENT) {
         static std::atomic<unsigned long long> mask{0};
-        return ensure_smem(k_row_tma<LOGN, tma_lpc<LOGN>(), PE>, RowStage<LOGN, tma_lpc<LOGN>()>::total, mask);
+        return ensure_smem(k_row_tma<LOGN, tma_lpc<LOGN>(), PE>, RowStage<LOGN, tma_lpc<LOGN>(), RTK_ROW_PP>::total, mask);
     } else {
         return row_attr<float, LOGN, MODE_DIFF_GAIN, PE>();
     }

@@ -8,7 +8,7 @@
 #include <map>
 #include <new>
 
-#include "../../include/rt.h"
+#include "rt.h"
 #include "rt_internal.h"
 
 using namespace rtk;

@@ -117,6 +117,7 @@ k_row(const cv<R> *in, cv<R> *out, R *__restrict__ Nv, const cv<R> *__restrict__
     const int t = threadIdx.x % T;
     const int row = blockIdx.x * LPC + threadIdx.x / T;
     auto sync = []() { __syncthreads(); };
+    LineBufs<V, false> lb{{line, line}, 0};
 
     const V *src = in + (size_t)row * N + t;
     V v[16];
@@ -124,15 +125,15 @@ k_row(const cv<R> *in, cv<R> *out, R *__restrict__ Nv, const cv<R> *__restrict__
     for (int s = 0; s < 16; ++s) v[s] = src[s * T];
 
     if constexpr (MODE == MODE_INV) {
-        fft_line<LOGN, +1, 1>(v, t, line, tw, sync);
+        fft_line<LOGN, +1, 1>(v, t, lb, tw, sync);
     } else {
-        fft_line<LOGN, -1, 1>(v, t, line, tw, sync);
+        fft_line<LOGN, -1, 1>(v, t, lb, tw, sync);
     }
     if constexpr (MODE >= MODE_DIFF) {
         const V *hp = h + t;
 #pragma unroll
         for (int s = 0; s < 16; ++s) v[s] = cmul(v[s], __ldg(hp + s * T));
-        fft_line<LOGN, +1, 1>(v, t, line, tw, sync);
+        fft_line<LOGN, +1, 1>(v, t, lb, tw, sync);
     }
     V *dst = out + (size_t)row * N + t;
     if constexpr (MODE == MODE_DIFF_GAIN) {
@@ -187,21 +188,22 @@ k_col(cv<R> *X, const cv<R> *__restrict__ tw, const cv<R> *__restrict__ h)
     const int c = threadIdx.x % C, t = threadIdx.x / C;
     V *line = reinterpret_cast<V *>(smraw) + c;
     auto sync = []() { __syncthreads(); };
+    LineBufs<V, false> lb{{line, line}, 0};
     V *col = X + (size_t)t * N + blockIdx.x * C + c;
 
     V v[16];
 #pragma unroll
     for (int s = 0; s < 16; ++s) v[s] = col[(size_t)s * T * N];
     if constexpr (MODE == MODE_INV) {
-        fft_line<LOGN, +1, C>(v, t, line, tw, sync);
+        fft_line<LOGN, +1, C>(v, t, lb, tw, sync);
     } else {
-        fft_line<LOGN, -1, C>(v, t, line, tw, sync);
+        fft_line<LOGN, -1, C>(v, t, lb, tw, sync);
     }
     if constexpr (MODE >= MODE_DIFF) {
         const V *hp = h + t;
 #pragma unroll
         for (int s = 0; s < 16; ++s) v[s] = cmul(v[s], __ldg(hp + s * T));
-        fft_line<LOGN, +1, C>(v, t, line, tw, sync);
+        fft_line<LOGN, +1, C>(v, t, lb, tw, sync);
     }
 #pragma unroll
     for (int s = 0; s < 16; ++s) col[(size_t)s * T * N] = v[s];

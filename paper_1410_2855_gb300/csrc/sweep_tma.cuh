@@ -21,20 +21,30 @@ namespace rtk {
 
 constexpr int ERR_TIMEOUT = -5;
 
-template <int LOGN, int LPC> struct RowStage {
+// Ping-pong exchange buffers in the persistent sweeps (one barrier per
+// exchange instead of two, for one more padded line buffer per line).
+#ifndef RTK_ROW_PP
+#define RTK_ROW_PP 0
+#endif
+#ifndef RTK_COL_PP
+#define RTK_COL_PP 1
+#endif
+
+template <int LOGN, int LPC, bool PP> struct RowStage {
     static constexpr int N = 1 << LOGN;
     static constexpr size_t e_bytes = round128((size_t)LPC * padded_len(N) * sizeof(float2));
     static constexpr size_t n_bytes = round128((size_t)LPC * N * sizeof(float));
     static constexpr size_t stage = e_bytes + n_bytes;
-    static constexpr size_t total = 128 + 2 * stage;  // two mbarriers, then two stages
+    static constexpr size_t extra = PP ? e_bytes : 0;   // second exchange buffer
+    static constexpr size_t total = 128 + 2 * stage + extra;  // two mbarriers, two stages, extra buffer
 };
 
-template <int LOGN, int C> struct ColStage {
+template <int LOGN, int C, bool PP> struct ColStage {
     static constexpr int N = 1 << LOGN;
     static constexpr int BR = N < 256 ? N : 256;  // rows per tensor-map box (box dims are <= 256)
     static constexpr int NBOX = N / BR;
     static constexpr size_t stage = round128((size_t)C * padded_len(N) * sizeof(float2));
-    static constexpr size_t total = 128 + 2 * stage;
+    static constexpr size_t total = 128 + (PP ? 3 : 2) * stage;
 };
 
 // Blocks per SM that the shared-memory plan allows (at most 8).
@@ -43,14 +53,26 @@ constexpr int smem_blocks(size_t bytes)
     return (int)((228 * 1024) / (bytes + 1024)) > 8 ? 8 : ((int)((228 * 1024) / (bytes + 1024)) > 0 ? (int)((228 * 1024) / (bytes + 1024)) : 1);
 }
 
+// Resident blocks asked of the compiler for the column sweep: what shared
+// memory allows, but never fewer than RTK_COL_REGS registers per thread (the
+// column FFT spills below ~96).
+#ifndef RTK_COL_REGS
+#define RTK_COL_REGS 128
+#endif
+constexpr int col_min_blocks(int threads, size_t bytes)
+{
+    return smem_blocks(bytes) < 65536 / (threads * RTK_COL_REGS) ? smem_blocks(bytes)
+                                                                   : (65536 / (threads * RTK_COL_REGS) > 0 ? 65536 / (threads * RTK_COL_REGS) : 1);
+}
+
 // Row sweep: LPC rows per group, T = n/16 threads per row.
-template <int LOGN, int LPC, int PE>
-__global__ void __launch_bounds__(LPC * Plan<LOGN>::T, smem_blocks(RowStage<LOGN, LPC>::total))
+template <int LOGN, int LPC, int PE, bool PP = RTK_ROW_PP>
+__global__ void __launch_bounds__(LPC * Plan<LOGN>::T, smem_blocks(RowStage<LOGN, LPC, PP>::total))
 k_row_tma(float2 *E, float *Nv, const float2 *__restrict__ tw, const float2 *__restrict__ h, GainParams<float> g,
           StatParams st, int ngroups)
 {
     using P = Plan<LOGN>;
-    using L = RowStage<LOGN, LPC>;
+    using L = RowStage<LOGN, LPC, PP>;
     constexpr int N = P::N, T = P::T, NT = LPC * T, LS = padded_len(N);
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
@@ -100,11 +122,15 @@ k_row_tma(float2 *E, float *Nv, const float2 *__restrict__ tw, const float2 *__r
         float2 v[16];
 #pragma unroll
         for (int si = 0; si < 16; ++si) v[si] = line[t + si * T];
-        fft_line<LOGN, -1, 1>(v, t, line, tw, sync);
+        // With ping-pong the first exchange goes to the extra buffer, so the
+        // dense stage is only overwritten after every thread has read it.
+        float2 *extra = reinterpret_cast<float2 *>(sm + 128 + 2 * L::stage) + lig * LS;
+        LineBufs<float2, PP> lb{{PP ? extra : line, line}, 0};
+        fft_line<LOGN, -1, 1>(v, t, lb, tw, sync);
         const float2 *hp = h + t;
 #pragma unroll
         for (int si = 0; si < 16; ++si) v[si] = cmul(v[si], __ldg(hp + si * T));
-        fft_line<LOGN, +1, 1>(v, t, line, tw, sync);
+        fft_line<LOGN, +1, 1>(v, t, lb, tw, sync);
 
         const float yc = (float)(row - N / 2) * step;
         const float yq = yc * yc * g.inv_rp2;
@@ -143,13 +169,14 @@ k_row_tma(float2 *E, float *Nv, const float2 *__restrict__ tw, const float2 *__r
 
 // Column sweep: tiles of C adjacent columns, loaded as NBOX tensor-map boxes
 // of BR rows x C complex columns.  Thread (c, t), c fastest.
-template <int LOGN, int C>
-__global__ void __launch_bounds__(C * Plan<LOGN>::T, smem_blocks(ColStage<LOGN, C>::total))
+template <int LOGN, int C, bool PP = RTK_COL_PP>
+__global__ void __launch_bounds__(C * Plan<LOGN>::T,
+                                  col_min_blocks(C * Plan<LOGN>::T, ColStage<LOGN, C, PP>::total))
 k_col_tma(float2 *E, const float2 *__restrict__ tw, const float2 *__restrict__ h,
           const __grid_constant__ CUtensorMap tmap, int ntiles, int *err)
 {
     using P = Plan<LOGN>;
-    using L = ColStage<LOGN, C>;
+    using L = ColStage<LOGN, C, PP>;
     constexpr int N = P::N, T = P::T;
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
@@ -189,11 +216,13 @@ k_col_tma(float2 *E, const float2 *__restrict__ tw, const float2 *__restrict__ h
         float2 v[16];
 #pragma unroll
         for (int si = 0; si < 16; ++si) v[si] = base[(t + si * T) * C + c];
-        fft_line<LOGN, -1, C>(v, t, base + c, tw, sync);
+        float2 *extra = stage(2);
+        LineBufs<float2, PP> lb{{PP ? extra + c : base + c, base + c}, 0};
+        fft_line<LOGN, -1, C>(v, t, lb, tw, sync);
         const float2 *hp = h + t;
 #pragma unroll
         for (int si = 0; si < 16; ++si) v[si] = cmul(v[si], __ldg(hp + si * T));
-        fft_line<LOGN, +1, C>(v, t, base + c, tw, sync);
+        fft_line<LOGN, +1, C>(v, t, lb, tw, sync);
         float2 *col = E + (size_t)t * N + tile * C + c;
 #pragma unroll
         for (int si = 0; si < 16; ++si) col[(size_t)si * T * N] = v[si];
