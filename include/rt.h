@@ -169,6 +169,39 @@ rt_status rt_read_spectrum(rt_handle *h, void *dst, size_t bytes);
  * Writes the signed (mx, my) and the folded power. Blocks. */
 rt_status rt_spectrum_peak(rt_handle *h, int ring, int *mx, int *my, double *power);
 
+/* ---- allocation-free stepping ------------------------------------------
+ * The paper has no counterpart to this entry point.  It exists for callers
+ * that cannot call cudaMalloc: a host that hands the library device buffers
+ * from its own memory pool or fixed budget and forbids any other device
+ * allocation (a plugin inside a framework that owns all device memory), or a
+ * latency-critical loop in which an allocation could synchronise the device
+ * and stall.
+ *
+ * rt_step_noalloc runs n_bounces of the fused FP32 bounce (the kernels that
+ * rt_step runs on an RT_FP32 handle) directly on the caller's device
+ * buffers, updated in place: `field` (n*n complex64, row-major) and
+ * `inversion` (n*n float), both 16-byte aligned.  It allocates nothing.  The
+ * scratch it needs (propagator and twiddle tables, reduction partials,
+ * counters) lives in one fixed array of about 97 KB of device memory that
+ * every GPU which loads this library holds until the process exits; n is
+ * therefore limited to RT_NOALLOC_MAX_N, and larger sizes return RT_EINVAL.
+ * Supported: RT_FP32 only, super-Gaussian pump of order 10 or uniform pump
+ * (anything else returns RT_EINVAL).  Options used: Isat, edge_px,
+ * pump_diam_over_window, cuda_stream, col_tile (NULL opts = defaults).
+ *
+ * The first call on each device looks up the array's device address, with
+ * that device current; make that first call before any stream capture.
+ * All calls share the one array: each call rebuilds the tables and clears
+ * the counters it needs, and calls whose work overlaps on the GPU race with
+ * one another, so order them on one stream or with events.
+ * With mean_intensity == NULL the call is asynchronous on the stream.  With
+ * a host pointer it waits for the work, returns a device error (RT_ENUMERIC,
+ * RT_ETIMEOUT) if one occurred, and stores <|E|^2> after the last bounce. */
+#define RT_NOALLOC_MAX_N 4096
+rt_status rt_step_noalloc(int n, double fresnel, const rt_pump *pump, double g0, double T1, double R,
+                          const rt_opts *opts, void *field, void *inversion, long long n_bounces,
+                          double *mean_intensity);
+
 /* Release every device buffer and graph of the handle (NULL is accepted). */
 rt_status rt_destroy(rt_handle *h);
 

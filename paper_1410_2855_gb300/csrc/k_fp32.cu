@@ -158,6 +158,8 @@ template <int LOGN> static int col_ok32(int colC)
 
 int col_tile_ok32(int logn, int colC) { RTK_LOGN_CASES(col_ok32, colC) }
 
+int default_col_tile32(int logn) { return logn >= 12 ? 2 : (logn >= 11 ? 4 : (logn >= 10 ? 8 : 16)); }
+
 // ---- row sweep (diffraction along x + local map) --------------------------------
 
 template <int LOGN, int PE>

@@ -72,6 +72,8 @@ def lib() -> ctypes.CDLL:
             "rt_read_spectrum": [vp, vp, sz],
             "rt_spectrum_peak": [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(d)],
             "rt_destroy": [vp],
+            "rt_step_noalloc": [i, d, ctypes.POINTER(rt_pump), d, d, d, ctypes.POINTER(rt_opts), vp, vp, ll,
+                                ctypes.POINTER(d)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -198,6 +200,22 @@ def rt_spectrum_peak(h, ring: int = 0):
 
 def rt_destroy(h):
     _check(lib().rt_destroy(h), "rt_destroy")
+
+
+RT_NOALLOC_MAX_N = 4096
+
+
+def rt_step_noalloc(n: int, fresnel: float, pump: rt_pump | None, g0: float, T1: float, R: float,
+                    opts: rt_opts | None, field, inversion, n_bounces: int, wait: bool = True):
+    """Allocation-free bounces on caller-owned device buffers (see include/rt.h):
+    `field` and `inversion` are contiguous CUDA tensors (complex64 / float32,
+    n x n) updated in place.  With wait=True returns the mean intensity after
+    the last bounce; with wait=False returns None without synchronising."""
+    mean = ctypes.c_double()
+    _check(lib().rt_step_noalloc(n, fresnel, ctypes.byref(pump) if pump is not None else None, g0, T1, R,
+                                 ctypes.byref(opts) if opts is not None else None, _ptr(field), _ptr(inversion),
+                                 int(n_bounces), ctypes.byref(mean) if wait else None), "rt_step_noalloc")
+    return mean.value if wait else None
 
 
 # --------------------------------------------------------- convenience wrapper

@@ -74,6 +74,15 @@ def test_create_rejects_bad_options(lib):
     assert lib.rt_create(64, 100.0, ctypes.byref(p), 0.2, 1000.0, 0.95, None, ctypes.byref(h)) == rt.RT_EINVAL
 
 
+def test_noalloc_rejects_oversize_and_unsupported_requests_on_the_host(lib):
+    big = ctypes.c_void_p(16)
+    assert lib.rt_step_noalloc(8192, 100.0, None, 0.2, 1000.0, 0.95, None, big, big, 1, None) == rt.RT_EINVAL
+    o = rt.rt_opts_default()
+    o.precision = rt.RT_FP64
+    assert lib.rt_step_noalloc(64, 100.0, None, 0.2, 1000.0, 0.95, ctypes.byref(o), big, big, 1, None) == rt.RT_EINVAL
+    assert lib.rt_step_noalloc(64, 100.0, None, 0.2, 1000.0, 0.95, None, None, big, 1, None) == rt.RT_EINVAL
+
+
 def test_null_handles_are_rejected(lib):
     assert lib.rt_step(None, 1) == rt.RT_EINVAL
     assert lib.rt_sync(None) == rt.RT_EINVAL
