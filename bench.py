@@ -4,17 +4,19 @@
 Workload: two 2048 x 2048 complex64 resonators, Fresnel number 1000,
 g0 in {0.1, 0.3}, T1 = 1e4 bounces, R = 0.9, super-Gaussian pump (order 10,
 radius 0.8), 8-pixel absorbing edge, seeded noise start.  One step = B
-bounces (default 500, one captured CUDA graph) of each resonator; the
-default 20 timed steps are the full 1e4 round trips.
+bounces (default 500, one captured CUDA graph per resonator) of each
+resonator; the default 20 timed steps are the full 1e4 round trips.  The two
+resonators run concurrently on their own streams (independent resonators
+overlap on the device; each keeps its state resident).
 
 Prints one JSON line.  `value` is resonator round trips per second over the
-timed steps with the state resident on the device (CUDA events on the
-handles' stream, L2 flushed between steps).  Alongside: per-kernel event
-timing and the HBM roofline of the dominant sweep, the same metric end to
-end through the C ABI from pinned host buffers, the plain FP64 GPU path and a
-cuFFT + PyTorch pointwise form on the same GPU (comparisons only), the error
-against the FP64 oracle after one bounce, and the oracle's own rate on the
-host cores.
+timed steps with the state resident on the device (CUDA events, L2 flushed
+between steps).  Alongside: per-kernel event timing and the HBM roofline of
+the dominant sweep, the same metric end to end through the C ABI from pinned
+host buffers, the one-stream (sequential) rate, the batched 256-resonator
+parameter sweep, the plain FP64 GPU path and a cuFFT + PyTorch pointwise form
+on the same GPU (comparisons only), the error against the FP64 oracle after
+one bounce, and the oracle's own rate on the host cores.
 
 `--impl reference` times the FP64 CPU oracle on the same workload instead
 (bounded samples of the same resonators per step).
@@ -45,7 +47,7 @@ METRIC = "round trips/s at 2048² FP32 vs FP64, % HBM peak; serve p50/p99 latenc
 UNIT = "round trips/s"
 COL_BYTES_PER_PT = 16   # column sweep: read and write the complex64 field
 ROW_BYTES_PER_PT = 24   # row sweep: field (8+8) and inversion (4+4)
-KERNEL_SOURCES = ["fft_core.cuh", "sweep.cuh", "k_fp32.cu"]
+KERNEL_SOURCES = ["fft_core.cuh", "sweep.cuh", "sweep_tma.cuh", "tma.cuh", "k_fp32.cu"]
 
 
 def parse_args():
@@ -55,7 +57,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--bounces-per-step", type=int, default=500)
-    ap.add_argument("--no-comparisons", action="store_true", help="skip FP64 / cuFFT / oracle legs")
+    ap.add_argument("--no-comparisons", action="store_true", help="skip the comparison legs")
     return ap.parse_args()
 
 
@@ -90,6 +92,7 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
+        self.out = ""
 
     def __enter__(self):
         try:
@@ -101,7 +104,6 @@ class ClockSampler:
         return self
 
     def __exit__(self, *a):
-        self.out = ""
         if self.proc:
             self.proc.terminate()
             try:
@@ -157,7 +159,8 @@ def profiled_traffic(kernel: str, n: int):
         return None
     vals = {}
     for line in text.splitlines():
-        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "kernel_source_sha")):
+        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "kernel_source_sha",
+                                                    "- traffic_bytes_per_launch", "- kernel_source_sha")):
             k, v = line.split(":", 1)
             vals[k.strip(" -*`")] = v.strip(" `")
     if vals.get("kernel_source_sha") != kernel_source_sha():
@@ -174,24 +177,23 @@ def oracle_params(p):
                            edge=p.edge, pump_order=p.pump_order, pump_radius=p.pump_radius)
 
 
-def oracle_rate(params_list, E0s, N0s, budget_s=12.0, min_bounces=2):
+def oracle_rate(params_list, E0s, N0s, budget_s=12.0):
     """Bounces/s of the FP64 oracle on the host cores (bounded sample)."""
     import oracle as orc
     threads = os.cpu_count() or 1
     done, t_total, per = 0, 0.0, 1
-    results = {}
+    first = {}
     while True:
         for i, p in enumerate(params_list):
             t0 = time.perf_counter()
             E, N, _ = orc.run(p, E0s[i], N0s[i], per, nthreads=threads, history=False)
             t_total += time.perf_counter() - t0
             done += per
-            results.setdefault(i, E)
-        if t_total >= budget_s or done >= 64:
-            if done >= min_bounces:
-                break
+            first.setdefault(i, E)
+        if (t_total >= budget_s or done >= 64) and done >= 2:
+            break
         per = min(per * 2, 4)
-    return done / t_total, threads, done, results
+    return done / t_total, threads, done, first
 
 
 # ---------------------------------------------------------------- reference
@@ -216,7 +218,8 @@ def run_reference(args):
             orc.run(p, E, N, 1, nthreads=threads, history=False)
     dt = time.perf_counter() - t0
     value = args.steps * len(params) / dt
-    sample = f"{args.steps} steps x 1 bounce of each of the {len(params)} 2048^2 resonators (FP64 oracle, table set-up included)"
+    sample = (f"{args.steps} steps x 1 bounce of each of the {len(params)} 2048^2 resonators "
+              "(FP64 oracle, table set-up included)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
@@ -228,6 +231,26 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------- ours
+
+class Fork:
+    """Run work on several streams as one step: the streams wait for an
+    event on `main` before the work and `main` waits for all of them after."""
+
+    def __init__(self, torch, main, streams):
+        self.torch, self.main, self.streams = torch, main, streams
+
+    def begin(self):
+        e = self.torch.cuda.Event()
+        e.record(self.main)
+        for s in self.streams:
+            s.wait_event(e)
+
+    def end(self):
+        for s in self.streams:
+            e = self.torch.cuda.Event()
+            e.record(s)
+            self.main.wait_event(e)
+
 
 def torch_cufft_rate(p, steps=100):
     """Comparison only: the same bounce with cuFFT (torch.fft) and PyTorch
@@ -278,11 +301,13 @@ def run_ours(args):
     torch.cuda.set_device(local_rank)
     build.build()
     dev = torch.device("cuda", local_rank)
-    stream = torch.cuda.Stream(device=dev)
+    main = torch.cuda.Stream(device=dev)
     B, K, W = args.bounces_per_step, args.steps, args.warmup
     params = workload(rank)
-    res = [rt.Resonator.from_params(p, precision=rt.RT_FP32, cuda_stream=stream.cuda_stream, chunk=B)
-           for p in params]
+    streams = [torch.cuda.Stream(device=dev) for _ in params]
+    res = [rt.Resonator.from_params(p, precision=rt.RT_FP32, cuda_stream=s.cuda_stream, chunk=B)
+           for p, s in zip(params, streams)]
+    fork = Fork(torch, main, streams)
     P = params[0].n ** 2
     E0 = [r.field() for r in res]
     N0 = [r.inversion() for r in res]
@@ -292,46 +317,49 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
 
-    with torch.cuda.stream(stream):
+    def step():
+        fork.begin()
+        for r in res:
+            rt.rt_step(r.h, B)
+        fork.end()
+
+    with torch.cuda.stream(main):
         for _ in range(W):
-            for r in res:
-                rt.rt_step(r.h, B)
-        stream.synchronize()
+            step()
+        torch.cuda.synchronize()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
         barrier()
         torch.cuda.synchronize()
         with ClockSampler(local_rank) as clk:
             for k in range(K):
                 flush.fill_(float(k))
-                evs[k][0].record(stream)
-                for r in res:
-                    rt.rt_step(r.h, B)
-                evs[k][1].record(stream)
-            stream.synchronize()
-            barrier()
+                evs[k][0].record(main)
+                step()
+                evs[k][1].record(main)
             torch.cuda.synchronize()
+            barrier()
         step_ms = [a.elapsed_time(b) for a, b in evs]
         total_ms = sum(step_ms)
         if world > 1:
             t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             total_ms = float(t.item())
-        units = world * K * B * len(res)
-        value = units / (total_ms / 1e3)
+        value = world * K * B * len(res) / (total_ms / 1e3)
         for r in res:
             r.sync()
 
-        # per-kernel durations (events on the launching stream around each sweep)
+        # per-kernel durations: events around each sweep on the launching stream,
+        # one resonator at a time (the kernels alone on the GPU)
         reps = 200
+        r, st = res[0], streams[0]
         e = [torch.cuda.Event(enable_timing=True) for _ in range(3 * reps)]
         for i in range(reps):
-            r = res[i % len(res)]
-            e[3 * i].record(stream)
+            e[3 * i].record(st)
             rt.rt_sweep(r.h, rt.RT_SWEEP_COLUMNS)
-            e[3 * i + 1].record(stream)
+            e[3 * i + 1].record(st)
             rt.rt_sweep(r.h, rt.RT_SWEEP_ROWS)
-            e[3 * i + 2].record(stream)
-        stream.synchronize()
+            e[3 * i + 2].record(st)
+        torch.cuda.synchronize()
         col_ms = statistics.mean(e[3 * i].elapsed_time(e[3 * i + 1]) for i in range(reps))
         row_ms = statistics.mean(e[3 * i + 1].elapsed_time(e[3 * i + 2]) for i in range(reps))
 
@@ -339,31 +367,34 @@ def run_ours(args):
     col_gbs = COL_BYTES_PER_PT * P / (col_ms / 1e3) / 1e9
     row_gbs = ROW_BYTES_PER_PT * P / (row_ms / 1e3) / 1e9
     if row_ms >= col_ms:
-        dom, dom_bytes, dom_gbs, dom_ms, dom_name = "row_sweep", ROW_BYTES_PER_PT * P, row_gbs, row_ms, "k_row"
+        dom, dom_bytes, dom_gbs, dom_ms = "row_sweep", ROW_BYTES_PER_PT * P, row_gbs, row_ms
     else:
-        dom, dom_bytes, dom_gbs, dom_ms, dom_name = "column_sweep", COL_BYTES_PER_PT * P, col_gbs, col_ms, "k_col"
-    bounce_gbs = (COL_BYTES_PER_PT + ROW_BYTES_PER_PT) * P * value / len(res) * len(res) / 1e9 / world
+        dom, dom_bytes, dom_gbs, dom_ms = "column_sweep", COL_BYTES_PER_PT * P, col_gbs, col_ms
+    bounce_gbs = (COL_BYTES_PER_PT + ROW_BYTES_PER_PT) * P * value / world / 1e9
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": config_block(B, {"l2": "flushed between steps (256 MiB write); the two resonators' 96 MiB "
-                                         "state stays L2-resident within a step",
-                                   "graph": f"one CUDA graph per {B} bounces"}),
+        "config": config_block(B, {"l2": "flushed between steps (256 MiB write); each resonator's 48 MiB state "
+                                         "stays L2-resident within a step",
+                                   "graph": f"one CUDA graph per {B} bounces per resonator",
+                                   "streams": "one per resonator, concurrent"}),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": dom_gbs, "peak": peak, "unit": "GB/s",
                      "frac": dom_gbs / peak, "peak_kind": f"of {peak_kind}",
                      "traffic": profiled_traffic(dom, params[0].n),
-                     "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms},
+                     "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms,
+                     "timing": "CUDA events around each launch, kernel alone on the GPU"},
         "kernels": {"column_sweep": {"avg_ms": col_ms, "gbs": col_gbs, "bytes_per_launch": COL_BYTES_PER_PT * P},
                     "row_sweep": {"avg_ms": row_ms, "gbs": row_gbs, "bytes_per_launch": ROW_BYTES_PER_PT * P}},
-        "bounce_hbm_fraction": bounce_gbs / peak,
+        "bounce_hbm": {"bytes_per_point": COL_BYTES_PER_PT + ROW_BYTES_PER_PT, "achieved_gbs": bounce_gbs,
+                       "frac": bounce_gbs / peak, "peak_kind": f"of {peak_kind}"},
         "gpu_launches": 2 * K * B * len(res),
         "clocks": clk.summary(),
     }
 
     if not args.no_comparisons:
-        out.update(comparisons(args, rt, torch, stream, params, res, E0, N0, rank, world))
+        out.update(comparisons(args, rt, torch, main, streams, params, res, E0, N0, rank, world))
     if world > 1:
         torch.distributed.barrier()
     for r in res:
@@ -374,68 +405,108 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def comparisons(args, rt, torch, stream, params, res, E0, N0, rank, world):
+def comparisons(args, rt, torch, main, streams, params, res, E0, N0, rank, world):
     B = args.bounces_per_step
     extra = {}
     P = params[0].n ** 2
+    fork = Fork(torch, main, streams)
     # ---- end to end through the C ABI from pinned host buffers
     hostE = [torch.from_numpy(e.view(np.float32).copy()).pin_memory() for e in E0]
     hostN = [torch.from_numpy(nv.copy()).pin_memory() for nv in N0]
     outE = [torch.empty(P * 2, dtype=torch.float32).pin_memory() for _ in res]
     K2 = max(2, min(args.steps, 6))
-    with torch.cuda.stream(stream):
-        for r, e, nv in zip(res, hostE, hostN):      # one untimed warm step
+
+    def e2e_step():
+        fork.begin()
+        for r, e, nv in zip(res, hostE, hostN):
             rt.rt_write_field(r.h, e)
             rt.rt_write_inversion(r.h, nv)
             rt.rt_step(r.h, B)
         for r, o in zip(res, outE):
-            rt.rt_read_field(r.h, o)
+            rt.rt_read_field(r.h, o)     # blocks until that resonator's step is done
+        fork.end()
+
+    with torch.cuda.stream(main):
+        e2e_step()
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(K2):
-            for r, e, nv in zip(res, hostE, hostN):
-                rt.rt_write_field(r.h, e)
-                rt.rt_write_inversion(r.h, nv)
-                rt.rt_step(r.h, B)
-            for r, o in zip(res, outE):
-                rt.rt_read_field(r.h, o)
+            e2e_step()
+        torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
     extra["e2e"] = {"value": world * K2 * B * len(res) / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": len(res) * 12 * P, "d2h_bytes_per_step": len(res) * 8 * P,
-                    "steps": K2}
+                    "steps": K2, "timing": "host wall clock around the steps"}
+
+    # ---- the same resonators one after the other on a single stream
+    with torch.cuda.stream(main):
+        one = [rt.Resonator.from_params(p, cuda_stream=main.cuda_stream, chunk=B) for p in params]
+        for r in one:
+            r.step(B)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(main)
+        for _ in range(4):
+            for r in one:
+                r.step(B)
+        e.record(main)
+        torch.cuda.synchronize()
+        for r in one:
+            r.close()
+    extra["one_stream"] = {"value": 4 * B * len(params) / (s.elapsed_time(e) / 1e3), "unit": UNIT}
+
+    # ---- batched parameter sweep: 256 resonators of side 256/512/1024 in one graph per 100 bounces
+    jobs = wl.batch_sweep(count=256, sides=(256, 512, 1024))
+    with torch.cuda.stream(main):
+        with rt.Batch(jobs, chunk=100, history_cap=128, cuda_stream=main.cuda_stream) as bt:
+            bt.step(100)
+            torch.cuda.synchronize()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(main)
+            bt.step(200)
+            e.record(main)
+            torch.cuda.synchronize()
+            bt.sync()
+            secs = s.elapsed_time(e) / 1e3
+            Pb = sum(j.n ** 2 for j in jobs)
+            peak, _ = measured_peak()
+            extra["batch_sweep"] = {
+                "workload": "256 resonators, sides uniform over {256,512,1024}, N_F log-uniform [100,1000], "
+                            "g0 U[0.1,0.3], T1 U[1e3,1e4], R=0.95; one CUDA graph per 100 bounces",
+                "round_trips_per_s": len(jobs) * 200 / secs, "point_bounces_per_s": Pb * 200 / secs,
+                "hbm_frac": 40 * Pb * 200 / secs / 1e9 / peak, "footprint_bytes": bt.footprint()}
 
     # ---- plain FP64 GPU path on the same GPU (unfused, six sweeps per bounce)
     p = params[1]
-    with rt.Resonator.from_params(p, precision=rt.RT_FP64, cuda_stream=stream.cuda_stream, chunk=50) as r64:
-        with torch.cuda.stream(stream):
+    with rt.Resonator.from_params(p, precision=rt.RT_FP64, cuda_stream=main.cuda_stream, chunk=50) as r64:
+        with torch.cuda.stream(main):
             rt.rt_step(r64.h, 50)
-            stream.synchronize()
+            torch.cuda.synchronize()
             s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s.record(stream)
+            s.record(main)
             rt.rt_step(r64.h, 200)
-            e.record(stream)
-            stream.synchronize()
+            e.record(main)
+            torch.cuda.synchronize()
         r64.sync()
         fp64 = 200 / (s.elapsed_time(e) / 1e3)
-    extra["fp64_plain"] = {"value": fp64, "unit": "round trips/s", "resonators": 1, "bounces": 200,
-                           "fused_fp32_speedup": None}
-    extra["torch_cufft_fp32"] = {"value": torch_cufft_rate(p), "unit": "round trips/s", "resonators": 1,
+    extra["fp64_plain"] = {"value": fp64, "unit": UNIT, "resonators": 1, "bounces": 200}
+    extra["torch_cufft_fp32"] = {"value": torch_cufft_rate(p), "unit": UNIT, "resonators": 1,
                                  "note": "comparison only: cuFFT C2C + PyTorch pointwise kernels"}
-    per_res = None
     if rank == 0:
         # ---- error after one bounce against the FP64 oracle, and the oracle's rate
         import oracle as orc
         orc.build()
         oparams = [oracle_params(q) for q in params]
-        E0w = [e.astype(np.complex128) for e in E0]
+        E0w = [x.astype(np.complex128) for x in E0]
         N0o = [orc.pump(q) for q in oparams]
         rate, threads, done, firsts = oracle_rate(oparams, E0w, N0o)
         errs = []
-        for q, e0, o1 in zip(params, E0, [firsts[i] for i in range(len(params))]):
+        for i, (q, e0) in enumerate(zip(params, E0)):
             with rt.Resonator.from_params(q, precision=rt.RT_FP32, chunk=0) as r1:
                 r1.set_field(e0)
                 r1.step(1)
                 g1 = r1.field()
-            errs.append(float(np.linalg.norm(g1 - o1) / np.linalg.norm(o1)))
+            errs.append(float(np.linalg.norm(g1 - firsts[i]) / np.linalg.norm(firsts[i])))
         extra["error_vs_oracle"] = {"bounce1_rel_l2": errs, "bar": 1e-5}
         extra["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                  "sample": f"{done} oracle bounces over the two 2048^2 resonators "

@@ -169,6 +169,71 @@ rt_status rt_read_spectrum(rt_handle *h, void *dst, size_t bytes);
  * Writes the signed (mx, my) and the folded power. Blocks. */
 rt_status rt_spectrum_peak(rt_handle *h, int ring, int *mx, int *my, double *power);
 
+/* ---- batches of resonators ---------------------------------------------
+ * Many independent resonators (eq. conv_map per resonator, each with its
+ * own grid size, Fresnel number, pump, gain, T1, R) stepped together: the
+ * resonators of one grid size share each persistent launch of the two
+ * sweeps, so small grids fill the GPU and large batches keep every SM busy.
+ * FP32 only; 32 <= n <= 2048 per job. */
+typedef struct {
+    int n;                        /* grid side (power of two, 32..2048) */
+    double fresnel;               /* N_F */
+    double g0, T1, R;             /* gain exponent per pass, relaxation (bounces), mirror reflectivity */
+    rt_pump pump;                 /* pump (profile copied at set-up) */
+    double Isat;                  /* saturation intensity */
+    int edge_px;                  /* absorbing edge width */
+    unsigned long long seed;      /* noise seed */
+    double noise_amp;             /* noise amplitude */
+    double pump_diam_over_window; /* D/W */
+} rt_job;
+
+/* Fill a job with the defaults of rt_opts_default / rt_create for side n. */
+rt_status rt_job_default(rt_job *job, int n);
+
+typedef struct rt_batch rt_batch;
+
+/* Create a batch of `count` resonators (slots 0..count-1) from jobs.
+ * opts: cuda_stream, history_cap, chunk and col_tile are used; precision
+ * must be RT_FP32.  Every slot starts as rt_create would start it and runs
+ * without a bounce limit.  RT_EINVAL, RT_ENOMEM, RT_ECUDA. */
+rt_status rt_batch_create(const rt_job *jobs, int count, const rt_opts *opts, rt_batch **out);
+
+/* Enqueue n_bounces iterations for every slot that has bounces left.  Async. */
+rt_status rt_batch_step(rt_batch *b, long long n_bounces);
+
+/* One half of a bounce over every active slot, for per-kernel timing:
+ * RT_SWEEP_COLUMNS or RT_SWEEP_ROWS (see rt_sweep).  Async. */
+rt_status rt_batch_sweep(rt_batch *b, int which);
+
+/* Re-initialise slot i with a new job of the same n (fresh noise field,
+ * N = N0, counters at zero).  The slot then runs n_bounces more bounces and
+ * stops (n_bounces < 0: no limit; 0: the slot stays idle).  Ordered on the
+ * batch stream.  Used by the serving loop to recycle slots. */
+rt_status rt_batch_set_job(rt_batch *b, int i, const rt_job *job, long long n_bounces);
+
+/* Wait for the batch stream; reports a sticky device error of any slot. */
+rt_status rt_batch_sync(rt_batch *b);
+
+/* Per-slot copies, layouts as rt_read_field etc.  Reads block. */
+rt_status rt_batch_read_field(rt_batch *b, int i, void *dst, size_t bytes);
+rt_status rt_batch_read_inversion(rt_batch *b, int i, void *dst, size_t bytes);
+rt_status rt_batch_write_field(rt_batch *b, int i, const void *src, size_t bytes);
+rt_status rt_batch_write_inversion(rt_batch *b, int i, const void *src, size_t bytes);
+
+/* Per-slot counters (synchronises). */
+rt_status rt_batch_stats(rt_batch *b, int i, rt_stats_t *out);
+
+/* Mean intensity of slot i's most recent bounces, oldest first (host dst). */
+rt_status rt_batch_read_history(rt_batch *b, int i, double *dst, long long max, long long *got);
+
+/* Bounce counters of all slots into counts[count] (host; synchronises). */
+rt_status rt_batch_bounces(rt_batch *b, long long *counts);
+
+/* Device bytes held by the batch. */
+rt_status rt_batch_footprint(rt_batch *b, size_t *bytes);
+
+rt_status rt_batch_destroy(rt_batch *b);
+
 /* ---- allocation-free stepping ------------------------------------------
  * The paper has no counterpart to this entry point.  It exists for callers
  * that cannot call cudaMalloc: a host that hands the library device buffers

@@ -42,6 +42,18 @@ __device__ __forceinline__ V cmk(typename real_of<V>::type a, typename real_of<V
 }
 template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return cmk<V>(a.x + b.x, a.y + b.y); }
 template <typename V> __device__ __forceinline__ V csub(V a, V b) { return cmk<V>(a.x - b.x, a.y - b.y); }
+#ifndef RTK_PACKED_ADD
+#define RTK_PACKED_ADD 1
+#endif
+#if RTK_PACKED_ADD
+// FP32 complex add/subtract as one packed two-lane instruction each
+// (sm_100 family); same IEEE round-to-nearest results as two scalar ops.
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) { return __fadd2_rn(a, b); }
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b)
+{
+    return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
+#endif
 template <typename V> __device__ __forceinline__ V cmul(V a, V b)
 {
     return cmk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -127,10 +139,12 @@ template <int LOGN> struct Plan {
 };
 
 // Twiddle from the forward table (exp(-...)), conjugated for the inverse.
-template <int DIR, typename V>
+// TWS: the table is in shared memory (plain load) rather than global memory
+// (read-only cache load).
+template <int DIR, bool TWS = false, typename V>
 __device__ __forceinline__ V twmul(V a, const V *__restrict__ tw, int k)
 {
-    const V w = __ldg(tw + k);
+    const V w = TWS ? tw[k] : __ldg(tw + k);
     return DIR > 0 ? cmulc(a, w) : cmul(a, w);
 }
 
@@ -162,7 +176,7 @@ template <typename V, bool PP> struct LineBufs {
 // is a barrier over every thread that shares them.  Shared addresses are a
 // per-thread base plus compile-time offsets: spans and T are multiples of 16
 // wherever the pad arithmetic allows it.
-template <int LOGN, int DIR, int CS, bool PP, typename V, typename SyncF>
+template <int LOGN, int DIR, int CS, bool PP, bool TWS = false, typename V, typename SyncF>
 __device__ __forceinline__ void fft_line(V (&v)[16], const int t, LineBufs<V, PP> &lb, const V *__restrict__ tw,
                                          SyncF sync)
 {
@@ -198,7 +212,7 @@ __device__ __forceinline__ void fft_line(V (&v)[16], const int t, LineBufs<V, PP
         }
         const V *twp = tw + off + (t & (Ns - 1));
 #pragma unroll
-        for (int r = 1; r < 16; ++r) v[r] = twmul<DIR>(v[r], twp, (r - 1) * Ns);
+        for (int r = 1; r < 16; ++r) v[r] = twmul<DIR, TWS>(v[r], twp, (r - 1) * Ns);
         off += 15 * Ns;
         dft<16, DIR>(v);
     }
@@ -228,7 +242,7 @@ __device__ __forceinline__ void fft_line(V (&v)[16], const int t, LineBufs<V, PP
             for (int r = 0; r < RL; ++r) u[r] = rb[r * (17 * NsL / 16) * CS];
             const V *twp = tw + off + j;
 #pragma unroll
-            for (int r = 1; r < RL; ++r) u[r] = twmul<DIR>(u[r], twp, (r - 1) * NsL);
+            for (int r = 1; r < RL; ++r) u[r] = twmul<DIR, TWS>(u[r], twp, (r - 1) * NsL);
             dft<RL, DIR>(u);
 #pragma unroll
             for (int r = 0; r < RL; ++r) v[i + r * NB] = u[r];

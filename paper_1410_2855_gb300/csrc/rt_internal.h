@@ -2,12 +2,18 @@
 // parameter blocks and the host-side launchers that dispatch on log2(n).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace rtk {
 
 enum PumpKind { PUMP_SUPERGAUSS = 0, PUMP_UNIFORM = 1, PUMP_ARRAY = 2 };
+
+// Pump evaluation inside the FP32 row sweep: super-Gaussian of order 10
+// computed on the fly, uniform, or a precomputed N0 table (array pumps and
+// any other super-Gaussian order).
+enum PumpEval { PE_SG10 = 0, PE_UNIFORM = 1, PE_TABLE = 2 };
 
 // Local map parameters: E <- sqrtR * A * exp(N/2) * E',
 // N <- N + (N0 - N (1 + I invIsat)) invT1, N0 = g0 * P(x, y).
@@ -38,6 +44,31 @@ struct PeakResult {
     double value;
     long long index;
 };
+
+// One resonator of a batched launch (device memory): its state, propagator
+// table, local-map parameters and statistics.  st.part must hold one double
+// per row group.  Items of a resonator whose bounce counter has reached
+// `target` are skipped, so resonators with different remaining bounce counts
+// can share launches.
+struct BatchRes {
+    float2 *E;
+    float *N;
+    const float2 *h;
+    const CUtensorMap *tmap;  // column-tile tensor map of E (64-byte aligned, device memory)
+    GainParams<float> g;
+    int pe;                   // PumpEval
+    int pad;
+    long long target;         // stop once *st.bounce >= target
+    StatParams st;
+};
+
+// Batched sweeps over nres resonators of side 2^logn (descriptors `res` in
+// device memory); err receives RT_ETIMEOUT if a copy wait runs out.
+cudaError_t launch_col_batch32(int logn, int colC, const BatchRes *res, int nres, const float2 *tw, int *err,
+                               cudaStream_t s);
+cudaError_t launch_row_batch32(int logn, const BatchRes *res, int nres, const float2 *tw, int *err, cudaStream_t s);
+cudaError_t prepare_batch32(int logn, int colC);
+int row_groups32(int logn);  // row groups per resonator of a batched row sweep
 
 // ---- FP32 fused path: two sweeps per bounce --------------------------------
 // Column sweep: per column, forward FFT, x h(my), inverse FFT (in place).

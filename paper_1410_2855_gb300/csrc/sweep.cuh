@@ -21,11 +21,6 @@ namespace rtk {
 
 enum SweepMode { MODE_FWD = 0, MODE_INV = 1, MODE_DIFF = 2, MODE_DIFF_GAIN = 3 };
 
-// Pump evaluation inside the row sweep: super-Gaussian of order 10 computed
-// on the fly, uniform, or a precomputed N0 table (array pumps and any other
-// super-Gaussian order).
-enum PumpEval { PE_SG10 = 0, PE_UNIFORM = 1, PE_TABLE = 2 };
-
 // Lines per block of a row sweep: about 256 threads.
 template <int LOGN> constexpr int row_lpc()
 {

@@ -1,17 +1,20 @@
 // Persistent, copy-engine-fed sweeps of the fused FP32 bounce.
 //
-// Each block loops over its share of lines (rows) or tiles (column strips).
-// While it transforms line group g, the copy engine (TMA) is already
-// loading group g + gridDim.x into the other of two shared-memory stages,
-// so global-memory latency is hidden behind the FFT arithmetic instead of
-// being paid by every block at its start.  A stage is laid out with the
-// line FFT's padded stride: the copy engine fills the first n elements of
-// each line densely, the first pass reads them, and from then on the same
-// bytes serve as that line's exchange buffer.  Results leave registers
-// straight to global memory.
+// Each block loops over work items: a group of rows (row sweep) or a tile of
+// adjacent columns (column sweep).  While it transforms item i, the copy
+// engine (TMA) is already loading item i + gridDim.x into the other of two
+// shared-memory stages, so global-memory latency is hidden behind the FFT
+// arithmetic.  A stage uses the line FFT's padded stride: the copy engine
+// fills the first n elements of each line densely, the first pass reads
+// them, and from then on the same bytes serve as that line's exchange
+// buffer.  Results leave registers straight to global memory.
+//
+// Batched forms take an array of per-resonator descriptors and spread the
+// items of every resonator of one grid size over one persistent launch, so
+// the last wave of a launch is a small fraction of its work.
 //
 // Every barrier wait is bounded in time; a timeout sets RT_ETIMEOUT in the
-// handle's error word, drains the copy still in flight and ends the block.
+// error word, drains the copy still in flight and ends the block.
 #pragma once
 
 #include "sweep.cuh"
@@ -35,9 +38,10 @@ template <int LOGN, int LPC, bool PP> struct RowStage {
     static constexpr size_t e_bytes = round128((size_t)LPC * padded_len(N) * sizeof(float2));
     static constexpr size_t n_bytes = round128((size_t)LPC * N * sizeof(float));
     static constexpr size_t stage = e_bytes + n_bytes;
-    static constexpr size_t extra = PP ? e_bytes : 0;   // second exchange buffer
-    static constexpr size_t total = 128 + 2 * stage + extra;  // two mbarriers, two stages, extra buffer
+    static constexpr size_t extra = PP ? e_bytes : 0;          // second exchange buffer
+    static constexpr size_t total = 128 + 2 * stage + extra;   // two mbarriers, two stages, extra buffer
 };
+template <int LOGN, int LPC> using RowPlan = RowStage<LOGN, LPC, RTK_ROW_PP>;
 
 template <int LOGN, int C, bool PP> struct ColStage {
     static constexpr int N = 1 << LOGN;
@@ -46,11 +50,13 @@ template <int LOGN, int C, bool PP> struct ColStage {
     static constexpr size_t stage = round128((size_t)C * padded_len(N) * sizeof(float2));
     static constexpr size_t total = 128 + (PP ? 3 : 2) * stage;
 };
+template <int LOGN, int C> using ColPlan = ColStage<LOGN, C, RTK_COL_PP>;
 
 // Blocks per SM that the shared-memory plan allows (at most 8).
 constexpr int smem_blocks(size_t bytes)
 {
-    return (int)((228 * 1024) / (bytes + 1024)) > 8 ? 8 : ((int)((228 * 1024) / (bytes + 1024)) > 0 ? (int)((228 * 1024) / (bytes + 1024)) : 1);
+    return (int)((228 * 1024) / (bytes + 1024)) > 8 ? 8
+           : ((int)((228 * 1024) / (bytes + 1024)) > 0 ? (int)((228 * 1024) / (bytes + 1024)) : 1);
 }
 
 // Resident blocks asked of the compiler for the column sweep: what shared
@@ -61,9 +67,146 @@ constexpr int smem_blocks(size_t bytes)
 #endif
 constexpr int col_min_blocks(int threads, size_t bytes)
 {
-    return smem_blocks(bytes) < 65536 / (threads * RTK_COL_REGS) ? smem_blocks(bytes)
-                                                                   : (65536 / (threads * RTK_COL_REGS) > 0 ? 65536 / (threads * RTK_COL_REGS) : 1);
+    return smem_blocks(bytes) < 65536 / (threads * RTK_COL_REGS)
+               ? smem_blocks(bytes)
+               : (65536 / (threads * RTK_COL_REGS) > 0 ? 65536 / (threads * RTK_COL_REGS) : 1);
 }
+
+// A batched resonator still has bounces to do.  Its counter only changes at
+// the end of a row sweep, after every item of that resonator in the launch
+// has been processed, so all items of a launch see the same answer.
+__device__ __forceinline__ bool res_active(const BatchRes &R)
+{
+    return __ldcg(R.st.bounce) < R.target;
+}
+
+// ---- shared pieces ----------------------------------------------------------
+
+// Bounded wait on a stage barrier; on a timeout the block drains the copy
+// still in flight, records RT_ETIMEOUT and reports true (leave the loop).
+__device__ __forceinline__ bool stage_wait_or_abort(uint64_t *bar, int it, bool next_in_flight, int *err)
+{
+    const bool late = !mbar_wait(&bar[it & 1], (uint32_t)((it >> 1) & 1));
+    if (__syncthreads_or(late)) {
+        if (threadIdx.x == 0) {
+            atomicExch(err, ERR_TIMEOUT);
+            if (next_in_flight) mbar_wait(&bar[(it + 1) & 1], (uint32_t)(((it + 1) >> 1) & 1));
+        }
+        return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void init_stage_barriers(uint64_t *bar)
+{
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+}
+
+// Local map of one row held in registers (slot s = column t + T s):
+// gain against the frozen inversion, mirror, absorbing edge, inversion
+// relaxation.  Returns sum |E_new|^2 over the thread's 16 elements.
+template <int LOGN, int PE>
+__device__ __forceinline__ float row_local_map(float2 (&v)[16], int t, int row, const float *nrow, float2 *erow,
+                                               float *ngl, const GainParams<float> &g)
+{
+    constexpr int N = 1 << LOGN, T = Plan<LOGN>::T;
+    const float step = 2.0f / (float)N;
+    const float xc0 = (float)(t - N / 2) * step;
+    const float yc = (float)(row - N / 2) * step;
+    const float yq = yc * yc * g.inv_rp2;
+    const bool row_in = row >= g.edge && row < N - g.edge;
+    float acc = 0.0f;
+#pragma unroll
+    for (int si = 0; si < 16; ++si) {
+        const int x = t + si * T;
+        const float nn = nrow[si * T];
+        float2 e = v[si];
+        const float inten = e.x * e.x + e.y * e.y;
+        const bool inside = row_in && x >= g.edge && x < N - g.edge;
+        e = cscale(e, inside ? g.sqrtR * fexp(0.5f * nn) : 0.0f);
+        float n0;
+        if constexpr (PE == PE_UNIFORM) {
+            n0 = g.g0;
+        } else if constexpr (PE == PE_TABLE) {
+            n0 = __ldg(g.pump_tab + (size_t)row * N + x);
+        } else {
+            const float xc = xc0 + (float)(si * T) * step;
+            const float q = xc * xc * g.inv_rp2 + yq;
+            const float q2 = q * q;
+            n0 = g.g0 * fexp(-(q2 * q2 * q));
+        }
+        ngl[si * T] = nn + (n0 - nn * (1.0f + inten * g.invIsat)) * g.invT1;
+        erow[si * T] = e;
+        acc += e.x * e.x + e.y * e.y;
+    }
+    return acc;
+}
+
+// Forward FFT, x h, inverse FFT of the line held in v (exchanges in lb).
+template <int LOGN, int CS, bool PP, typename SyncF>
+__device__ __forceinline__ void diffract_line(float2 (&v)[16], int t, LineBufs<float2, PP> &lb,
+                                              const float2 *__restrict__ tw, const float2 *__restrict__ h,
+                                              SyncF sync)
+{
+    constexpr int T = Plan<LOGN>::T;
+    fft_line<LOGN, -1, CS>(v, t, lb, tw, sync);
+    const float2 *hp = h + t;
+#pragma unroll
+    for (int si = 0; si < 16; ++si) v[si] = cmul(v[si], __ldg(hp + si * T));
+    fft_line<LOGN, +1, CS>(v, t, lb, tw, sync);
+}
+
+// Per-resonator mean intensity of a batched row sweep: each item (row group)
+// stores its block sum; the last item of a resonator to arrive adds them up
+// in item order and records the mean (deterministic).
+template <int NT>
+__device__ __forceinline__ void item_finish(double v, const StatParams &st, int item, int nitems, double inv_points)
+{
+    static_assert(NT % 32 == 0, "whole warps");
+    __shared__ double red[NT / 32];
+    __shared__ int is_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < NT / 32; ++w) s += red[w];
+        st.part[item] = s;
+        __threadfence();
+        is_last = (atomicAdd(st.count, 1u) == (unsigned)nitems - 1u);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nitems; i += NT) s += __ldcg(st.part + i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    __syncthreads();
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < NT / 32; ++w) tot += red[w];
+        const double mean = tot * inv_points;
+        const long long b = *st.bounce;
+        if (st.hist_cap > 0) st.hist[b % st.hist_cap] = mean;
+        *st.last_mean = mean;
+        *st.bounce = b + 1;
+        if (!isfinite(mean)) atomicExch(st.err, -4);
+        *st.count = 0u;
+    }
+}
+
+// ---- single resonator -------------------------------------------------------
 
 // Row sweep: LPC rows per group, T = n/16 threads per row.
 template <int LOGN, int LPC, int PE, bool PP = RTK_ROW_PP>
@@ -89,17 +232,9 @@ k_row_tma(float2 *E, float *Nv, const float2 *__restrict__ tw, const float2 *__r
         }
     };
 
-    if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_barrier_init();
-    }
-    __syncthreads();
+    init_stage_barriers(bar);
     int grp = blockIdx.x;
     if (threadIdx.x == 0 && grp < ngroups) issue(0, grp);
-
-    const float step = 2.0f / (float)N;
-    const float xc0 = (float)(t - N / 2) * step;
     double dacc = 0.0;
     for (int it = 0; grp < ngroups; ++it, grp += gridDim.x) {
         const int s = it & 1;
@@ -108,17 +243,9 @@ k_row_tma(float2 *E, float *Nv, const float2 *__restrict__ tw, const float2 *__r
             fence_proxy_async_smem();
             issue(s ^ 1, nxt);
         }
-        const bool late = !mbar_wait(&bar[s], (uint32_t)((it >> 1) & 1));
-        if (__syncthreads_or(late)) {
-            if (threadIdx.x == 0) {
-                atomicExch(st.err, ERR_TIMEOUT);
-                if (nxt < ngroups) mbar_wait(&bar[s ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
-            }
-            break;
-        }
+        if (stage_wait_or_abort(bar, it, nxt < ngroups, st.err)) break;
         const int row = grp * LPC + lig;
         float2 *line = stage_e(s) + lig * LS;
-        const float *nrow = stage_n(s) + lig * N + t;
         float2 v[16];
 #pragma unroll
         for (int si = 0; si < 16; ++si) v[si] = line[t + si * T];
@@ -126,42 +253,9 @@ k_row_tma(float2 *E, float *Nv, const float2 *__restrict__ tw, const float2 *__r
         // dense stage is only overwritten after every thread has read it.
         float2 *extra = reinterpret_cast<float2 *>(sm + 128 + 2 * L::stage) + lig * LS;
         LineBufs<float2, PP> lb{{PP ? extra : line, line}, 0};
-        fft_line<LOGN, -1, 1>(v, t, lb, tw, sync);
-        const float2 *hp = h + t;
-#pragma unroll
-        for (int si = 0; si < 16; ++si) v[si] = cmul(v[si], __ldg(hp + si * T));
-        fft_line<LOGN, +1, 1>(v, t, lb, tw, sync);
-
-        const float yc = (float)(row - N / 2) * step;
-        const float yq = yc * yc * g.inv_rp2;
-        const bool row_in = row >= g.edge && row < N - g.edge;
-        float2 *erow = E + (size_t)row * N + t;
-        float *ngl = Nv + (size_t)row * N + t;
-        float acc = 0.0f;
-#pragma unroll
-        for (int si = 0; si < 16; ++si) {
-            const int x = t + si * T;
-            const float nn = nrow[si * T];
-            float2 e = v[si];
-            const float inten = e.x * e.x + e.y * e.y;
-            const bool inside = row_in && x >= g.edge && x < N - g.edge;
-            e = cscale(e, inside ? g.sqrtR * fexp(0.5f * nn) : 0.0f);
-            float n0;
-            if constexpr (PE == PE_UNIFORM) {
-                n0 = g.g0;
-            } else if constexpr (PE == PE_TABLE) {
-                n0 = __ldg(g.pump_tab + (size_t)row * N + x);
-            } else {
-                const float xc = xc0 + (float)(si * T) * step;
-                const float q = xc * xc * g.inv_rp2 + yq;
-                const float q2 = q * q;
-                n0 = g.g0 * fexp(-(q2 * q2 * q));
-            }
-            ngl[si * T] = nn + (n0 - nn * (1.0f + inten * g.invIsat)) * g.invT1;
-            erow[si * T] = e;
-            acc += e.x * e.x + e.y * e.y;
-        }
-        dacc += (double)acc;
+        diffract_line<LOGN, 1>(v, t, lb, tw, h, sync);
+        dacc += (double)row_local_map<LOGN, PE>(v, t, row, stage_n(s) + lig * N + t, E + (size_t)row * N + t,
+                                                Nv + (size_t)row * N + t, g);
         __syncthreads();  // stage s fully consumed before it is refilled
     }
     finish_mean<NT>(dacc, st, 1.0 / ((double)N * (double)N));
@@ -189,12 +283,7 @@ k_col_tma(float2 *E, const float2 *__restrict__ tw, const float2 *__restrict__ h
             tma_load_2d(stage(s) + b * L::BR * C, &tmap, 2 * tile * C, b * L::BR, &bar[s]);
     };
 
-    if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_barrier_init();
-    }
-    __syncthreads();
+    init_stage_barriers(bar);
     int tile = blockIdx.x;
     if (threadIdx.x == 0 && tile < ntiles) issue(0, tile);
     for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
@@ -204,29 +293,145 @@ k_col_tma(float2 *E, const float2 *__restrict__ tw, const float2 *__restrict__ h
             fence_proxy_async_smem();
             issue(s ^ 1, nxt);
         }
-        const bool late = !mbar_wait(&bar[s], (uint32_t)((it >> 1) & 1));
-        if (__syncthreads_or(late)) {
-            if (threadIdx.x == 0) {
-                atomicExch(err, ERR_TIMEOUT);
-                if (nxt < ntiles) mbar_wait(&bar[s ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
-            }
-            break;
-        }
+        if (stage_wait_or_abort(bar, it, nxt < ntiles, err)) break;
         float2 *base = stage(s);
         float2 v[16];
 #pragma unroll
         for (int si = 0; si < 16; ++si) v[si] = base[(t + si * T) * C + c];
-        float2 *extra = stage(2);
-        LineBufs<float2, PP> lb{{PP ? extra + c : base + c, base + c}, 0};
-        fft_line<LOGN, -1, C>(v, t, lb, tw, sync);
-        const float2 *hp = h + t;
-#pragma unroll
-        for (int si = 0; si < 16; ++si) v[si] = cmul(v[si], __ldg(hp + si * T));
-        fft_line<LOGN, +1, C>(v, t, lb, tw, sync);
+        LineBufs<float2, PP> lb{{PP ? stage(2) + c : base + c, base + c}, 0};
+        diffract_line<LOGN, C>(v, t, lb, tw, h, sync);
         float2 *col = E + (size_t)t * N + tile * C + c;
 #pragma unroll
         for (int si = 0; si < 16; ++si) col[(size_t)si * T * N] = v[si];
         __syncthreads();  // stage s fully consumed before it is refilled
+    }
+}
+
+// ---- batches of resonators of one grid size -----------------------------------
+
+// Row sweep over nres resonators: item i is row group i % G of resonator
+// i / G, G = n / LPC.  The pump evaluation is chosen per resonator.
+template <int LOGN, int LPC, bool PP = RTK_ROW_PP>
+__global__ void __launch_bounds__(LPC * Plan<LOGN>::T, smem_blocks(RowStage<LOGN, LPC, PP>::total))
+k_row_tma_batch(const BatchRes *__restrict__ res, int nres, const float2 *__restrict__ tw, int *err)
+{
+    using P = Plan<LOGN>;
+    using L = RowStage<LOGN, LPC, PP>;
+    constexpr int N = P::N, T = P::T, NT = LPC * T, LS = padded_len(N), G = N / LPC;
+    extern __shared__ __align__(128) unsigned char sm[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
+    const int lig = threadIdx.x / T, t = threadIdx.x % T;
+    const int nitems = nres * G;
+    auto stage_e = [](int s) { return reinterpret_cast<float2 *>(sm + 128 + s * L::stage); };
+    auto stage_n = [](int s) { return reinterpret_cast<float *>(sm + 128 + s * L::stage + L::e_bytes); };
+    auto sync = []() { __syncthreads(); };
+    // Items of resonators that are done are skipped: no copy is issued for
+    // them and no barrier phase is consumed, so the stage parity follows the
+    // count of issued copies (`used`), not the item index.
+    auto issue = [&](int s, int item) {
+        const BatchRes &R = res[item / G];
+        const int grp = item % G;
+        mbar_arrive_expect_tx(&bar[s], (uint32_t)(LPC * N * (sizeof(float2) + sizeof(float))));
+        for (int l = 0; l < LPC; ++l) {
+            const size_t row = (size_t)grp * LPC + l;
+            bulk_g2s(stage_e(s) + l * LS, R.E + row * N, N * sizeof(float2), &bar[s]);
+            bulk_g2s(stage_n(s) + l * N, R.N + row * N, N * sizeof(float), &bar[s]);
+        }
+    };
+    auto next_active = [&](int from) {
+        for (int i = from; i < nitems; i += gridDim.x)
+            if (res_active(res[i / G])) return i;
+        return nitems;
+    };
+
+    init_stage_barriers(bar);
+    int item = next_active(blockIdx.x);
+    if (threadIdx.x == 0 && item < nitems) issue(0, item);
+    for (int it = 0; item < nitems; ++it) {
+        const int s = it & 1;
+        const int nxt = next_active(item + (int)gridDim.x);
+        if (threadIdx.x == 0 && nxt < nitems) {
+            fence_proxy_async_smem();
+            issue(s ^ 1, nxt);
+        }
+        if (stage_wait_or_abort(bar, it, nxt < nitems, err)) break;
+        const BatchRes &R = res[item / G];
+        const int grp = item % G;
+        const int row = grp * LPC + lig;
+        float2 *line = stage_e(s) + lig * LS;
+        float2 v[16];
+#pragma unroll
+        for (int si = 0; si < 16; ++si) v[si] = line[t + si * T];
+        float2 *extra = reinterpret_cast<float2 *>(sm + 128 + 2 * L::stage) + lig * LS;
+        LineBufs<float2, PP> lb{{PP ? extra : line, line}, 0};
+        diffract_line<LOGN, 1>(v, t, lb, tw, R.h, sync);
+        const GainParams<float> g = R.g;
+        const float *nrow = stage_n(s) + lig * N + t;
+        float2 *erow = R.E + (size_t)row * N + t;
+        float *ngl = R.N + (size_t)row * N + t;
+        float acc;
+        if (R.pe == PE_UNIFORM) acc = row_local_map<LOGN, PE_UNIFORM>(v, t, row, nrow, erow, ngl, g);
+        else if (R.pe == PE_TABLE) acc = row_local_map<LOGN, PE_TABLE>(v, t, row, nrow, erow, ngl, g);
+        else acc = row_local_map<LOGN, PE_SG10>(v, t, row, nrow, erow, ngl, g);
+        item_finish<NT>((double)acc, R.st, grp, G, 1.0 / ((double)N * (double)N));  // barriers inside
+        item = nxt;
+    }
+}
+
+// Column sweep over nres resonators: item i is tile i % (n/C) of resonator
+// i / (n/C), loaded through that resonator's tensor map.
+template <int LOGN, int C, bool PP = RTK_COL_PP>
+__global__ void __launch_bounds__(C * Plan<LOGN>::T,
+                                  col_min_blocks(C * Plan<LOGN>::T, ColStage<LOGN, C, PP>::total))
+k_col_tma_batch(const BatchRes *__restrict__ res, int nres, const float2 *__restrict__ tw, int *err)
+{
+    using P = Plan<LOGN>;
+    using L = ColStage<LOGN, C, PP>;
+    constexpr int N = P::N, T = P::T, TILES = N / C;
+    extern __shared__ __align__(128) unsigned char sm[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
+    const int c = threadIdx.x % C, t = threadIdx.x / C;
+    const int nitems = nres * TILES;
+    auto stage = [](int s) { return reinterpret_cast<float2 *>(sm + 128 + s * L::stage); };
+    auto sync = []() { __syncthreads(); };
+    auto issue = [&](int s, int item) {
+        const CUtensorMap *map = res[item / TILES].tmap;
+        const int tile = item % TILES;
+        mbar_arrive_expect_tx(&bar[s], (uint32_t)(N * C * sizeof(float2)));
+        for (int b = 0; b < L::NBOX; ++b)
+            tma_load_2d(stage(s) + b * L::BR * C, map, 2 * tile * C, b * L::BR, &bar[s]);
+    };
+
+    auto next_active = [&](int from) {
+        for (int i = from; i < nitems; i += gridDim.x)
+            if (res_active(res[i / TILES])) return i;
+        return nitems;
+    };
+
+    init_stage_barriers(bar);
+    int item = next_active(blockIdx.x);
+    if (threadIdx.x == 0 && item < nitems) issue(0, item);
+    for (int it = 0; item < nitems; ++it) {
+        const int s = it & 1;
+        const int nxt = next_active(item + (int)gridDim.x);
+        if (threadIdx.x == 0 && nxt < nitems) {
+            fence_proxy_async_smem();
+            issue(s ^ 1, nxt);
+        }
+        if (stage_wait_or_abort(bar, it, nxt < nitems, err)) break;
+        const BatchRes &R = res[item / TILES];
+        const int tile = item % TILES;
+        float2 *base = stage(s);
+        float2 v[16];
+#pragma unroll
+        for (int si = 0; si < 16; ++si) v[si] = base[(t + si * T) * C + c];
+        LineBufs<float2, PP> lb{{PP ? stage(2) + c : base + c, base + c}, 0};
+        diffract_line<LOGN, C>(v, t, lb, tw, R.h, sync);
+        float2 *col = R.E + (size_t)t * N + tile * C + c;
+#pragma unroll
+        for (int si = 0; si < 16; ++si) col[(size_t)si * T * N] = v[si];
+        __syncthreads();  // stage s fully consumed before it is refilled
+        item = nxt;
     }
 }
 

@@ -38,6 +38,13 @@ class rt_opts(ctypes.Structure):
                 ("history_cap", ctypes.c_longlong), ("chunk", ctypes.c_int), ("col_tile", ctypes.c_int)]
 
 
+class rt_job(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("fresnel", ctypes.c_double), ("g0", ctypes.c_double), ("T1", ctypes.c_double),
+                ("R", ctypes.c_double), ("pump", rt_pump), ("Isat", ctypes.c_double), ("edge_px", ctypes.c_int),
+                ("seed", ctypes.c_ulonglong), ("noise_amp", ctypes.c_double),
+                ("pump_diam_over_window", ctypes.c_double)]
+
+
 class rt_stats_t(ctypes.Structure):
     _fields_ = [("bounces", ctypes.c_longlong), ("mean_intensity", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("n", ctypes.c_int), ("precision", ctypes.c_int), ("last_error", ctypes.c_int),
@@ -74,6 +81,21 @@ def lib() -> ctypes.CDLL:
             "rt_destroy": [vp],
             "rt_step_noalloc": [i, d, ctypes.POINTER(rt_pump), d, d, d, ctypes.POINTER(rt_opts), vp, vp, ll,
                                 ctypes.POINTER(d)],
+            "rt_job_default": [ctypes.POINTER(rt_job), i],
+            "rt_batch_create": [ctypes.POINTER(rt_job), i, ctypes.POINTER(rt_opts), ctypes.POINTER(vp)],
+            "rt_batch_step": [vp, ll],
+            "rt_batch_sweep": [vp, i],
+            "rt_batch_set_job": [vp, i, ctypes.POINTER(rt_job), ll],
+            "rt_batch_sync": [vp],
+            "rt_batch_read_field": [vp, i, vp, sz],
+            "rt_batch_read_inversion": [vp, i, vp, sz],
+            "rt_batch_write_field": [vp, i, vp, sz],
+            "rt_batch_write_inversion": [vp, i, vp, sz],
+            "rt_batch_stats": [vp, i, ctypes.POINTER(rt_stats_t)],
+            "rt_batch_read_history": [vp, i, vp, ll, ctypes.POINTER(ll)],
+            "rt_batch_bounces": [vp, vp],
+            "rt_batch_footprint": [vp, ctypes.POINTER(sz)],
+            "rt_batch_destroy": [vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -291,6 +313,115 @@ class Resonator:
     def close(self):
         if self.h:
             rt_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ batches
+
+def rt_job_default(n: int) -> rt_job:
+    j = rt_job()
+    _check(lib().rt_job_default(ctypes.byref(j), n), "rt_job_default")
+    return j
+
+
+def job_from_params(p) -> rt_job:
+    """rt_job from a workloads.Resonator parameter record (super-Gaussian pump)."""
+    j = rt_job_default(p.n)
+    j.fresnel, j.g0, j.T1, j.R = p.fresnel, p.g0, p.T1, p.R
+    j.pump = rt_pump(kind=RT_PUMP_SUPERGAUSS, order=p.pump_order, radius=p.pump_radius, profile=None)
+    j.Isat, j.edge_px, j.seed, j.noise_amp, j.pump_diam_over_window = p.Isat, p.edge, p.seed, p.noise_amp, p.d_over_w
+    return j
+
+
+class Batch:
+    """Resonators stepped together (C ABI rt_batch_*): ``Batch(jobs, **opts)``
+    with jobs a list of rt_job or workloads.Resonator records; options are
+    rt_opts fields (cuda_stream, history_cap, chunk, col_tile)."""
+
+    def __init__(self, jobs, **opts):
+        js = [j if isinstance(j, rt_job) else job_from_params(j) for j in jobs]
+        self.n = [j.n for j in js]
+        arr = (rt_job * len(js))(*js)
+        o = rt_opts_default()
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
+        self.h = ctypes.c_void_p()
+        _check(lib().rt_batch_create(arr, len(js), ctypes.byref(o), ctypes.byref(self.h)), "rt_batch_create")
+
+    def __len__(self):
+        return len(self.n)
+
+    def step(self, n_bounces: int):
+        _check(lib().rt_batch_step(self.h, int(n_bounces)), "rt_batch_step")
+        return self
+
+    def sweep(self, which: int):
+        _check(lib().rt_batch_sweep(self.h, which), "rt_batch_sweep")
+
+    def set_job(self, i: int, job, n_bounces: int = -1):
+        j = job if isinstance(job, rt_job) else job_from_params(job)
+        _check(lib().rt_batch_set_job(self.h, i, ctypes.byref(j), int(n_bounces)), "rt_batch_set_job")
+
+    def sync(self):
+        _check(lib().rt_batch_sync(self.h), "rt_batch_sync")
+
+    def field(self, i: int) -> np.ndarray:
+        out = np.empty((self.n[i], self.n[i]), np.complex64)
+        _check(lib().rt_batch_read_field(self.h, i, out.ctypes.data, out.nbytes), "rt_batch_read_field")
+        return out
+
+    def inversion(self, i: int) -> np.ndarray:
+        out = np.empty((self.n[i], self.n[i]), np.float32)
+        _check(lib().rt_batch_read_inversion(self.h, i, out.ctypes.data, out.nbytes), "rt_batch_read_inversion")
+        return out
+
+    def write_field(self, i: int, src):
+        src = src if not isinstance(src, np.ndarray) else np.ascontiguousarray(src, np.complex64)
+        _check(lib().rt_batch_write_field(self.h, i, _ptr(src), _nbytes(src)), "rt_batch_write_field")
+
+    def write_inversion(self, i: int, src):
+        src = src if not isinstance(src, np.ndarray) else np.ascontiguousarray(src, np.float32)
+        _check(lib().rt_batch_write_inversion(self.h, i, _ptr(src), _nbytes(src)), "rt_batch_write_inversion")
+
+    def stats(self, i: int) -> rt_stats_t:
+        s = rt_stats_t()
+        _check(lib().rt_batch_stats(self.h, i, ctypes.byref(s)), "rt_batch_stats")
+        return s
+
+    def history(self, i: int, max_values: int) -> np.ndarray:
+        out = np.zeros(max(int(max_values), 0), np.float64)
+        got = ctypes.c_longlong()
+        _check(lib().rt_batch_read_history(self.h, i, out.ctypes.data if out.size else None, out.size,
+                                           ctypes.byref(got)), "rt_batch_read_history")
+        return out[: got.value]
+
+    def bounces(self) -> np.ndarray:
+        out = np.zeros(len(self.n), np.int64)
+        _check(lib().rt_batch_bounces(self.h, out.ctypes.data), "rt_batch_bounces")
+        return out
+
+    def footprint(self) -> int:
+        b = ctypes.c_size_t()
+        _check(lib().rt_batch_footprint(self.h, ctypes.byref(b)), "rt_batch_footprint")
+        return b.value
+
+    def close(self):
+        if self.h:
+            lib().rt_batch_destroy(self.h)
             self.h = None
 
     def __enter__(self):
