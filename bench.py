@@ -290,6 +290,35 @@ def torch_cufft_rate(p, steps=100):
     return steps / (s.elapsed_time(e) / 1e3)
 
 
+def serve_replay(rt, stream, count=40, rate_hz=50.0):
+    """Replay the first `count` requests of the seeded Poisson stream (mean
+    rate_hz; sides 128..2048, bounces log-uniform in [1e3, 1e5]) against a
+    server with 500-bounce rounds and an 8 GiB budget; latency is completion
+    minus submission on the server clock."""
+    trace = wl.serve_trace(count=count, rate_hz=rate_hz)
+    with rt.Server(chunk=500, budget_bytes=8 << 30, cuda_stream=stream.cuda_stream) as srv:
+        t0 = time.perf_counter()
+        for req in trace:
+            delay = t0 + req.arrival_s - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            srv.submit(req.job, req.bounces)
+        srv.drain(1800.0)
+        res = srv.poll(4 * count)
+        st = srv.stats()
+    lat = sorted(r.finish_s - r.submit_s for r in res)
+    work = sum(float(r.n) ** 2 * r.bounces for r in res)
+    span = max(r.finish_s for r in res) - min(r.submit_s for r in res)
+    offered = sum(float(q.job.n) ** 2 * q.bounces for q in trace) / max(trace[-1].arrival_s, 1e-9)
+    return {"workload": f"first {count} requests of a Poisson stream at {rate_hz:g} req/s, sides uniform over "
+                        "{128,...,2048}, bounces log-uniform in [1e3,1e5]; 500-bounce rounds, 8 GiB budget",
+            "requests": len(res), "failed": sum(1 for r in res if r.status != 0),
+            "p50_latency_s": lat[len(lat) // 2], "p99_latency_s": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "round_trips_per_s": sum(r.bounces for r in res) / span,
+            "served_point_bounces_per_s": work / span, "offered_point_bounces_per_s": offered,
+            "rounds": st.rounds}
+
+
 def run_ours(args):
     import torch
     from paper_1410_2855_gb300 import build, rt
@@ -475,6 +504,9 @@ def comparisons(args, rt, torch, main, streams, params, res, E0, N0, rank, world
                             "g0 U[0.1,0.3], T1 U[1e3,1e4], R=0.95; one CUDA graph per 100 bounces",
                 "round_trips_per_s": len(jobs) * 200 / secs, "point_bounces_per_s": Pb * 200 / secs,
                 "hbm_frac": 40 * Pb * 200 / secs / 1e9 / peak, "footprint_bytes": bt.footprint()}
+
+    # ---- serving: a bounded replay of the Poisson request stream
+    extra["serve"] = serve_replay(rt, main)
 
     # ---- plain FP64 GPU path on the same GPU (unfused, six sweeps per bounce)
     p = params[1]

@@ -234,6 +234,66 @@ rt_status rt_batch_footprint(rt_batch *b, size_t *bytes);
 
 rt_status rt_batch_destroy(rt_batch *b);
 
+/* ---- serving: continuous batching of simulation requests -----------------
+ * A server owns one GPU stream and a device-memory budget.  Requests (a job
+ * and a bounce count) may be submitted at any time from any thread.  A
+ * worker thread runs scheduling rounds: it admits queued requests (oldest
+ * first) while their footprint fits the budget, runs `chunk` bounces of
+ * every resident request in shared batched launches (requests of one grid
+ * size share each launch; a request stops exactly at its own bounce count),
+ * then retires finished requests, copying each final field to the buffer
+ * given at submission.  State stays on the device between rounds.  A
+ * request's result is the same as running it alone on a handle. */
+typedef struct rt_server rt_server;
+
+typedef struct {
+    long long budget_bytes;   /* device memory for resident requests (8 GiB) */
+    int chunk;                /* bounces per scheduling round (500) */
+    int max_per_size;         /* resident requests of one grid size at most (128) */
+    void *cuda_stream;        /* stream to run on; NULL = the server creates its own */
+} rt_serve_opts;
+
+typedef struct {
+    long long id;             /* from rt_serve_submit */
+    int status;               /* RT_OK, or the error that ended the request */
+    int n;                    /* grid side */
+    long long bounces;        /* bounces run */
+    double mean_intensity;    /* <|E|^2> after the last bounce */
+    double submit_s;          /* server clock (seconds since creation): submission */
+    double admit_s;           /* admission (first round that ran it) */
+    double finish_s;          /* completion (its field copied out) */
+} rt_result;
+
+typedef struct {
+    long long submitted, queued, running, done;
+    long long resident_bytes;          /* device bytes held for requests */
+    double point_bounces;              /* sum over finished rounds of n^2 x bounces run */
+    double busy_s;                     /* wall time spent in scheduling rounds */
+    long long rounds;
+} rt_serve_stats_t;
+
+rt_status rt_serve_opts_default(rt_serve_opts *opts);
+rt_status rt_serve_create(const rt_serve_opts *opts, rt_server **out);
+
+/* Queue a request of n_bounces (> 0) bounces of `job` (32 <= n <= 2048,
+ * super-Gaussian order-10 or uniform pump).  field_out (host or device,
+ * n*n complex64, may be NULL) receives the final field before the result is
+ * posted; it must stay valid until then.  *id receives the request id.
+ * RT_EINVAL for bad jobs or a request that could never fit the budget. */
+rt_status rt_serve_submit(rt_server *s, const rt_job *job, long long n_bounces, void *field_out, long long *id);
+
+/* Move up to `max` finished results into out (oldest first); *got = count. */
+rt_status rt_serve_poll(rt_server *s, rt_result *out, int max, int *got);
+
+/* Wait until every submitted request has finished or `timeout_s` passes
+ * (RT_ETIMEOUT). */
+rt_status rt_serve_drain(rt_server *s, double timeout_s);
+
+rt_status rt_serve_stats(rt_server *s, rt_serve_stats_t *out);
+
+/* Stop the worker (queued requests are dropped) and free everything. */
+rt_status rt_serve_destroy(rt_server *s);
+
 /* ---- allocation-free stepping ------------------------------------------
  * The paper has no counterpart to this entry point.  It exists for callers
  * that cannot call cudaMalloc: a host that hands the library device buffers

@@ -1,0 +1,172 @@
+// Slot set-up shared by batches and the server (engine.h).
+#include <climits>
+#include <cmath>
+#include <cstring>
+
+#include "engine.h"
+
+namespace rtk {
+
+namespace {
+size_t al256(size_t b) { return (b + 255) / 256 * 256; }
+bool fpos(double v) { return std::isfinite(v) && v > 0.0; }
+}  // namespace
+
+int log2_of(int n)
+{
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+
+bool job_ok(const rt_job &j)
+{
+    if (j.n < 32 || j.n > 2048 || (j.n & (j.n - 1))) return false;
+    if (!fpos(j.fresnel) || !std::isfinite(j.g0) || j.g0 < 0.0 || !std::isfinite(j.T1) || j.T1 < 1.0) return false;
+    if (!std::isfinite(j.R) || j.R <= 0.0 || j.R > 1.0) return false;
+    if (!fpos(j.Isat) || j.edge_px < 0 || j.edge_px > j.n / 2 || !fpos(j.pump_diam_over_window)) return false;
+    if (!std::isfinite(j.noise_amp) || j.noise_amp < 0.0) return false;
+    if (j.pump.kind < RT_PUMP_SUPERGAUSS || j.pump.kind > RT_PUMP_ARRAY) return false;
+    if (j.pump.kind == RT_PUMP_SUPERGAUSS && (!fpos(j.pump.order) || !fpos(j.pump.radius))) return false;
+    if (j.pump.kind == RT_PUMP_ARRAY && !j.pump.profile) return false;
+    return true;
+}
+
+int pump_eval(const rt_pump &p)
+{
+    return p.kind == RT_PUMP_UNIFORM ? PE_UNIFORM
+                                     : ((p.kind == RT_PUMP_SUPERGAUSS && p.order == 10.0) ? PE_SG10 : PE_TABLE);
+}
+
+double job_alpha(const rt_job &j) { return j.pump_diam_over_window * j.pump_diam_over_window / j.fresnel; }
+
+namespace {
+void slot_layout(int n, long long hist_cap, bool table, size_t off[7], size_t *total)
+{
+    const size_t N = (size_t)n, P = N * N, cap = hist_cap > 0 ? (size_t)hist_cap : 0;
+    const size_t sz[7] = {al256(P * sizeof(float2)),                                  // E
+                          al256(P * sizeof(float)),                                   // N
+                          al256(N * sizeof(float2)),                                  // h
+                          al256((size_t)row_groups32(log2_of(n)) * sizeof(double)),  // part
+                          al256(cap * sizeof(double)),                                // history
+                          al256(sizeof(CUtensorMap)),                                 // tensor map
+                          table ? al256(P * sizeof(float)) : 0};                      // N0 table
+    size_t t = 0;
+    for (int k = 0; k < 7; ++k) {
+        off[k] = t;
+        t += sz[k];
+    }
+    *total = t;
+}
+}  // namespace
+
+size_t slot_bytes(int n, long long hist_cap, bool table)
+{
+    size_t off[7], t;
+    slot_layout(n, hist_cap, table, off, &t);
+    return t;
+}
+
+cudaError_t slot_alloc(int n, long long hist_cap, bool table, SlotBufs *out)
+{
+    size_t off[7], total;
+    slot_layout(n, hist_cap, table, off, &total);
+    SlotBufs b;
+    cudaError_t e = cudaMalloc(&b.mem, total);
+    if (e != cudaSuccess) return e;
+    b.bytes = total;
+    b.E = reinterpret_cast<float2 *>(b.mem + off[0]);
+    b.N = reinterpret_cast<float *>(b.mem + off[1]);
+    b.h = reinterpret_cast<float2 *>(b.mem + off[2]);
+    b.part = reinterpret_cast<double *>(b.mem + off[3]);
+    b.hist = hist_cap > 0 ? reinterpret_cast<double *>(b.mem + off[4]) : nullptr;
+    b.tmap = reinterpret_cast<CUtensorMap *>(b.mem + off[5]);
+    b.pump_tab = table ? reinterpret_cast<float *>(b.mem + off[6]) : nullptr;
+    *out = b;
+    return cudaSuccess;
+}
+
+void slot_free(SlotBufs *b)
+{
+    if (b->mem) cudaFree(b->mem);
+    *b = SlotBufs();
+}
+
+BatchRes slot_descriptor(const rt_job &job, const SlotBufs &b, SlotCtl *ctl, long long hist_cap, long long target)
+{
+    BatchRes r{};
+    r.E = b.E;
+    r.N = b.N;
+    r.h = b.h;
+    r.tmap = b.tmap;
+    const int pe = pump_eval(job.pump);
+    GainParams<float> &g = r.g;
+    g.sqrtR = (float)std::sqrt(job.R);
+    g.invT1 = (float)(1.0 / job.T1);
+    g.invIsat = (float)(1.0 / job.Isat);
+    g.g0 = (float)job.g0;
+    g.inv_rp2 = job.pump.kind == RT_PUMP_SUPERGAUSS ? (float)(1.0 / (job.pump.radius * job.pump.radius)) : 0.0f;
+    g.half_order = (float)(0.5 * job.pump.order);
+    g.int_half_order = pe == PE_SG10 ? 5 : 0;
+    g.edge = job.edge_px;
+    g.pump_kind = job.pump.kind;
+    g.pump_tab = b.pump_tab;
+    r.pe = pe;
+    r.target = target;
+    r.st.part = b.part;
+    r.st.count = &ctl->count;
+    r.st.hist = b.hist;
+    r.st.hist_cap = b.hist ? hist_cap : 0;
+    r.st.bounce = &ctl->bounce;
+    r.st.last_mean = &ctl->last_mean;
+    r.st.err = &ctl->err;
+    return r;
+}
+
+cudaError_t slot_start(const rt_job &job, const SlotBufs &b, int colC, float2 *class_tw, SlotCtl *ctl,
+                       BatchRes *d_desc, long long hist_cap, long long target, cudaStream_t s)
+{
+    const int n = job.n;
+    const size_t P = (size_t)n * n;
+    cudaError_t e;
+    if ((e = launch_tables32(n, job_alpha(job), class_tw, b.h, s)) != cudaSuccess) return e;
+    if ((e = launch_noise32(n, job.seed, job.noise_amp, b.E, s)) != cudaSuccess) return e;
+    double *profile = nullptr;
+    if (job.pump.kind == RT_PUMP_ARRAY) {
+        if ((e = cudaMallocAsync(reinterpret_cast<void **>(&profile), P * sizeof(double), s)) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(profile, job.pump.profile, P * sizeof(double), cudaMemcpyDefault, s)) != cudaSuccess)
+            return e;
+    }
+    e = launch_pump32(n, job.pump.kind, job.g0, job.pump.order, job.pump.radius, profile, b.N, s);
+    if (profile) cudaFreeAsync(profile, s);
+    if (e != cudaSuccess) return e;
+    if (pump_eval(job.pump) == PE_TABLE) {
+        if (!b.pump_tab) return cudaErrorInvalidValue;
+        if ((e = cudaMemcpyAsync(b.pump_tab, b.N, P * sizeof(float), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+            return e;
+    }
+    alignas(64) unsigned char map[128];
+    if ((e = make_col_tensor_map(map, b.E, n, colC)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(b.tmap, map, sizeof(map), cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ctl, 0, sizeof(SlotCtl), s)) != cudaSuccess) return e;
+    const BatchRes r = slot_descriptor(job, b, ctl, hist_cap, target);
+    return cudaMemcpyAsync(d_desc, &r, sizeof(r), cudaMemcpyHostToDevice, s);
+}
+
+cudaError_t slot_set_target(BatchRes *d_desc, long long target, cudaStream_t s)
+{
+    // The host value is staged before cudaMemcpyAsync returns (pageable source).
+    return cudaMemcpyAsync(&d_desc->target, &target, sizeof(target), cudaMemcpyHostToDevice, s);
+}
+
+cudaError_t enqueue_classes_bounce(const std::vector<ClassLaunch> &cls, int *err, cudaStream_t s)
+{
+    cudaError_t e;
+    for (const ClassLaunch &c : cls)
+        if ((e = launch_col_batch32(c.logn, c.colC, c.d_res, c.nres, c.tw, err, s)) != cudaSuccess) return e;
+    for (const ClassLaunch &c : cls)
+        if ((e = launch_row_batch32(c.logn, c.d_res, c.nres, c.tw, err, s)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+}  // namespace rtk

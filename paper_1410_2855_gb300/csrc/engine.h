@@ -1,0 +1,87 @@
+// Host-side engine shared by batches and the server: one resonator "slot"
+// (its device buffers, counters and batched-launch descriptor) and the size
+// classes that group slots of one grid size into shared launches.
+#pragma once
+
+#include <vector>
+
+#include "rt.h"
+#include "rt_internal.h"
+
+namespace rtk {
+
+// Per-slot device counters (one 64-byte line each).
+struct SlotCtl {
+    unsigned int count;  // arrival counter of the row-sweep reduction
+    int err;             // sticky error (RT_ENUMERIC)
+    long long bounce;    // bounces done since the slot's job started
+    double last_mean;    // mean intensity after the last bounce
+    long long pad[5];
+};
+static_assert(sizeof(SlotCtl) == 64, "slot control block is one line");
+
+// Device buffers of one slot, carved from one allocation.
+struct SlotBufs {
+    unsigned char *mem = nullptr;
+    size_t bytes = 0;
+    float2 *E = nullptr;
+    float *N = nullptr;
+    float2 *h = nullptr;
+    double *part = nullptr;
+    double *hist = nullptr;
+    CUtensorMap *tmap = nullptr;
+    float *pump_tab = nullptr;
+};
+
+bool job_ok(const rt_job &j);            // 32 <= n <= 2048 and parameters in range
+int pump_eval(const rt_pump &p);         // PumpEval of a job's pump
+double job_alpha(const rt_job &j);       // lambda z / W^2 = (D/W)^2 / N_F
+int log2_of(int n);
+
+// Bytes and allocation of a slot for side n (table: N0 table for PE_TABLE).
+size_t slot_bytes(int n, long long hist_cap, bool table);
+cudaError_t slot_alloc(int n, long long hist_cap, bool table, SlotBufs *out);
+void slot_free(SlotBufs *b);
+
+// Descriptor of a slot for the batched kernels.
+BatchRes slot_descriptor(const rt_job &job, const SlotBufs &b, SlotCtl *ctl, long long hist_cap, long long target);
+
+// Start `job` in a slot (as rt_create starts a handle): propagator table,
+// class twiddles, noise field, N = N0, tensor map, zeroed counters, and the
+// descriptor written to *d_desc.  All on stream s.
+cudaError_t slot_start(const rt_job &job, const SlotBufs &b, int colC, float2 *class_tw, SlotCtl *ctl,
+                       BatchRes *d_desc, long long hist_cap, long long target, cudaStream_t s);
+
+// Set only the bounce target of a slot's descriptor (stops or idles it).
+cudaError_t slot_set_target(BatchRes *d_desc, long long target, cudaStream_t s);
+
+// Grid sizes of one persistent batched launch set.
+struct ClassLaunch {
+    int logn, colC;
+    const BatchRes *d_res;
+    int nres;
+    const float2 *tw;
+};
+
+// One bounce of every class: all column sweeps, then all row sweeps.
+cudaError_t enqueue_classes_bounce(const std::vector<ClassLaunch> &cls, int *err, cudaStream_t s);
+
+// Device index guard.
+struct DeviceGuard {
+    int prev = -1, want;
+    explicit DeviceGuard(int d) : want(d)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != want) cudaSetDevice(want);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0 && prev != want) cudaSetDevice(prev);
+    }
+};
+
+inline rt_status cuda_to_status(cudaError_t e)
+{
+    return e == cudaSuccess ? RT_OK : (e == cudaErrorMemoryAllocation ? RT_ENOMEM : RT_ECUDA);
+}
+
+}  // namespace rtk

@@ -80,6 +80,21 @@ __device__ __forceinline__ bool res_active(const BatchRes &R)
     return __ldcg(R.st.bounce) < R.target;
 }
 
+// First item >= i on this block's stride (items congruent to blockIdx.x
+// modulo gridDim.x) that belongs to an active resonator; a finished
+// resonator is skipped in one step.  `per` items per resonator.
+__device__ __forceinline__ int next_active_item(const BatchRes *__restrict__ res, int per, int nitems, int i)
+{
+    const int grid = gridDim.x, b = blockIdx.x;
+    while (i < nitems) {
+        const int r = i / per;
+        if (res_active(res[r])) return i;
+        const int first = (r + 1) * per;
+        i = first + (int)((((long long)b - first) % grid + grid) % grid);
+    }
+    return nitems;
+}
+
 // ---- shared pieces ----------------------------------------------------------
 
 // Bounded wait on a stage barrier; on a timeout the block drains the copy
@@ -338,11 +353,7 @@ k_row_tma_batch(const BatchRes *__restrict__ res, int nres, const float2 *__rest
             bulk_g2s(stage_n(s) + l * N, R.N + row * N, N * sizeof(float), &bar[s]);
         }
     };
-    auto next_active = [&](int from) {
-        for (int i = from; i < nitems; i += gridDim.x)
-            if (res_active(res[i / G])) return i;
-        return nitems;
-    };
+    auto next_active = [&](int i) { return next_active_item(res, G, nitems, i); };
 
     init_stage_barriers(bar);
     int item = next_active(blockIdx.x);
@@ -402,11 +413,7 @@ k_col_tma_batch(const BatchRes *__restrict__ res, int nres, const float2 *__rest
             tma_load_2d(stage(s) + b * L::BR * C, map, 2 * tile * C, b * L::BR, &bar[s]);
     };
 
-    auto next_active = [&](int from) {
-        for (int i = from; i < nitems; i += gridDim.x)
-            if (res_active(res[i / TILES])) return i;
-        return nitems;
-    };
+    auto next_active = [&](int i) { return next_active_item(res, TILES, nitems, i); };
 
     init_stage_barriers(bar);
     int item = next_active(blockIdx.x);

@@ -45,6 +45,23 @@ class rt_job(ctypes.Structure):
                 ("pump_diam_over_window", ctypes.c_double)]
 
 
+class rt_serve_opts(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_longlong), ("chunk", ctypes.c_int), ("max_per_size", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class rt_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("status", ctypes.c_int), ("n", ctypes.c_int),
+                ("bounces", ctypes.c_longlong), ("mean_intensity", ctypes.c_double), ("submit_s", ctypes.c_double),
+                ("admit_s", ctypes.c_double), ("finish_s", ctypes.c_double)]
+
+
+class rt_serve_stats_t(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("queued", ctypes.c_longlong), ("running", ctypes.c_longlong),
+                ("done", ctypes.c_longlong), ("resident_bytes", ctypes.c_longlong),
+                ("point_bounces", ctypes.c_double), ("busy_s", ctypes.c_double), ("rounds", ctypes.c_longlong)]
+
+
 class rt_stats_t(ctypes.Structure):
     _fields_ = [("bounces", ctypes.c_longlong), ("mean_intensity", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("n", ctypes.c_int), ("precision", ctypes.c_int), ("last_error", ctypes.c_int),
@@ -96,6 +113,13 @@ def lib() -> ctypes.CDLL:
             "rt_batch_bounces": [vp, vp],
             "rt_batch_footprint": [vp, ctypes.POINTER(sz)],
             "rt_batch_destroy": [vp],
+            "rt_serve_opts_default": [ctypes.POINTER(rt_serve_opts)],
+            "rt_serve_create": [ctypes.POINTER(rt_serve_opts), ctypes.POINTER(vp)],
+            "rt_serve_submit": [vp, ctypes.POINTER(rt_job), ll, vp, ctypes.POINTER(ll)],
+            "rt_serve_poll": [vp, ctypes.POINTER(rt_result), i, ctypes.POINTER(i)],
+            "rt_serve_drain": [vp, d],
+            "rt_serve_stats": [vp, ctypes.POINTER(rt_serve_stats_t)],
+            "rt_serve_destroy": [vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -422,6 +446,75 @@ class Batch:
     def close(self):
         if self.h:
             lib().rt_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ serving
+
+def rt_serve_opts_default() -> rt_serve_opts:
+    o = rt_serve_opts()
+    _check(lib().rt_serve_opts_default(ctypes.byref(o)), "rt_serve_opts_default")
+    return o
+
+
+class Server:
+    """Continuous-batching server (C ABI rt_serve_*).  ``Server(**opts)`` with
+    rt_serve_opts fields (budget_bytes, chunk, max_per_size, cuda_stream)."""
+
+    def __init__(self, **opts):
+        o = rt_serve_opts_default()
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
+        self.h = ctypes.c_void_p()
+        _check(lib().rt_serve_create(ctypes.byref(o), ctypes.byref(self.h)), "rt_serve_create")
+        self._keep = {}
+
+    def submit(self, job, n_bounces: int, field_out=None) -> int:
+        """Queue a request; field_out (numpy complex64 n x n or a device
+        tensor) receives the final field."""
+        j = job if isinstance(job, rt_job) else job_from_params(job)
+        rid = ctypes.c_longlong()
+        _check(lib().rt_serve_submit(self.h, ctypes.byref(j), int(n_bounces),
+                                     _ptr(field_out) if field_out is not None else None, ctypes.byref(rid)),
+               "rt_serve_submit")
+        if field_out is not None:
+            self._keep[rid.value] = field_out
+        return rid.value
+
+    def poll(self, max_results: int = 1024):
+        buf = (rt_result * max_results)()
+        got = ctypes.c_int()
+        _check(lib().rt_serve_poll(self.h, buf, max_results, ctypes.byref(got)), "rt_serve_poll")
+        out = [buf[k] for k in range(got.value)]
+        for r in out:
+            self._keep.pop(r.id, None)
+        return out
+
+    def drain(self, timeout_s: float = 600.0):
+        _check(lib().rt_serve_drain(self.h, float(timeout_s)), "rt_serve_drain")
+
+    def stats(self) -> rt_serve_stats_t:
+        s = rt_serve_stats_t()
+        _check(lib().rt_serve_stats(self.h, ctypes.byref(s)), "rt_serve_stats")
+        return s
+
+    def close(self):
+        if self.h:
+            lib().rt_serve_destroy(self.h)
             self.h = None
 
     def __enter__(self):
