@@ -1,0 +1,62 @@
+"""Write tests/golden/longrun_512.json: the FP64 oracle's long run of the
+512^2 resonator (N_F = 100, g0 = 0.15, T1 = 5000, R = 0.95, super-Gaussian
+pump of order 10 and radius 0.8, 8-pixel edge, splitmix64 noise start of
+amplitude 1e-6, 1e4 bounces).
+
+Beyond a few tens of bounces the map is chaotic, so the stored values are
+statistics that a faithful FP32 run must reproduce rather than the field
+itself: the mean intensity averaged over the last 1000 bounces, the mean
+intensity every 100 bounces, and the dominant spatial frequency of the final
+field (all bins, and bins with max(|mx|, |my|) >= 2), with m and -m folded.
+
+Calls only the oracle:  python tests/golden/make_longrun.py [threads]
+"""
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import oracle as orc  # noqa: E402
+from paper_1410_2855_gb300 import workloads as wl  # noqa: E402
+
+
+def main():
+    threads = int(sys.argv[1]) if len(sys.argv) > 1 else (os.cpu_count() or 1)
+    c, nb = wl.C2, wl.C2_BOUNCES
+    p = orc.make_params(c.n, orc.alpha_from_fresnel(c.fresnel, c.d_over_w), c.g0, c.T1, c.R, Isat=c.Isat,
+                        edge=c.edge, pump_order=c.pump_order, pump_radius=c.pump_radius)
+    E, N = orc.init_state(p, c.seed, c.noise_amp)
+    t0 = time.time()
+    E, N, hist = orc.run(p, E, N, nb, nthreads=threads)
+    S = orc.spectrum(E, nthreads=threads)
+    peaks = {}
+    for ring in (0, 2):
+        mx, my, pw, ru = orc.spectrum_peak(S, ring)
+        peaks[str(ring)] = {"mx": mx, "my": my, "power": pw, "runner_up": ru}
+    out = {
+        "_source": "FP64 oracle (oracle/bouncemap_oracle.c), written by tests/golden/make_longrun.py",
+        "resonator": {"n": c.n, "fresnel": c.fresnel, "g0": c.g0, "T1": c.T1, "R": c.R, "Isat": c.Isat,
+                      "edge": c.edge, "pump_order": c.pump_order, "pump_radius": c.pump_radius,
+                      "d_over_w": c.d_over_w, "seed": c.seed, "noise_amp": c.noise_amp},
+        "bounces": nb,
+        "mean_intensity_last_1000": float(np.mean(hist[-1000:])),
+        "mean_intensity_every_100": [float(v) for v in hist[99::100]],
+        "final_mean_intensity": float(hist[-1]),
+        "final_mean_inversion": float(np.mean(N)),
+        "peaks": peaks,
+        "oracle_seconds": round(time.time() - t0, 1),
+        "threads": threads,
+    }
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "longrun_512.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    print(path, out["mean_intensity_last_1000"], out["peaks"])
+
+
+if __name__ == "__main__":
+    main()

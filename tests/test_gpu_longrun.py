@@ -1,0 +1,35 @@
+"""Long horizon: the 512^2 resonator (N_F = 100, g0 = 0.15, T1 = 5000,
+R = 0.95) run for 1e4 bounces from the seeded noise start.  The map is
+chaotic well before that, so the FP32 and FP64 GPU paths are held to the
+statistics the FP64 oracle fixed in tests/golden/longrun_512.json (written
+by tests/golden/make_longrun.py): the mean intensity over the last 1000
+bounces within 1%, and the dominant spatial frequency (m and -m folded)
+exactly, unless the oracle's runner-up is within 1e-3 of its peak."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1410_2855_gb300 import build, rt, workloads as wl
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "longrun_512.json")
+
+
+@pytest.mark.parametrize("precision", [rt.RT_FP32, rt.RT_FP64])
+def test_long_run_statistics_match_oracle(precision):
+    build.build()
+    g = json.load(open(GOLDEN))
+    c = wl.C2
+    with rt.Resonator.from_params(c, precision=precision, history_cap=20000, chunk=500) as r:
+        r.step(g["bounces"])
+        hist = r.history(g["bounces"])
+        peaks = {ring: r.peak(ring) for ring in (0, 2)}
+    assert len(hist) == g["bounces"] and np.all(np.isfinite(hist))
+    mean = float(np.mean(hist[-1000:]))
+    assert abs(mean / g["mean_intensity_last_1000"] - 1.0) <= 0.01
+    for ring, (mx, my, pw) in peaks.items():
+        ref = g["peaks"][str(ring)]
+        tie = ref["runner_up"] >= (1.0 - 1e-3) * ref["power"]
+        assert tie or (mx, my) == (ref["mx"], ref["my"]), (ring, mx, my, ref)
