@@ -333,6 +333,8 @@ def run_ours(args):
     main = torch.cuda.Stream(device=dev)
     B, K, W = args.bounces_per_step, args.steps, args.warmup
     params = workload(rank)
+    from paper_1410_2855_gb300 import tune
+    col_tile, col_us = tune.rt_autotune(params[0].n, reps=50)   # column-sweep tile width for this GPU
     streams = [torch.cuda.Stream(device=dev) for _ in params]
     res = [rt.Resonator.from_params(p, precision=rt.RT_FP32, cuda_stream=s.cuda_stream, chunk=B)
            for p, s in zip(params, streams)]
@@ -408,7 +410,8 @@ def run_ours(args):
         "config": config_block(B, {"l2": "flushed between steps (256 MiB write); each resonator's 48 MiB state "
                                          "stays L2-resident within a step",
                                    "graph": f"one CUDA graph per {B} bounces per resonator",
-                                   "streams": "one per resonator, concurrent"}),
+                                   "streams": "one per resonator, concurrent",
+                                   "col_tile": col_tile, "col_tile_source": "autotuned at start-up"}),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": dom_gbs, "peak": peak, "unit": "GB/s",
                      "frac": dom_gbs / peak, "peak_kind": f"of {peak_kind}",
                      "traffic": profiled_traffic(dom, params[0].n),

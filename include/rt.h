@@ -169,6 +169,21 @@ rt_status rt_read_spectrum(rt_handle *h, void *dst, size_t bytes);
  * Writes the signed (mx, my) and the folded power. Blocks. */
 rt_status rt_spectrum_peak(rt_handle *h, int ring, int *mx, int *my, double *power);
 
+/* ---- autotuning ---------------------------------------------------------
+ * The column sweep's tile width (columns per block: 2, 4, 8 or 16) trades
+ * load balance and copy-engine box width against shared memory and
+ * occupancy.  rt_autotune times the sweep of a scratch n x n FP32 resonator
+ * on the current device for every width that fits (reps launches each,
+ * CUDA events) and records the fastest for this process; handles, batches
+ * and servers created afterwards with col_tile = 0 use it.  rt_tune_set
+ * records a width directly (e.g. loaded from a JSON cache file by the
+ * Python binding); rt_tune_get reports the width in use for n (tuned, or
+ * the built-in default; *tuned says which).  Not part of the paper's
+ * method. */
+rt_status rt_autotune(int n, int reps, int *best_col_tile, double *best_us);
+rt_status rt_tune_set(int n, int col_tile);
+rt_status rt_tune_get(int n, int *col_tile, int *tuned);
+
 /* ---- batches of resonators ---------------------------------------------
  * Many independent resonators (eq. conv_map per resonator, each with its
  * own grid size, Fresnel number, pump, gain, T1, R) stepped together: the

@@ -158,7 +158,30 @@ template <int LOGN> static int col_ok32(int colC)
 
 int col_tile_ok32(int logn, int colC) { RTK_LOGN_CASES(col_ok32, colC) }
 
-int default_col_tile32(int logn) { return logn >= 12 ? 2 : (logn >= 11 ? 4 : (logn >= 10 ? 8 : 16)); }
+// Tile widths chosen by the autotuner (0: not tuned), per log2 n.
+static std::atomic<int> g_tuned_col[13];
+
+// Built-in widths: the autotuner's choices on GB300 (2 at 4096, 4 at
+// 1024-2048, 8 below; 16 only where 8 does not fit a whole warp's rows).
+int builtin_col_tile32(int logn) { return logn >= 12 ? 2 : (logn >= 10 ? 4 : (logn >= 6 ? 8 : 16)); }
+
+int default_col_tile32(int logn)
+{
+    if (logn >= 0 && logn < 13) {
+        const int t = g_tuned_col[logn].load();
+        if (t > 0 && col_tile_ok32(logn, t)) return t;
+    }
+    return builtin_col_tile32(logn);
+}
+
+int set_tuned_col_tile32(int logn, int colC)
+{
+    if (logn < 5 || logn > 12 || (colC != 0 && !col_tile_ok32(logn, colC))) return 0;
+    g_tuned_col[logn].store(colC);
+    return 1;
+}
+
+int tuned_col_tile32(int logn) { return (logn >= 0 && logn < 13) ? g_tuned_col[logn].load() : 0; }
 
 // ---- row sweep (diffraction along x + local map) --------------------------------
 

@@ -123,15 +123,6 @@ GainParams<R> gain_params(rt_handle *h)
     return g;
 }
 
-// Default column-tile width of the FP32 column sweep.
-int default_col_c(int logn)
-{
-    if (logn >= 12) return 2;
-    if (logn >= 11) return 4;
-    if (logn >= 10) return 8;
-    return 16;
-}
-
 cudaError_t enqueue_bounce(rt_handle *h, cudaStream_t s)
 {
     const StatParams st = stat_params(h);
@@ -307,7 +298,7 @@ rt_status rt_create(int n, double fresnel, const rt_pump *pump, double g0, doubl
     h->pump = p;
     h->pump.profile = nullptr;
     h->stream = static_cast<cudaStream_t>(o.cuda_stream);
-    h->colC = o.col_tile ? o.col_tile : default_col_c(h->logn);
+    h->colC = o.col_tile ? o.col_tile : default_col_tile32(h->logn);
     // N0 on the fly for the order-10 super-Gaussian and the uniform pump, else from a table
     h->pe = p.kind == RT_PUMP_UNIFORM ? 1 : ((p.kind == RT_PUMP_SUPERGAUSS && p.order == 10.0) ? 0 : 2);
     cudaGetDevice(&h->device);

@@ -91,7 +91,10 @@ int row_blocks32(int logn);            // blocks of the row sweep (size of StatP
 cudaError_t prepare_bounce32(int logn, int colC, int pe);
 cudaError_t prepare_bounce64(int logn);
 int col_tile_ok32(int logn, int colC); // 1 if that column tile width is instantiated and fits
-int default_col_tile32(int logn);      // column tile width used when none is requested
+int default_col_tile32(int logn);      // column tile width used when none is requested (tuned or built in)
+int builtin_col_tile32(int logn);      // the built-in choice
+int set_tuned_col_tile32(int logn, int colC);  // record a tuned width (0 clears); 1 on success
+int tuned_col_tile32(int logn);        // tuned width or 0
 
 // Forward 2-D transform helpers (spectrum readout), FP32: rows out of place, columns in place.
 cudaError_t launch_row_fft32(int logn, const float2 *in, float2 *out, const float2 *tw, int dir, cudaStream_t s);
