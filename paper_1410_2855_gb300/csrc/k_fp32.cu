@@ -190,7 +190,7 @@ static cudaError_t row_tma32_pe(float2 *E, float *N, const float2 *tw, const flo
                                 const StatParams &st, cudaStream_t s)
 {
     constexpr int LPC = tma_lpc<LOGN>();
-    using L = RowStage<LOGN, LPC, RTK_ROW_PP>;
+    using L = RowStage<LOGN, LPC, RTK_ROW_PP, PE == PE_TABLE>;
     auto k = k_row_tma<LOGN, LPC, PE>;
     static std::atomic<unsigned long long> mask{0};
     static std::atomic<int> per_sm{0};
@@ -397,7 +397,8 @@ template <int LOGN, int PE> static cudaError_t row_prep32()
 {
     if constexpr (RTK_PERSISTENT) {
         static std::atomic<unsigned long long> mask{0};
-        return ensure_smem(k_row_tma<LOGN, tma_lpc<LOGN>(), PE>, RowStage<LOGN, tma_lpc<LOGN>(), RTK_ROW_PP>::total, mask);
+        return ensure_smem(k_row_tma<LOGN, tma_lpc<LOGN>(), PE>,
+                           RowStage<LOGN, tma_lpc<LOGN>(), RTK_ROW_PP, PE == PE_TABLE>::total, mask);
     } else {
         return row_attr<float, LOGN, MODE_DIFF_GAIN, PE>();
     }

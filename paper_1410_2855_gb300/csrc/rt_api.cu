@@ -11,6 +11,12 @@
 #include "rt.h"
 #include "rt_internal.h"
 
+// 1: FP32 handles with the order-10 super-Gaussian pump read N0 from a table
+// staged with each row (4 more bytes per point, no exp per point).
+#ifndef RTK_ROW_PUMP_TABLE
+#define RTK_ROW_PUMP_TABLE 0
+#endif
+
 using namespace rtk;
 
 namespace {
@@ -301,6 +307,10 @@ rt_status rt_create(int n, double fresnel, const rt_pump *pump, double g0, doubl
     h->colC = o.col_tile ? o.col_tile : default_col_tile32(h->logn);
     // N0 on the fly for the order-10 super-Gaussian and the uniform pump, else from a table
     h->pe = p.kind == RT_PUMP_UNIFORM ? 1 : ((p.kind == RT_PUMP_SUPERGAUSS && p.order == 10.0) ? 0 : 2);
+#if RTK_ROW_PUMP_TABLE
+    // FP32 handles read N0 from a table staged with the rows instead of evaluating it.
+    if (h->precision == RT_FP32 && h->pe == 0) h->pe = 2;
+#endif
     cudaGetDevice(&h->device);
 
     auto fail = [&](rt_status s) {

@@ -33,11 +33,13 @@ constexpr int ERR_TIMEOUT = -5;
 #define RTK_COL_PP 1
 #endif
 
-template <int LOGN, int LPC, bool PP> struct RowStage {
+// TAB: the stage also carries the rows' N0 (pump table) values.
+template <int LOGN, int LPC, bool PP, bool TAB = false> struct RowStage {
     static constexpr int N = 1 << LOGN;
     static constexpr size_t e_bytes = round128((size_t)LPC * padded_len(N) * sizeof(float2));
     static constexpr size_t n_bytes = round128((size_t)LPC * N * sizeof(float));
-    static constexpr size_t stage = e_bytes + n_bytes;
+    static constexpr size_t t_bytes = TAB ? n_bytes : 0;
+    static constexpr size_t stage = e_bytes + n_bytes + t_bytes;
     static constexpr size_t extra = PP ? e_bytes : 0;          // second exchange buffer
     static constexpr size_t total = 128 + 2 * stage + extra;   // two mbarriers, two stages, extra buffer
 };
@@ -125,9 +127,9 @@ __device__ __forceinline__ void init_stage_barriers(uint64_t *bar)
 // Local map of one row held in registers (slot s = column t + T s):
 // gain against the frozen inversion, mirror, absorbing edge, inversion
 // relaxation.  Returns sum |E_new|^2 over the thread's 16 elements.
-template <int LOGN, int PE>
+template <int LOGN, int PE, bool STAGED_N0 = false>
 __device__ __forceinline__ float row_local_map(float2 (&v)[16], int t, int row, const float *nrow, float2 *erow,
-                                               float *ngl, const GainParams<float> &g)
+                                               float *ngl, const GainParams<float> &g, const float *n0row = nullptr)
 {
     constexpr int N = 1 << LOGN, T = Plan<LOGN>::T;
     const float step = 2.0f / (float)N;
@@ -147,6 +149,8 @@ __device__ __forceinline__ float row_local_map(float2 (&v)[16], int t, int row, 
         float n0;
         if constexpr (PE == PE_UNIFORM) {
             n0 = g.g0;
+        } else if constexpr (PE == PE_TABLE && STAGED_N0) {
+            n0 = n0row[si * T];
         } else if constexpr (PE == PE_TABLE) {
             n0 = __ldg(g.pump_tab + (size_t)row * N + x);
         } else {
@@ -223,27 +227,33 @@ __device__ __forceinline__ void item_finish(double v, const StatParams &st, int 
 
 // ---- single resonator -------------------------------------------------------
 
-// Row sweep: LPC rows per group, T = n/16 threads per row.
+// Row sweep: LPC rows per group, T = n/16 threads per row.  With a pump
+// table (PE_TABLE) the rows' N0 values are staged by the copy engine too.
 template <int LOGN, int LPC, int PE, bool PP = RTK_ROW_PP>
-__global__ void __launch_bounds__(LPC * Plan<LOGN>::T, smem_blocks(RowStage<LOGN, LPC, PP>::total))
+__global__ void __launch_bounds__(LPC * Plan<LOGN>::T, smem_blocks(RowStage<LOGN, LPC, PP, PE == PE_TABLE>::total))
 k_row_tma(float2 *E, float *Nv, const float2 *__restrict__ tw, const float2 *__restrict__ h, GainParams<float> g,
           StatParams st, int ngroups)
 {
     using P = Plan<LOGN>;
-    using L = RowStage<LOGN, LPC, PP>;
+    constexpr bool TAB = PE == PE_TABLE;
+    using L = RowStage<LOGN, LPC, PP, TAB>;
     constexpr int N = P::N, T = P::T, NT = LPC * T, LS = padded_len(N);
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
     const int lig = threadIdx.x / T, t = threadIdx.x % T;
     auto stage_e = [](int s) { return reinterpret_cast<float2 *>(sm + 128 + s * L::stage); };
     auto stage_n = [](int s) { return reinterpret_cast<float *>(sm + 128 + s * L::stage + L::e_bytes); };
+    auto stage_t = [](int s) {
+        return reinterpret_cast<float *>(sm + 128 + s * L::stage + L::e_bytes + L::n_bytes);
+    };
     auto sync = []() { __syncthreads(); };
     auto issue = [&](int s, int grp) {
-        mbar_arrive_expect_tx(&bar[s], (uint32_t)(LPC * N * (sizeof(float2) + sizeof(float))));
+        mbar_arrive_expect_tx(&bar[s], (uint32_t)(LPC * N * (sizeof(float2) + (TAB ? 2 : 1) * sizeof(float))));
         for (int l = 0; l < LPC; ++l) {
             const size_t row = (size_t)grp * LPC + l;
             bulk_g2s(stage_e(s) + l * LS, E + row * N, N * sizeof(float2), &bar[s]);
             bulk_g2s(stage_n(s) + l * N, Nv + row * N, N * sizeof(float), &bar[s]);
+            if constexpr (TAB) bulk_g2s(stage_t(s) + l * N, g.pump_tab + row * N, N * sizeof(float), &bar[s]);
         }
     };
 
@@ -269,8 +279,8 @@ k_row_tma(float2 *E, float *Nv, const float2 *__restrict__ tw, const float2 *__r
         float2 *extra = reinterpret_cast<float2 *>(sm + 128 + 2 * L::stage) + lig * LS;
         LineBufs<float2, PP> lb{{PP ? extra : line, line}, 0};
         diffract_line<LOGN, 1>(v, t, lb, tw, h, sync);
-        dacc += (double)row_local_map<LOGN, PE>(v, t, row, stage_n(s) + lig * N + t, E + (size_t)row * N + t,
-                                                Nv + (size_t)row * N + t, g);
+        dacc += (double)row_local_map<LOGN, PE, TAB>(v, t, row, stage_n(s) + lig * N + t, E + (size_t)row * N + t,
+                                                     Nv + (size_t)row * N + t, g, stage_t(s) + lig * N + t);
         __syncthreads();  // stage s fully consumed before it is refilled
     }
     finish_mean<NT>(dacc, st, 1.0 / ((double)N * (double)N));
