@@ -290,6 +290,20 @@ def torch_cufft_rate(p, steps=100):
     return steps / (s.elapsed_time(e) / 1e3)
 
 
+def weak_scaling_rate(local_ms, local_units, world, device=None):
+    """Whole-job rate of a weak-scaling run: every rank processed local_units
+    in its own local_ms; the job took the slowest rank's time.  Returns
+    (units per second over all ranks, max ms)."""
+    total_ms = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * local_units / (total_ms / 1e3), total_ms
+
+
 def serve_replay(rt, stream, count=40, rate_hz=50.0):
     """Replay the first `count` requests of the seeded Poisson stream (mean
     rate_hz; sides 128..2048, bounces log-uniform in [1e3, 1e5]) against a
@@ -370,12 +384,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             barrier()
         step_ms = [a.elapsed_time(b) for a, b in evs]
-        total_ms = sum(step_ms)
-        if world > 1:
-            t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
-        value = world * K * B * len(res) / (total_ms / 1e3)
+        value, total_ms = weak_scaling_rate(sum(step_ms), K * B * len(res), world, dev)
         for r in res:
             r.sync()
 
