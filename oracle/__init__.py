@@ -57,6 +57,8 @@ class Params(ctypes.Structure):
         ("pump_order", ctypes.c_double),
         ("pump_radius", ctypes.c_double),
         ("pump_profile", ctypes.c_void_p),
+        ("z_over_F", ctypes.c_double),
+        ("roughness", ctypes.c_void_p),
     ]
 
 
@@ -110,14 +112,20 @@ def alpha_from_fresnel(fresnel: float, d_over_w: float) -> float:
 
 
 def make_params(n, alpha, g0, T1, R, Isat=1.0, edge=8, pump_kind=PUMP_SUPERGAUSS,
-                pump_order=10.0, pump_radius=0.8, pump_profile=None):
+                pump_order=10.0, pump_radius=0.8, pump_profile=None, z_over_F=0.0, roughness=None):
     p = Params(n=n, alpha=alpha, g0=g0, T1=T1, R=R, Isat=Isat, edge=edge, pump_kind=pump_kind,
-               pump_order=pump_order, pump_radius=pump_radius, pump_profile=None)
-    keep = None
+               pump_order=pump_order, pump_radius=pump_radius, pump_profile=None, z_over_F=z_over_F,
+               roughness=None)
+    keep = []
     if pump_kind == PUMP_ARRAY:
-        keep = _f64(pump_profile).reshape(n, n)
-        p.pump_profile = keep.ctypes.data
-    p._keep = keep  # keeps the profile alive as long as the params
+        prof = _f64(pump_profile).reshape(n, n)
+        p.pump_profile = prof.ctypes.data
+        keep.append(prof)
+    if roughness is not None:
+        psi = _f64(roughness).reshape(n, n)
+        p.roughness = psi.ctypes.data
+        keep.append(psi)
+    p._keep = keep  # keeps the arrays alive as long as the params
     return p
 
 

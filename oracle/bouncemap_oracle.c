@@ -27,9 +27,17 @@
  *     the modulus D_0 of eq. complex_aperture2, the saturable-gain form of
  *     the class-B equations):
  *         I = |E'|^2
- *         E_{n+1} = sqrt(R) * A(x) A(y) * exp(N_n / 2) * E'
+ *         E_{n+1} = sqrt(R) * A(x) A(y) * D(x, y) * exp(N_n / 2) * E'
  *         N_{n+1} = N_n + (N0 - N_n (1 + I / Isat)) / T1
  *     A = 0 on the outer `edge` pixels of each axis, 1 inside.
+ *   - Argument of the complex aperture (eq. complex_aperture2: a mirror of
+ *     focal length F, phase k r^2 / 2F, and a roughness phase psi), applied
+ *     complex-conjugated because the propagator above is the conjugate of
+ *     the one paired with that equation (eq. Maxw_Bloch):
+ *         D = exp(-i (k r^2 / (2F) + psi)),
+ *     and in window units (r = x W/2, k = 2 pi/lambda, W^2/lambda = z/alpha)
+ *         k r^2 / (2F) = (pi / (4 alpha)) (z / F) (x^2 + y^2).
+ *     F > 0 then focuses; z/F = 0 and no psi give D = 1.
  *   - Pump N0 = g0 * exp(-(r / r_p)^order) (super-Gaussian), g0 (uniform)
  *     or g0 * profile (array).
  *
@@ -64,6 +72,8 @@ typedef struct {
     double pump_order;     /* super-Gaussian exponent */
     double pump_radius;    /* r_p as a fraction of the window half-width */
     const double *pump_profile; /* n*n values in [0,1] when pump_kind == 2 */
+    double z_over_F;       /* propagation distance per bounce over the mirror's focal length (0: flat) */
+    const double *roughness; /* n*n roughness phase psi in radians, or NULL */
 } orc_params;
 
 int orc_version(void) { return 1; }
@@ -257,20 +267,38 @@ void orc_noise(int n, uint64_t seed, double amp, cplx *E)
 
 static int inside_edge(int j, int n, int edge) { return j >= edge && j < n - edge; }
 
-/* Local part of the map (eq. conv_map's f, the mirror and the aperture
- * modulus D_0): gain against the frozen inversion N_n, then relaxation of
- * N toward the pump driven by the arriving intensity |E'|^2. */
+/* Argument k r^2/(2F) + psi of the complex aperture at pixel (x, y), in
+ * window units (see the conventions above). */
+static double aperture_argument(const orc_params *p, int x, int y)
+{
+    int n = p->n;
+    double xc = (double)(x - n / 2) / (double)(n / 2);
+    double yc = (double)(y - n / 2) / (double)(n / 2);
+    double theta = ORC_PI / (4.0 * p->alpha) * p->z_over_F * (xc * xc + yc * yc);
+    if (p->roughness) theta += p->roughness[(size_t)y * n + x];
+    return theta;
+}
+
+/* Local part of the map (eq. conv_map's f, the mirror and the complex
+ * aperture D_0 exp(-i theta)): gain against the frozen inversion N_n, then
+ * relaxation of N toward the pump driven by the arriving intensity |E'|^2. */
 static void gain_step(cplx *E, double *N, const double *N0, const orc_params *p)
 {
     int n = p->n;
     double sqrtR = sqrt(p->R);
+    int phased = p->z_over_F != 0.0 || p->roughness != NULL;
     for (int y = 0; y < n; ++y) {
         for (int x = 0; x < n; ++x) {
             size_t i = (size_t)y * n + x;
             double inten = creal(E[i]) * creal(E[i]) + cimag(E[i]) * cimag(E[i]);
             double Nn = N[i];
             double A = (inside_edge(x, n, p->edge) && inside_edge(y, n, p->edge)) ? 1.0 : 0.0;
-            E[i] = sqrtR * A * exp(0.5 * Nn) * E[i];
+            cplx D = A;
+            if (phased) {
+                double theta = aperture_argument(p, x, y);
+                D = A * (cos(theta) - sin(theta) * _Complex_I);
+            }
+            E[i] = sqrtR * exp(0.5 * Nn) * D * E[i];
             N[i] = Nn + (N0[i] - Nn * (1.0 + inten / p->Isat)) / p->T1;
         }
     }

@@ -327,3 +327,141 @@ def test_paper_parameters_give_the_quoted_fresnel_range_and_period():
     for D in g["gain_region_diameter_m"]:
         W = D / 0.8
         assert abs(orc.alpha_from_fresnel(D * D / (lam * L), 0.8) - lam * L / W ** 2) < 1e-15
+
+
+# ------------------------------------------- complex aperture: curved mirror, roughness
+
+def _lens_guide_eigenmode(u, beta):
+    """Self-reproducing Gaussian exp(-r^2 / (2 s)) of the unfolded cavity
+    "propagate one bounce, then the mirror lens" with z/F = u (0 < u < 4),
+    in window units.  Paraxial Gaussian algebra: free propagation adds
+    i beta to s (beta = 2 alpha / pi, the 1/k of the window units), the
+    thin lens exp(-i c r^2) adds 2 i c to 1/s, and c = (pi / (4 alpha)) u =
+    u / (2 beta).  The fixed point s = i beta sigma solves
+    sigma^2 + sigma + 1/u = 0 with Re s > 0."""
+    w = math.sqrt(4.0 / u - 1.0) / 2.0
+    return 1j * beta * complex(-0.5, -w)
+
+
+@pytest.mark.parametrize("u", [0.16, 1.0, 2.0, 3.0])
+def test_curved_mirror_eigenmode_advances_by_the_gouy_phase(u):
+    # A flat/curved-mirror cavity is a periodic lens guide (lens spacing z,
+    # focal length F).  Its Gaussian eigenmode returns each period with the
+    # same profile and the on-axis phase advance -theta, cos theta =
+    # (A + D)/2 = 1 - z/(2F) in two transverse dimensions (Kogelnik & Li,
+    # 1966).  theta depends on z/F only, so it pins the lens strength
+    # relative to the propagator as well as the focusing sign.
+    n = 128
+    beta = min(0.008, 0.01 * u * math.sqrt(4.0 / u - 1.0) / 2.0)
+    alpha = math.pi * beta / 2.0
+    s = _lens_guide_eigenmode(u, beta)
+    x = (np.arange(n) - n // 2) / (n // 2)
+    r2 = x[None, :] ** 2 + x[:, None] ** 2
+    E0 = np.exp(-r2 / (2.0 * s))
+    p = orc.make_params(n, alpha, 0.0, 1e9, 1.0, edge=0, pump_kind=orc.PUMP_UNIFORM, z_over_F=u)
+    theta = math.acos(1.0 - u / 2.0)
+    E = E0
+    for b in range(1, 6):
+        E, N, _ = orc.run(p, E, np.zeros((n, n)), 1)
+        assert np.max(np.abs(E - np.exp(-1j * b * theta) * E0)) < 1e-11
+    # The opposite lens sign (a diverging mirror) has no such mode.
+    q = orc.make_params(n, alpha, 0.0, 1e9, 1.0, edge=0, pump_kind=orc.PUMP_UNIFORM, z_over_F=-u)
+    E, _, _ = orc.run(q, E0, np.zeros((n, n)), 5)
+    assert np.max(np.abs(E - np.exp(-5j * theta) * E0)) > 0.05
+
+
+def test_curved_mirror_focuses_a_gaussian_beam_to_the_closed_form_waist():
+    # A Gaussian of waist a reaches the mirror with a flat front; the lens
+    # then curves it: 1/s -> 1/a^2 + 2 i c, c = (pi/(4 alpha)) z/F.  It comes
+    # to a focus (s real) after d_w = F / (1 + (F/Z)^2) bounces, Z = a^2/beta
+    # the Rayleigh range in bounces and F = 1/(z/F), with the second moment
+    # <r^2> = Re s there.  One oracle bounce diffracts first, so start from
+    # the field one bounce before the waist: s0 = a^2 - i beta.
+    n, a, u, beta = 256, 0.12, 0.25, 0.004
+    alpha = math.pi * beta / 2.0
+    c = u / (2.0 * beta)
+    x = (np.arange(n) - n // 2) / (n // 2)
+    r2 = x[None, :] ** 2 + x[:, None] ** 2
+    s0 = complex(a * a, -beta)
+    E0 = np.exp(-r2 / (2.0 * s0))
+    p = orc.make_params(n, alpha, 0.0, 1e9, 1.0, edge=0, pump_kind=orc.PUMP_UNIFORM, z_over_F=u)
+    E1, _, _ = orc.run(p, E0, np.zeros((n, n)), 1)
+    s_lens = 1.0 / (1.0 / (a * a) + 2j * c)
+    expect = (s0 / (a * a)) * np.exp(-r2 / (2.0 * s_lens))
+    assert np.max(np.abs(E1 - expect)) < 1e-11
+    F, Z = 1.0 / u, a * a / beta
+    d_w = F / (1.0 + (F / Z) ** 2)
+
+    def second_moment(d):
+        I = np.abs(orc.diffract(E1, alpha * d)) ** 2
+        return float(np.sum(I * r2) / np.sum(I))
+
+    w = second_moment(d_w)
+    assert abs(w - s_lens.real) < 1e-9 * s_lens.real
+    assert w < second_moment(0.9 * d_w) and w < second_moment(1.1 * d_w)
+    # A diverging mirror (z/F < 0) has no focus ahead: the beam only grows.
+    q = orc.make_params(n, alpha, 0.0, 1e9, 1.0, edge=0, pump_kind=orc.PUMP_UNIFORM, z_over_F=-u)
+    E1d, _, _ = orc.run(q, E0, np.zeros((n, n)), 1)
+    I0 = np.abs(E1d) ** 2
+    I1 = np.abs(orc.diffract(E1d, alpha * d_w)) ** 2
+    assert np.sum(I1 * r2) / np.sum(I1) > np.sum(I0 * r2) / np.sum(I0)
+
+
+def test_roughness_phase_tilt_closed_form():
+    # A linear roughness phase psi = pi (mx0 x + my0 y) is a tilted mirror:
+    # on a uniform field it imprints the plane wave of frequency -(mx0, my0),
+    # the next bounce propagates that wave (phase -pi alpha |m|^2) and tilts
+    # it again.  After b bounces:
+    #   E_b = exp(-i pi alpha |m0|^2 sum_{k<b} k^2) exp(-i b psi).
+    # Distinct mx0, my0 pin the table's orientation (psi[y n + x]).
+    n, alpha, mx0, my0 = 64, 0.013, 3, -2
+    x = (np.arange(n) - n // 2) / (n // 2)
+    psi = math.pi * (mx0 * x[None, :] + my0 * x[:, None])
+    p = orc.make_params(n, alpha, 0.0, 1e9, 1.0, edge=0, pump_kind=orc.PUMP_UNIFORM, roughness=psi)
+    E = np.ones((n, n), np.complex128)
+    m2 = mx0 * mx0 + my0 * my0
+    for b in range(1, 7):
+        E, _, _ = orc.run(p, E, np.zeros((n, n)), 1)
+        k2 = sum(k * k for k in range(1, b))
+        expect = np.exp(-1j * math.pi * alpha * m2 * k2) * np.exp(-1j * b * psi)
+        assert np.max(np.abs(E - expect)) < 1e-11
+    # Transposing psi gives a different field.
+    q = orc.make_params(n, alpha, 0.0, 1e9, 1.0, edge=0, pump_kind=orc.PUMP_UNIFORM, roughness=psi.T.copy())
+    Et, _, _ = orc.run(q, np.ones((n, n), np.complex128), np.zeros((n, n)), 2)
+    E2, _, _ = orc.run(p, np.ones((n, n), np.complex128), np.zeros((n, n)), 2)
+    assert np.max(np.abs(Et - E2)) > 0.5
+
+
+def test_aperture_phase_leaves_intensity_and_gain_untouched():
+    # The aperture argument is a pure phase: with diffraction switched off
+    # (alpha = 2, an identity bounce) the intensities, the inversion and the
+    # mean intensity equal those of the flat, smooth mirror exactly.
+    n = 32
+    rng = np.random.default_rng(3)
+    E0 = crandn(rng, (n, n))
+    N0 = rng.uniform(0.0, 0.3, (n, n))
+    psi = rng.normal(0.0, 1.0, (n, n))
+    flat = orc.make_params(n, 2.0, 0.2, 50.0, 0.9, edge=2)
+    rough = orc.make_params(n, 2.0, 0.2, 50.0, 0.9, edge=2, z_over_F=0.7, roughness=psi)
+    Ef, Nf, hf = orc.run(flat, E0, N0, 1)
+    Er, Nr, hr = orc.run(rough, E0, N0, 1)
+    assert np.max(np.abs(np.abs(Er) - np.abs(Ef))) < 1e-14
+    assert np.array_equal(Nf, Nr)
+    assert abs(hf[0] - hr[0]) < 1e-15 * hf[0]
+    x = (np.arange(n) - n // 2) / (n // 2)
+    theta = math.pi / (4 * 2.0) * 0.7 * (x[None, :] ** 2 + x[:, None] ** 2) + psi
+    inside = np.abs(Ef) > 0
+    assert np.max(np.abs(Er[inside] - Ef[inside] * np.exp(-1j * theta[inside]))) < 1e-13
+
+
+def test_paper_cavity_mirror_is_a_stable_lens_guide():
+    # Flat facet + concave mirror of radius Rc at distance L, unfolded: one
+    # bounce propagates z = 2L and passes one lens of focal length Rc/2, so
+    # z/F = 4 L / Rc.  For the quoted geometry that is 0.16: inside the
+    # stability range 0 < z/F < 4 (|cos theta| < 1), which the eigenmode test
+    # above exercises at this value.
+    with open(os.path.join(GOLDEN, "paper_parameters.json")) as f:
+        g = json.load(f)
+    u = 4.0 * g["cavity_length_m"] / g["mirror_radius_of_curvature_m"]
+    assert abs(u - 0.16) < 1e-12
+    assert abs(1.0 - u / 2.0) < 1.0
