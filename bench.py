@@ -26,6 +26,7 @@ from __future__ import annotations
 
 import argparse
 import csv
+import dataclasses
 import hashlib
 import io
 import json
@@ -47,7 +48,8 @@ METRIC = "round trips/s at 2048² FP32 vs FP64, % HBM peak; serve p50/p99 latenc
 UNIT = "round trips/s"
 COL_BYTES_PER_PT = 16   # column sweep: read and write the complex64 field
 ROW_BYTES_PER_PT = 24   # row sweep: field (8+8) and inversion (4+4)
-KERNEL_SOURCES = ["fft_core.cuh", "sweep.cuh", "sweep_tma.cuh", "tma.cuh", "k_fp32.cu"]
+KERNEL_SOURCES = ["fft_core.cuh", "sweep.cuh", "sweep_tma.cuh", "tma.cuh", "launch.cuh", "k_fp32_col.cu",
+                  "k_fp32_row.cu"]
 
 
 def parse_args():
@@ -495,6 +497,32 @@ def comparisons(args, rt, torch, main, streams, params, res, E0, N0, rank, world
         for r in one:
             r.close()
     extra["one_stream"] = {"value": 4 * B * len(params) / (s.elapsed_time(e) / 1e3), "unit": UNIT}
+
+    # ---- curved and rough mirror (aperture phase in the row sweep), one resonator on one stream
+    extra["curved_mirror"] = {}
+    flat = dataclasses.replace(wl.CURVED, z_over_F=0.0, roughness_rms=0.0)
+    lens = dataclasses.replace(wl.CURVED, roughness_rms=0.0)
+    for name, q in (("flat", flat), ("lens", lens), ("lens_roughness", wl.CURVED)):
+        with torch.cuda.stream(main):
+            with rt.Resonator.from_params(q, cuda_stream=main.cuda_stream, chunk=B) as r:
+                r.step(B)
+                torch.cuda.synchronize()
+                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s.record(main)
+                r.step(2 * B)
+                e.record(main)
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(51)]
+                for i in range(50):
+                    ev[i].record(main)
+                    rt.rt_sweep(r.h, rt.RT_SWEEP_ROWS)
+                ev[50].record(main)
+                torch.cuda.synchronize()
+                r.sync()
+                extra["curved_mirror"][name] = {
+                    "round_trips_per_s": 2 * B / (s.elapsed_time(e) / 1e3),
+                    "row_sweep_ms": ev[0].elapsed_time(ev[50]) / 50}
+    extra["curved_mirror"]["workload"] = ("2048^2, N_F 1000, g0 0.3, R 0.9; z/F 0.16 (50 mm mirror, L 2 mm); "
+                                          "roughness 0.05 rad rms; one stream, graphs of %d bounces" % B)
 
     # ---- batched parameter sweep: 256 resonators of side 256/512/1024 in one graph per 100 bounces
     jobs = wl.batch_sweep(count=256, sides=(256, 512, 1024))

@@ -12,7 +12,7 @@
  *
  *   E'      = IDFT2( DFT2(E_n) * exp(-i pi alpha (mx^2 + my^2)) ) / n^2
  *   I       = |E'|^2
- *   E_{n+1} = sqrt(R) * A(x) A(y) * exp(N_n / 2) * E'
+ *   E_{n+1} = sqrt(R) * A(x) A(y) * D(x, y) * exp(N_n / 2) * E'
  *   N_{n+1} = N_n + (N0(x, y) - N_n (1 + I / Isat)) / T1
  *
  * with alpha = (D/W)^2 / N_F (N_F = D^2 / (lambda z) the cavity Fresnel
@@ -20,6 +20,28 @@
  * absorbing edge (0 on the outer edge_px pixels of each axis), N0 the pump
  * (unsaturated inversion) and (mx, my) the signed DFT frequencies.  Pixel j
  * sits at x_j = (j - n/2) / (n/2): the window half-width is 1.
+ *
+ * Multi-slice gain medium (opts.slices = m > 1; the thin-slice form of the
+ * integral-equation section for a gain medium spread along the cavity):
+ * a bounce is m steps "diffract z/m, then slice s", slice s amplifying
+ * E <- exp(N_s / 2) E and relaxing N_s <- N_s + (N0/m - N_s (1 + I_s/Isat))/T1
+ * with its own inversion N_s and the intensity I_s arriving at it; the
+ * mirror (sqrt R, A, D) acts once, after the last slice.  m = 1 is the map
+ * above.  The inversion of such a handle is m n x n arrays, slice-major, in
+ * rt_read_inversion / rt_write_inversion; it starts at N0/m per slice.
+ *
+ * D is the phase of the complex aperture of eq. complex_aperture2 (a curved
+ * mirror of focal length F and a random roughness phase psi):
+ *
+ *   D(x, y) = exp(-i (c (x^2 + y^2) + psi(x, y))),  c = (pi / (4 alpha)) (z / F),
+ *
+ * which is k r^2 / (2F) in window units (r = x W/2, k = 2 pi / lambda,
+ * W^2 / lambda = z / alpha).  The paper prints exp(+i ...) together with the
+ * opposite sign of the propagator (eq. Maxw_Bloch); the propagator above
+ * follows eq. limit_of_operators_renorm_final, and the aperture phase is
+ * conjugated with it, so the whole map is the complex conjugate of that
+ * printed pair and F > 0 focuses (a concave mirror of radius of curvature
+ * Rc has F = Rc / 2).  D = 1 unless z_over_F or roughness is set.
  *
  * Layout.  Grids are n x n, row-major (element [y*n + x]).  The field is
  * interleaved complex: complex64 (2 x float) for RT_FP32 handles, complex128
@@ -87,6 +109,12 @@ typedef struct {
     long long history_cap;        /* >0: keep the mean intensity of the last history_cap bounces (65536) */
     int chunk;                    /* bounces per captured CUDA graph in rt_step; 0 = no graphs (500) */
     int col_tile;                 /* FP32 column-sweep tile width in columns (2, 4, 8 or 16); 0 = library choice (0) */
+    double z_over_F;              /* curved mirror: propagation distance per bounce over its focal length F,
+                                     > 0 focuses, 0 = flat mirror (0); finite */
+    const double *roughness;      /* mirror roughness: host array of n*n doubles psi[y*n + x] in radians,
+                                     copied at creation; NULL = smooth (NULL) */
+    int slices;                   /* gain medium as m thin slices per bounce, 1 <= m <= 64 (0 or 1: one
+                                     slice at the mirror; handles only, see below) (0) */
 } rt_opts;
 
 rt_status rt_opts_default(rt_opts *opts);
@@ -108,7 +136,7 @@ typedef struct {
  * and mirror reflectivity R (0 < R <= 1).  Allocates the field, inversion and
  * tables on the device, draws the seeded complex Gaussian noise field
  * (splitmix64 counter stream + Box-Muller, in FP64, rounded to the handle's
- * precision) and sets N = N0.  Section "Integral equation form", eqs.
+ * precision) and sets N = N0 (N0/m per slice).  Section "Integral equation form", eqs.
  * complex_8F and complex_aperture2; the noise start and the full inversion
  * are the initial condition of the map.
  * Returns RT_EINVAL for out-of-range arguments, RT_ENOMEM, RT_ECUDA. */
@@ -128,7 +156,7 @@ rt_status rt_step(rt_handle *h, long long n_bounces);
  * enqueues; the propagator factorisation follows from eq.
  * limit_of_operators_renorm_final with a separable Laplacian.  Calling the
  * row sweep without the column sweep first is not a bounce of the map.
- * FP32 handles only (RT_EINVAL otherwise).  Asynchronous. */
+ * FP32 single-slice handles only (RT_EINVAL otherwise).  Asynchronous. */
 enum { RT_SWEEP_COLUMNS = 0, RT_SWEEP_ROWS = 1 };
 rt_status rt_sweep(rt_handle *h, int which);
 
@@ -161,6 +189,17 @@ rt_status rt_read_history(rt_handle *h, double *dst, long long max, long long *g
 /* Far-field spectrum S = |DFT2(E)|^2 of the current field (n*n float or
  * double, unnormalised) to dst (host or device).  Blocks. */
 rt_status rt_read_spectrum(rt_handle *h, void *dst, size_t bytes);
+
+/* The field at an intracavity plane: the current field (at the mirror and
+ * gain plane) diffracted a further zeta * z, zeta any finite real (negative
+ * values propagate backwards; zeta = 1 is one bounce's diffraction without
+ * the local map):
+ *   E_zeta = IDFT2( DFT2(E) * exp(-i pi alpha zeta (mx^2 + my^2)) ) / n^2.
+ * The planes L_m = p^2 / (2 lambda m) between the mirrors, where the arrays
+ * of period p/m form (section "Comparison with experiment"), are
+ * zeta = L_m / z.  Written to dst (host or device) in the layout of
+ * rt_read_field; the handle's state is unchanged.  Blocks. */
+rt_status rt_read_field_at(rt_handle *h, double zeta, void *dst, size_t bytes);
 
 /* Dominant spatial frequency of the current field.  Bin k and its mirror
  * -k (mod n) form one peak of folded power S[k] + S[-k] (S[k] once if
@@ -200,6 +239,8 @@ typedef struct {
     unsigned long long seed;      /* noise seed */
     double noise_amp;             /* noise amplitude */
     double pump_diam_over_window; /* D/W */
+    double z_over_F;              /* curved mirror z / F (0 = flat) */
+    const double *roughness;      /* n*n roughness phase psi, host, copied at set-up; NULL = smooth */
 } rt_job;
 
 /* Fill a job with the defaults of rt_opts_default / rt_create for side n. */
@@ -291,9 +332,10 @@ rt_status rt_serve_opts_default(rt_serve_opts *opts);
 rt_status rt_serve_create(const rt_serve_opts *opts, rt_server **out);
 
 /* Queue a request of n_bounces (> 0) bounces of `job` (32 <= n <= 2048,
- * super-Gaussian order-10 or uniform pump).  field_out (host or device,
- * n*n complex64, may be NULL) receives the final field before the result is
- * posted; it must stay valid until then.  *id receives the request id.
+ * super-Gaussian order-10 or uniform pump, flat or curved mirror without a
+ * roughness table).  field_out (host or device, n*n complex64, may be NULL)
+ * receives the final field before the result is posted; it must stay valid
+ * until then.  *id receives the request id.
  * RT_EINVAL for bad jobs or a request that could never fit the budget. */
 rt_status rt_serve_submit(rt_server *s, const rt_job *job, long long n_bounces, void *field_out, long long *id);
 
@@ -322,12 +364,13 @@ rt_status rt_serve_destroy(rt_server *s);
  * buffers, updated in place: `field` (n*n complex64, row-major) and
  * `inversion` (n*n float), both 16-byte aligned.  It allocates nothing.  The
  * scratch it needs (propagator and twiddle tables, reduction partials,
- * counters) lives in one fixed array of about 97 KB of device memory that
+ * counters) lives in one fixed array of about 130 KB of device memory that
  * every GPU which loads this library holds until the process exits; n is
  * therefore limited to RT_NOALLOC_MAX_N, and larger sizes return RT_EINVAL.
- * Supported: RT_FP32 only, super-Gaussian pump of order 10 or uniform pump
- * (anything else returns RT_EINVAL).  Options used: Isat, edge_px,
- * pump_diam_over_window, cuda_stream, col_tile (NULL opts = defaults).
+ * Supported: RT_FP32 only, super-Gaussian pump of order 10 or uniform pump,
+ * flat or curved mirror without roughness (anything else returns
+ * RT_EINVAL).  Options used: Isat, edge_px, pump_diam_over_window,
+ * cuda_stream, col_tile, z_over_F (NULL opts = defaults).
  *
  * The first call on each device looks up the array's device address, with
  * that device current; make that first call before any stream capture.

@@ -59,6 +59,7 @@ class Params(ctypes.Structure):
         ("pump_profile", ctypes.c_void_p),
         ("z_over_F", ctypes.c_double),
         ("roughness", ctypes.c_void_p),
+        ("slices", ctypes.c_int),
     ]
 
 
@@ -112,10 +113,10 @@ def alpha_from_fresnel(fresnel: float, d_over_w: float) -> float:
 
 
 def make_params(n, alpha, g0, T1, R, Isat=1.0, edge=8, pump_kind=PUMP_SUPERGAUSS,
-                pump_order=10.0, pump_radius=0.8, pump_profile=None, z_over_F=0.0, roughness=None):
+                pump_order=10.0, pump_radius=0.8, pump_profile=None, z_over_F=0.0, roughness=None, slices=1):
     p = Params(n=n, alpha=alpha, g0=g0, T1=T1, R=R, Isat=Isat, edge=edge, pump_kind=pump_kind,
                pump_order=pump_order, pump_radius=pump_radius, pump_profile=None, z_over_F=z_over_F,
-               roughness=None)
+               roughness=None, slices=slices)
     keep = []
     if pump_kind == PUMP_ARRAY:
         prof = _f64(pump_profile).reshape(n, n)
@@ -169,6 +170,14 @@ def pump(params: Params) -> np.ndarray:
     return N0
 
 
+def initial_inversion(params: Params) -> np.ndarray:
+    """The fully pumped start: N = N0 (one slice), or N0/m in each of m
+    slices (m x n x n)."""
+    N0 = pump(params)
+    m = max(params.slices, 1)
+    return N0 if m == 1 else np.repeat((N0 / m)[None], m, axis=0)
+
+
 def splitmix64(seed: int, c: int) -> int:
     return int(lib().orc_splitmix64(seed, c))
 
@@ -181,9 +190,13 @@ def noise(n, seed, amp) -> np.ndarray:
 
 def run(params: Params, E, N, nb, nthreads=1, history=True):
     """Run nb bounces from (E, N).  Returns (E, N, hist) with fresh arrays;
-    hist[b] is the mean intensity after bounce b (None if history=False)."""
+    hist[b] is the mean intensity after bounce b (None if history=False).
+    With m > 1 slices N holds m inversions (m x n x n)."""
     E = _c128(E).copy()
     N = _f64(N).copy()
+    m = max(params.slices, 1)
+    if E.size != params.n ** 2 or N.size != m * params.n ** 2:
+        raise ValueError("field must be n x n and the inversion slices x n x n")
     hist = np.empty(max(int(nb), 0), np.float64) if history else None
     rc = lib().orc_run(ctypes.byref(params), E.ctypes.data, N.ctypes.data, int(nb),
                        hist.ctypes.data if history else None, nthreads)

@@ -38,6 +38,14 @@
  *     and in window units (r = x W/2, k = 2 pi/lambda, W^2/lambda = z/alpha)
  *         k r^2 / (2F) = (pi / (4 alpha)) (z / F) (x^2 + y^2).
  *     F > 0 then focuses; z/F = 0 and no psi give D = 1.
+ *   - Multi-slice gain medium (the thin-slice form the integral-equation
+ *     section mentions for a gain medium that is not concentrated near one
+ *     plane): with m slices a bounce is m steps "diffract z/m, then slice
+ *     s": E <- exp(N_s / 2) E, N_s <- N_s + (N0/m - N_s (1 + I_s/Isat))/T1
+ *     with I_s = |E|^2 arriving at slice s; each slice has its own
+ *     inversion and a pump of N0/m, so the small-signal gain per pass stays
+ *     g0.  The mirror (sqrt R, A, D) acts once, after the last slice.  With
+ *     m = 1 this is the map above.
  *   - Pump N0 = g0 * exp(-(r / r_p)^order) (super-Gaussian), g0 (uniform)
  *     or g0 * profile (array).
  *
@@ -74,6 +82,7 @@ typedef struct {
     const double *pump_profile; /* n*n values in [0,1] when pump_kind == 2 */
     double z_over_F;       /* propagation distance per bounce over the mirror's focal length (0: flat) */
     const double *roughness; /* n*n roughness phase psi in radians, or NULL */
+    int slices;            /* thin gain slices per bounce (0 or 1: one) */
 } orc_params;
 
 int orc_version(void) { return 1; }
@@ -281,25 +290,26 @@ static double aperture_argument(const orc_params *p, int x, int y)
 
 /* Local part of the map (eq. conv_map's f, the mirror and the complex
  * aperture D_0 exp(-i theta)): gain against the frozen inversion N_n, then
- * relaxation of N toward the pump driven by the arriving intensity |E'|^2. */
-static void gain_step(cplx *E, double *N, const double *N0, const orc_params *p)
+ * relaxation of N toward the pump driven by the arriving intensity |E'|^2.
+ * One slice of m: pump N0/m; the mirror only when `mirror` is set. */
+static void gain_step(cplx *E, double *N, const double *N0, const orc_params *p, int m, int mirror)
 {
     int n = p->n;
-    double sqrtR = sqrt(p->R);
-    int phased = p->z_over_F != 0.0 || p->roughness != NULL;
+    double sqrtR = mirror ? sqrt(p->R) : 1.0;
+    int phased = mirror && (p->z_over_F != 0.0 || p->roughness != NULL);
     for (int y = 0; y < n; ++y) {
         for (int x = 0; x < n; ++x) {
             size_t i = (size_t)y * n + x;
             double inten = creal(E[i]) * creal(E[i]) + cimag(E[i]) * cimag(E[i]);
             double Nn = N[i];
-            double A = (inside_edge(x, n, p->edge) && inside_edge(y, n, p->edge)) ? 1.0 : 0.0;
+            double A = (!mirror || (inside_edge(x, n, p->edge) && inside_edge(y, n, p->edge))) ? 1.0 : 0.0;
             cplx D = A;
             if (phased) {
                 double theta = aperture_argument(p, x, y);
                 D = A * (cos(theta) - sin(theta) * _Complex_I);
             }
             E[i] = sqrtR * exp(0.5 * Nn) * D * E[i];
-            N[i] = Nn + (N0[i] - Nn * (1.0 + inten / p->Isat)) / p->T1;
+            N[i] = Nn + (N0[i] / (double)m - Nn * (1.0 + inten / p->Isat)) / p->T1;
         }
     }
 }
@@ -311,23 +321,27 @@ static double mean_intensity(const cplx *E, size_t P)
     return s / (double)P;
 }
 
-/* Run nb bounces in place on (E, N).  hist (may be NULL) receives the mean
- * intensity <|E_{b+1}|^2> after each bounce b = 0 .. nb-1.
+/* Run nb bounces in place on (E, N); N holds one n*n inversion per slice
+ * (slice-major).  hist (may be NULL) receives the mean intensity
+ * <|E_{b+1}|^2> after each bounce b = 0 .. nb-1.
  * Returns 0, or -1 on invalid parameters, -2 on allocation failure. */
 int orc_run(const orc_params *p, cplx *E, double *N, long long nb, double *hist, int nthreads)
 {
     int n = p->n;
-    if (!is_pow2(n) || p->T1 <= 0.0 || p->R < 0.0 || p->Isat <= 0.0 || p->edge < 0) return -1;
+    int m = p->slices > 1 ? p->slices : 1;
+    if (!is_pow2(n) || p->T1 <= 0.0 || p->R < 0.0 || p->Isat <= 0.0 || p->edge < 0 || p->slices < 0) return -1;
     if (p->pump_kind == 2 && !p->pump_profile) return -1;
     size_t P = (size_t)n * n;
     cplx *H = (cplx *)malloc(sizeof(cplx) * P);
     double *N0 = (double *)malloc(sizeof(double) * P);
     if (!H || !N0) { free(H); free(N0); return -2; }
-    orc_phase_2d(n, p->alpha, H);
+    orc_phase_2d(n, p->alpha / (double)m, H);
     orc_pump(p, N0);
     for (long long b = 0; b < nb; ++b) {
-        diffract_with(E, H, n, nthreads);
-        gain_step(E, N, N0, p);
+        for (int s = 0; s < m; ++s) {
+            diffract_with(E, H, n, nthreads);
+            gain_step(E, N + (size_t)s * P, N0, p, m, s == m - 1);
+        }
         if (hist) hist[b] = mean_intensity(E, P);
     }
     free(H);

@@ -29,8 +29,11 @@ bool job_ok(const rt_job &j)
     if (j.pump.kind < RT_PUMP_SUPERGAUSS || j.pump.kind > RT_PUMP_ARRAY) return false;
     if (j.pump.kind == RT_PUMP_SUPERGAUSS && (!fpos(j.pump.order) || !fpos(j.pump.radius))) return false;
     if (j.pump.kind == RT_PUMP_ARRAY && !j.pump.profile) return false;
+    if (!std::isfinite(j.z_over_F)) return false;
     return true;
 }
+
+bool job_rough(const rt_job &j) { return j.roughness != nullptr; }
 
 int pump_eval(const rt_pump &p)
 {
@@ -41,18 +44,22 @@ int pump_eval(const rt_pump &p)
 double job_alpha(const rt_job &j) { return j.pump_diam_over_window * j.pump_diam_over_window / j.fresnel; }
 
 namespace {
-void slot_layout(int n, long long hist_cap, bool table, size_t off[7], size_t *total)
+constexpr int kParts = 9;
+
+void slot_layout(int n, long long hist_cap, bool table, bool rough, size_t off[kParts], size_t *total)
 {
     const size_t N = (size_t)n, P = N * N, cap = hist_cap > 0 ? (size_t)hist_cap : 0;
-    const size_t sz[7] = {al256(P * sizeof(float2)),                                  // E
-                          al256(P * sizeof(float)),                                   // N
-                          al256(N * sizeof(float2)),                                  // h
-                          al256((size_t)row_groups32(log2_of(n)) * sizeof(double)),  // part
-                          al256(cap * sizeof(double)),                                // history
-                          al256(sizeof(CUtensorMap)),                                 // tensor map
-                          table ? al256(P * sizeof(float)) : 0};                      // N0 table
+    const size_t sz[kParts] = {al256(P * sizeof(float2)),                                  // E
+                               al256(P * sizeof(float)),                                   // N
+                               al256(N * sizeof(float2)),                                  // h
+                               al256((size_t)row_groups32(log2_of(n)) * sizeof(double)),  // part
+                               al256(cap * sizeof(double)),                                // history
+                               al256(sizeof(CUtensorMap)),                                 // tensor map
+                               table ? al256(P * sizeof(float)) : 0,                       // N0 table
+                               al256(N * sizeof(float2)),                                  // lens
+                               rough ? al256(P * sizeof(float2)) : 0};                     // aperture table
     size_t t = 0;
-    for (int k = 0; k < 7; ++k) {
+    for (int k = 0; k < kParts; ++k) {
         off[k] = t;
         t += sz[k];
     }
@@ -60,17 +67,17 @@ void slot_layout(int n, long long hist_cap, bool table, size_t off[7], size_t *t
 }
 }  // namespace
 
-size_t slot_bytes(int n, long long hist_cap, bool table)
+size_t slot_bytes(int n, long long hist_cap, bool table, bool rough)
 {
-    size_t off[7], t;
-    slot_layout(n, hist_cap, table, off, &t);
+    size_t off[kParts], t;
+    slot_layout(n, hist_cap, table, rough, off, &t);
     return t;
 }
 
-cudaError_t slot_alloc(int n, long long hist_cap, bool table, SlotBufs *out)
+cudaError_t slot_alloc(int n, long long hist_cap, bool table, bool rough, SlotBufs *out)
 {
-    size_t off[7], total;
-    slot_layout(n, hist_cap, table, off, &total);
+    size_t off[kParts], total;
+    slot_layout(n, hist_cap, table, rough, off, &total);
     SlotBufs b;
     cudaError_t e = cudaMalloc(&b.mem, total);
     if (e != cudaSuccess) return e;
@@ -82,6 +89,8 @@ cudaError_t slot_alloc(int n, long long hist_cap, bool table, SlotBufs *out)
     b.hist = hist_cap > 0 ? reinterpret_cast<double *>(b.mem + off[4]) : nullptr;
     b.tmap = reinterpret_cast<CUtensorMap *>(b.mem + off[5]);
     b.pump_tab = table ? reinterpret_cast<float *>(b.mem + off[6]) : nullptr;
+    b.lens = reinterpret_cast<float2 *>(b.mem + off[7]);
+    b.phase = rough ? reinterpret_cast<float2 *>(b.mem + off[8]) : nullptr;
     *out = b;
     return cudaSuccess;
 }
@@ -111,6 +120,8 @@ BatchRes slot_descriptor(const rt_job &job, const SlotBufs &b, SlotCtl *ctl, lon
     g.edge = job.edge_px;
     g.pump_kind = job.pump.kind;
     g.pump_tab = b.pump_tab;
+    g.lens = (!job_rough(job) && job.z_over_F != 0.0) ? b.lens : nullptr;
+    g.phase = job_rough(job) ? b.phase : nullptr;
     r.pe = pe;
     r.target = target;
     r.st.part = b.part;
@@ -144,6 +155,18 @@ cudaError_t slot_start(const rt_job &job, const SlotBufs &b, int colC, float2 *c
         if (!b.pump_tab) return cudaErrorInvalidValue;
         if ((e = cudaMemcpyAsync(b.pump_tab, b.N, P * sizeof(float), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
             return e;
+    }
+    const double c = lens_curvature(job_alpha(job), job.z_over_F);
+    if (job_rough(job)) {
+        if (!b.phase) return cudaErrorInvalidValue;
+        double *psi = nullptr;
+        if ((e = cudaMallocAsync(reinterpret_cast<void **>(&psi), P * sizeof(double), s)) != cudaSuccess) return e;
+        e = cudaMemcpyAsync(psi, job.roughness, P * sizeof(double), cudaMemcpyDefault, s);
+        if (e == cudaSuccess) e = launch_phase32(n, c, psi, b.phase, s);
+        cudaFreeAsync(psi, s);
+        if (e != cudaSuccess) return e;
+    } else if (job.z_over_F != 0.0) {
+        if ((e = launch_lens32(n, c, b.lens, s)) != cudaSuccess) return e;
     }
     alignas(64) unsigned char map[128];
     if ((e = make_col_tensor_map(map, b.E, n, colC)) != cudaSuccess) return e;

@@ -31,24 +31,28 @@ struct SlotBufs {
     double *hist = nullptr;
     CUtensorMap *tmap = nullptr;
     float *pump_tab = nullptr;
+    float2 *lens = nullptr;   // per-axis curved-mirror factors (always present, n entries)
+    float2 *phase = nullptr;  // n*n aperture factors of a rough mirror (only when allocated for one)
 };
 
 bool job_ok(const rt_job &j);            // 32 <= n <= 2048 and parameters in range
+bool job_rough(const rt_job &j);         // the job's mirror has a roughness table
 int pump_eval(const rt_pump &p);         // PumpEval of a job's pump
 double job_alpha(const rt_job &j);       // lambda z / W^2 = (D/W)^2 / N_F
 int log2_of(int n);
 
-// Bytes and allocation of a slot for side n (table: N0 table for PE_TABLE).
-size_t slot_bytes(int n, long long hist_cap, bool table);
-cudaError_t slot_alloc(int n, long long hist_cap, bool table, SlotBufs *out);
+// Bytes and allocation of a slot for side n (table: N0 table for PE_TABLE;
+// rough: aperture table for a rough mirror).
+size_t slot_bytes(int n, long long hist_cap, bool table, bool rough);
+cudaError_t slot_alloc(int n, long long hist_cap, bool table, bool rough, SlotBufs *out);
 void slot_free(SlotBufs *b);
 
 // Descriptor of a slot for the batched kernels.
 BatchRes slot_descriptor(const rt_job &job, const SlotBufs &b, SlotCtl *ctl, long long hist_cap, long long target);
 
 // Start `job` in a slot (as rt_create starts a handle): propagator table,
-// class twiddles, noise field, N = N0, tensor map, zeroed counters, and the
-// descriptor written to *d_desc.  All on stream s.
+// class twiddles, aperture phase, noise field, N = N0, tensor map, zeroed
+// counters, and the descriptor written to *d_desc.  All on stream s.
 cudaError_t slot_start(const rt_job &job, const SlotBufs &b, int colC, float2 *class_tw, SlotCtl *ctl,
                        BatchRes *d_desc, long long hist_cap, long long target, cudaStream_t s);
 

@@ -1,0 +1,97 @@
+// FP32 fused path, batched sweeps (all resonators of one grid size per
+// persistent launch): launchers and instantiations.
+#include "launch.cuh"
+
+namespace rtk {
+
+template <int LOGN, int C>
+static cudaError_t col_batch32_c(const BatchRes *res, int nres, const float2 *tw, int *err, cudaStream_t s)
+{
+    if constexpr (!col_tma_fits<LOGN, C>()) {
+        return cudaErrorInvalidValue;
+    } else {
+        using L = ColPlan<LOGN, C>;
+        auto k = k_col_tma_batch<LOGN, C>;
+        static std::atomic<unsigned long long> mask{0};
+        static std::atomic<int> per_sm{0};
+        cudaError_t e = ensure_smem(k, L::total, mask);
+        if (e != cudaSuccess) return e;
+        const int items = nres * ((1 << LOGN) / C);
+        const int grid = persistent_grid(k, C * Plan<LOGN>::T, L::total, items, per_sm);
+        k<<<grid, C * Plan<LOGN>::T, L::total, s>>>(res, nres, tw, err);
+        return cudaGetLastError();
+    }
+}
+
+template <int LOGN>
+static cudaError_t col_batch32(int colC, const BatchRes *res, int nres, const float2 *tw, int *err, cudaStream_t s)
+{
+    switch (colC) {
+    case 2: return col_batch32_c<LOGN, 2>(res, nres, tw, err, s);
+    case 4: return col_batch32_c<LOGN, 4>(res, nres, tw, err, s);
+    case 8: return col_batch32_c<LOGN, 8>(res, nres, tw, err, s);
+    case 16: return col_batch32_c<LOGN, 16>(res, nres, tw, err, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_col_batch32(int logn, int colC, const BatchRes *res, int nres, const float2 *tw, int *err,
+                               cudaStream_t s)
+{
+    if (nres <= 0) return cudaSuccess;
+    RTK_LOGN_CASES(col_batch32, colC, res, nres, tw, err, s)
+}
+
+template <int LOGN>
+static cudaError_t row_batch32(const BatchRes *res, int nres, const float2 *tw, int *err, cudaStream_t s)
+{
+    constexpr int LPC = tma_lpc<LOGN>();
+    using L = RowPlan<LOGN, LPC>;
+    auto k = k_row_tma_batch<LOGN, LPC>;
+    static std::atomic<unsigned long long> mask{0};
+    static std::atomic<int> per_sm{0};
+    cudaError_t e = ensure_smem(k, L::total, mask);
+    if (e != cudaSuccess) return e;
+    const int items = nres * ((1 << LOGN) / LPC);
+    const int grid = persistent_grid(k, LPC * Plan<LOGN>::T, L::total, items, per_sm);
+    k<<<grid, LPC * Plan<LOGN>::T, L::total, s>>>(res, nres, tw, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_batch32(int logn, const BatchRes *res, int nres, const float2 *tw, int *err, cudaStream_t s)
+{
+    if (nres <= 0) return cudaSuccess;
+    RTK_LOGN_CASES(row_batch32, res, nres, tw, err, s)
+}
+
+template <int LOGN> static int row_groups_impl() { return (1 << LOGN) / tma_lpc<LOGN>(); }
+int row_groups32(int logn) { RTK_LOGN_CASES(row_groups_impl) }
+
+template <int LOGN, int C> static cudaError_t col_batch_prep_c()
+{
+    if constexpr (!col_tma_fits<LOGN, C>()) {
+        return cudaErrorInvalidValue;
+    } else {
+        static std::atomic<unsigned long long> mask{0};
+        return ensure_smem(k_col_tma_batch<LOGN, C>, ColPlan<LOGN, C>::total, mask);
+    }
+}
+
+template <int LOGN> static cudaError_t batch_prep32(int colC)
+{
+    static std::atomic<unsigned long long> mask{0};
+    constexpr int LPC = tma_lpc<LOGN>();
+    cudaError_t e = ensure_smem(k_row_tma_batch<LOGN, LPC>, RowPlan<LOGN, LPC>::total, mask);
+    if (e != cudaSuccess) return e;
+    switch (colC) {
+    case 2: return col_batch_prep_c<LOGN, 2>();
+    case 4: return col_batch_prep_c<LOGN, 4>();
+    case 8: return col_batch_prep_c<LOGN, 8>();
+    case 16: return col_batch_prep_c<LOGN, 16>();
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t prepare_batch32(int logn, int colC) { RTK_LOGN_CASES(batch_prep32, colC) }
+
+}  // namespace rtk

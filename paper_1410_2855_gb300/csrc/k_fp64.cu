@@ -25,18 +25,16 @@ static cudaError_t row_fft64(const double2 *in, double2 *out, const double2 *tw,
 {
     constexpr size_t sm = row_smem_bytes<double, LOGN>();
     constexpr int LPC = row_lpc<LOGN>();
-    const GainParams<double> g{};
-    const StatParams st{};
     if (dir < 0) {
         cudaError_t e = row_attr<double, LOGN, MODE_FWD>();
-        auto k = k_row<double, LOGN, MODE_FWD, PE_SG10>;
+        auto k = k_row<double, LOGN, MODE_FWD>;
         if (e != cudaSuccess) return e;
-        k<<<(1 << LOGN) / LPC, LPC * Plan<LOGN>::T, sm, s>>>(in, out, nullptr, tw, nullptr, g, st);
+        k<<<(1 << LOGN) / LPC, LPC * Plan<LOGN>::T, sm, s>>>(in, out, tw, nullptr);
     } else {
         cudaError_t e = row_attr<double, LOGN, MODE_INV>();
-        auto k = k_row<double, LOGN, MODE_INV, PE_SG10>;
+        auto k = k_row<double, LOGN, MODE_INV>;
         if (e != cudaSuccess) return e;
-        k<<<(1 << LOGN) / LPC, LPC * Plan<LOGN>::T, sm, s>>>(in, out, nullptr, tw, nullptr, g, st);
+        k<<<(1 << LOGN) / LPC, LPC * Plan<LOGN>::T, sm, s>>>(in, out, tw, nullptr);
     }
     return cudaGetLastError();
 }
@@ -73,6 +71,41 @@ cudaError_t launch_col_fft64(int logn, double2 *X, const double2 *tw, int dir, c
     RTK_LOGN_CASES(col_fft64, X, tw, dir, s)
 }
 
+// Plain diffraction of a copy of the field (intracavity readout).
+template <int LOGN>
+static cudaError_t row_diff_plain64(const double2 *in, double2 *out, const double2 *tw, const double2 *h,
+                                    cudaStream_t s)
+{
+    constexpr int LPC = row_lpc<LOGN>();
+    cudaError_t e = row_attr<double, LOGN, MODE_DIFF>();
+    if (e != cudaSuccess) return e;
+    k_row<double, LOGN, MODE_DIFF>
+        <<<(1 << LOGN) / LPC, LPC * Plan<LOGN>::T, row_smem_bytes<double, LOGN>(), s>>>(in, out, tw, h);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_diffract_plain64(int logn, const double2 *in, double2 *out, const double2 *tw,
+                                        const double2 *h, cudaStream_t s)
+{
+    RTK_LOGN_CASES(row_diff_plain64, in, out, tw, h, s)
+}
+
+template <int LOGN>
+static cudaError_t col_diff_plain64(double2 *X, const double2 *tw, const double2 *h, cudaStream_t s)
+{
+    constexpr int C = col_c64<LOGN>();
+    cudaError_t e = col_attr<double, LOGN, C, MODE_DIFF>();
+    if (e != cudaSuccess) return e;
+    k_col<double, LOGN, C, MODE_DIFF>
+        <<<(1 << LOGN) / C, C * Plan<LOGN>::T, col_smem_bytes<double, LOGN, C>(), s>>>(X, tw, h);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_col_diffract_plain64(int logn, double2 *X, const double2 *tw, const double2 *h, cudaStream_t s)
+{
+    RTK_LOGN_CASES(col_diff_plain64, X, tw, h, s)
+}
+
 // E[y, x] *= h[x] h[y]: the separable transfer function, 1/n^2 included.
 __global__ void __launch_bounds__(256) k_mul_h64(int n, double2 *E, const double2 *__restrict__ h)
 {
@@ -89,8 +122,8 @@ cudaError_t launch_mul_h64(int n, double2 *E, const double2 *h, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// Local map in FP64 (gain, mirror, absorbing edge, inversion relaxation) and
-// the mean intensity of the new field.
+// Local map in FP64 (gain, mirror with its aperture phase, absorbing edge,
+// inversion relaxation) and the mean intensity of the new field.
 __global__ void __launch_bounds__(256) k_gain64(int n, double2 *E, double *__restrict__ N, GainParams<double> g,
                                                StatParams st)
 {
@@ -104,6 +137,8 @@ __global__ void __launch_bounds__(256) k_gain64(int n, double2 *E, double *__res
         const bool inside = x >= g.edge && x < n - g.edge && y >= g.edge && y < n - g.edge;
         const double gain = inside ? g.sqrtR * exp(0.5 * nn) : 0.0;
         e = cscale(e, gain);
+        if (g.phase) e = cmul(e, g.phase[i]);
+        else if (g.lens) e = cmul(e, cmul(g.lens[x], g.lens[y]));
         const double yc = (double)(y - n / 2) * (2.0 / (double)n);
         const double n0 = pump_value(g, x, y, n, yc * yc);
         N[i] = nn + (n0 - nn * (1.0 + inten * g.invIsat)) * g.invT1;
@@ -134,9 +169,28 @@ cudaError_t launch_tables64(int n, double alpha, double2 *tw, double2 *h, cudaSt
     return cudaGetLastError();
 }
 
+cudaError_t launch_prop64(int n, double alpha, double2 *h, cudaStream_t s)
+{
+    k_prop_table<double2><<<(n + 255) / 256, 256, 0, s>>>(n, alpha, h);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_noise64(int n, unsigned long long seed, double amp, double2 *E, cudaStream_t s)
 {
     k_noise<double2><<<grid_for((size_t)n * n, 256, 2048), 256, 0, s>>>(n, seed, amp, E);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lens64(int n, double c, double2 *lens, cudaStream_t s)
+{
+    k_lens_table<double2><<<(n + 255) / 256, 256, 0, s>>>(n, c / 3.14159265358979323846, lens);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phase64(int n, double c, const double *psi, double2 *phase, cudaStream_t s)
+{
+    k_phase_table<double2><<<grid_for((size_t)n * n, 256, 2048), 256, 0, s>>>(n, c / 3.14159265358979323846, psi,
+                                                                               phase);
     return cudaGetLastError();
 }
 

@@ -78,13 +78,18 @@ struct rt_handle {
     cudaStream_t capture_stream = nullptr;
     void *E = nullptr, *N = nullptr, *tw = nullptr, *h = nullptr;
     void *pump_tab = nullptr;     // N0 table (array pump, FP32 path)
+    void *lens = nullptr;         // per-axis curved-mirror factors (no roughness)
+    void *phase = nullptr;        // n*n aperture factors (roughness, with the lens folded in)
     double *profile = nullptr;    // device copy of the array pump profile
     void *X = nullptr, *S = nullptr;  // spectrum scratch (lazily allocated)
+    void *hz = nullptr;               // propagator of the last intracavity readout distance (lazily allocated)
     double *part = nullptr;
     double *peak_val = nullptr;
     long long *peak_idx = nullptr;
     double *hist = nullptr;
     Ctl *ctl = nullptr;
+    Ctl *slice_ctl = nullptr;     // reduction counters of the slices before the last (m > 1)
+    int slices = 1;
     long long bounces = 0;
     int colC = 4;
     int pe = 0;                   // pump evaluation of the FP32 row sweep (PumpEval)
@@ -93,62 +98,80 @@ struct rt_handle {
     size_t esz() const { return precision == RT_FP64 ? 16 : 8; }
     size_t rsz() const { return precision == RT_FP64 ? 8 : 4; }
     size_t points() const { return (size_t)n * n; }
+    size_t inv_points() const { return points() * (size_t)slices; }
 };
 
 namespace {
 
-StatParams stat_params(rt_handle *h)
+// Statistics of a bounce (the last slice); the slices before it reduce into
+// their own counters and leave the bounce count and history alone.
+StatParams stat_params(rt_handle *h, bool last = true)
 {
     StatParams st{};
+    Ctl *c = last ? h->ctl : h->slice_ctl;
     st.part = h->part;
-    st.count = &h->ctl->count;
-    st.hist = h->hist;
-    st.hist_cap = h->opts.history_cap;
-    st.bounce = &h->ctl->bounce;
-    st.last_mean = &h->ctl->last_mean;
+    st.count = &c->count;
+    st.hist = last ? h->hist : nullptr;
+    st.hist_cap = last ? h->opts.history_cap : 0;
+    st.bounce = &c->bounce;
+    st.last_mean = &c->last_mean;
     st.err = &h->ctl->err;
     return st;
 }
 
+// Local-map parameters of one slice: the pump is N0/m in every slice; the
+// mirror (sqrt R, edge, aperture phase) acts only in the last.
 template <typename R>
-GainParams<R> gain_params(rt_handle *h)
+GainParams<R> gain_params(rt_handle *h, bool last = true)
 {
     GainParams<R> g{};
-    g.sqrtR = (R)std::sqrt(h->R);
+    g.sqrtR = last ? (R)std::sqrt(h->R) : R(1);
     g.invT1 = (R)(1.0 / h->T1);
     g.invIsat = (R)(1.0 / h->opts.Isat);
-    g.g0 = (R)h->g0;
+    g.g0 = (R)(h->g0 / h->slices);
     const double r = h->pump.radius;
     g.inv_rp2 = (R)(1.0 / (r * r));
     const double half = 0.5 * h->pump.order;
     g.half_order = (R)half;
     g.int_half_order = (h->pump.kind == RT_PUMP_SUPERGAUSS && half == 5.0) ? 5 : 0;
-    g.edge = h->opts.edge_px;
+    g.edge = last ? h->opts.edge_px : 0;
     g.pump_kind = h->pump.kind;
     g.pump_tab = reinterpret_cast<const R *>(h->pump_tab);
+    using C = typename cplx_of<R>::type;
+    g.lens = last ? static_cast<const C *>(h->lens) : nullptr;
+    g.phase = last ? static_cast<const C *>(h->phase) : nullptr;
     return g;
 }
 
+// One bounce: per slice (one unless the gain medium is sliced) the
+// diffraction over z/m and the slice's local map on its own inversion.
 cudaError_t enqueue_bounce(rt_handle *h, cudaStream_t s)
 {
-    const StatParams st = stat_params(h);
-    if (h->precision == RT_FP32) {
-        float2 *E = static_cast<float2 *>(h->E);
-        const float2 *tw = static_cast<const float2 *>(h->tw), *hh = static_cast<const float2 *>(h->h);
-        cudaError_t e = launch_col_diffract32(h->logn, h->colC, E, tw, hh, h->tmap, &h->ctl->err, s);
-        if (e != cudaSuccess) return e;
-        return launch_row_diffract_gain32(h->logn, h->pe, E, static_cast<float *>(h->N), tw, hh, gain_params<float>(h), st,
-                                          s);
-    }
-    double2 *E = static_cast<double2 *>(h->E);
-    const double2 *tw = static_cast<const double2 *>(h->tw), *hh = static_cast<const double2 *>(h->h);
+    const size_t P = h->points();
     cudaError_t e;
-    if ((e = launch_row_fft64(h->logn, E, E, tw, -1, s)) != cudaSuccess) return e;
-    if ((e = launch_col_fft64(h->logn, E, tw, -1, s)) != cudaSuccess) return e;
-    if ((e = launch_mul_h64(h->n, E, hh, s)) != cudaSuccess) return e;
-    if ((e = launch_col_fft64(h->logn, E, tw, +1, s)) != cudaSuccess) return e;
-    if ((e = launch_row_fft64(h->logn, E, E, tw, +1, s)) != cudaSuccess) return e;
-    return launch_gain64(h->n, E, static_cast<double *>(h->N), gain_params<double>(h), st, s);
+    for (int k = 0; k < h->slices; ++k) {
+        const bool last = k == h->slices - 1;
+        const StatParams st = stat_params(h, last);
+        if (h->precision == RT_FP32) {
+            float2 *E = static_cast<float2 *>(h->E);
+            const float2 *tw = static_cast<const float2 *>(h->tw), *hh = static_cast<const float2 *>(h->h);
+            if ((e = launch_col_diffract32(h->logn, h->colC, E, tw, hh, h->tmap, &h->ctl->err, s)) != cudaSuccess)
+                return e;
+            e = launch_row_diffract_gain32(h->logn, h->pe, E, static_cast<float *>(h->N) + k * P, tw, hh,
+                                           gain_params<float>(h, last), st, s);
+        } else {
+            double2 *E = static_cast<double2 *>(h->E);
+            const double2 *tw = static_cast<const double2 *>(h->tw), *hh = static_cast<const double2 *>(h->h);
+            if ((e = launch_row_fft64(h->logn, E, E, tw, -1, s)) != cudaSuccess) return e;
+            if ((e = launch_col_fft64(h->logn, E, tw, -1, s)) != cudaSuccess) return e;
+            if ((e = launch_mul_h64(h->n, E, hh, s)) != cudaSuccess) return e;
+            if ((e = launch_col_fft64(h->logn, E, tw, +1, s)) != cudaSuccess) return e;
+            if ((e = launch_row_fft64(h->logn, E, E, tw, +1, s)) != cudaSuccess) return e;
+            e = launch_gain64(h->n, E, static_cast<double *>(h->N) + k * P, gain_params<double>(h, last), st, s);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t get_graph(rt_handle *h, long long k, cudaGraphExec_t *out)
@@ -158,7 +181,9 @@ cudaError_t get_graph(rt_handle *h, long long k, cudaGraphExec_t *out)
         *out = it->second;
         return cudaSuccess;
     }
-    cudaError_t e = h->precision == RT_FP32 ? prepare_bounce32(h->logn, h->colC, h->pe) : prepare_bounce64(h->logn);
+    cudaError_t e = h->precision == RT_FP32 ? prepare_bounce32(h->logn, h->colC, h->pe, h->lens || h->phase)
+                                            : prepare_bounce64(h->logn);
+    if (e == cudaSuccess && h->precision == RT_FP32 && h->slices > 1) e = prepare_row32(h->logn, h->pe, false);
     if (e != cudaSuccess) return e;
     e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
@@ -195,8 +220,8 @@ void release(rt_handle *h)
 {
     for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
-    void *bufs[] = {h->E, h->N, h->tw, h->h, h->pump_tab, h->profile, h->X, h->S,
-                    h->part, h->peak_val, h->peak_idx, h->hist, h->ctl};
+    void *bufs[] = {h->E, h->N, h->tw, h->h, h->pump_tab, h->lens, h->phase, h->profile, h->X, h->S, h->hz,
+                    h->part, h->peak_val, h->peak_idx, h->hist, h->ctl, h->slice_ctl};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
@@ -284,6 +309,7 @@ rt_status rt_create(int n, double fresnel, const rt_pump *pump, double g0, doubl
     if (!finite_pos(o.Isat) || o.edge_px < 0 || o.edge_px > n / 2) return RT_EINVAL;
     if (o.precision != RT_FP32 && o.precision != RT_FP64) return RT_EINVAL;
     if (!std::isfinite(o.noise_amp) || o.noise_amp < 0.0 || !finite_pos(o.pump_diam_over_window)) return RT_EINVAL;
+    if (!std::isfinite(o.z_over_F) || o.slices < 0 || o.slices > 64) return RT_EINVAL;
     if (o.history_cap < 0 || o.chunk < 0) return RT_EINVAL;
     if (o.col_tile != 0 && (o.precision != RT_FP32 || !col_tile_ok32(ilog2(n), o.col_tile))) return RT_EINVAL;
     if (p.kind == RT_PUMP_SUPERGAUSS && (!finite_pos(p.order) || !finite_pos(p.radius))) return RT_EINVAL;
@@ -303,6 +329,8 @@ rt_status rt_create(int n, double fresnel, const rt_pump *pump, double g0, doubl
     h->opts = o;
     h->pump = p;
     h->pump.profile = nullptr;
+    h->opts.roughness = nullptr;
+    h->slices = o.slices > 1 ? o.slices : 1;
     h->stream = static_cast<cudaStream_t>(o.cuda_stream);
     h->colC = o.col_tile ? o.col_tile : default_col_tile32(h->logn);
     // N0 on the fly for the order-10 super-Gaussian and the uniform pump, else from a table
@@ -327,36 +355,66 @@ rt_status rt_create(int n, double fresnel, const rt_pump *pump, double g0, doubl
     const size_t P = h->points();
     RT_CREATE_TRY(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
     RT_CREATE_TRY(cudaMalloc(&h->E, P * h->esz()));
-    RT_CREATE_TRY(cudaMalloc(&h->N, P * h->rsz()));
+    RT_CREATE_TRY(cudaMalloc(&h->N, h->inv_points() * h->rsz()));
     RT_CREATE_TRY(cudaMalloc(&h->tw, (size_t)(twiddle_entries(h->logn) + 1) * h->esz()));
     RT_CREATE_TRY(cudaMalloc(&h->h, (size_t)n * h->esz()));
     RT_CREATE_TRY(cudaMalloc(&h->part, sizeof(double) * kMaxPart));
     RT_CREATE_TRY(cudaMalloc(reinterpret_cast<void **>(&h->ctl), sizeof(Ctl)));
     RT_CREATE_TRY(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->stream));
+    if (h->slices > 1) {
+        RT_CREATE_TRY(cudaMalloc(reinterpret_cast<void **>(&h->slice_ctl), sizeof(Ctl)));
+        RT_CREATE_TRY(cudaMemsetAsync(h->slice_ctl, 0, sizeof(Ctl), h->stream));
+    }
     if (o.history_cap > 0) RT_CREATE_TRY(cudaMalloc(&h->hist, sizeof(double) * (size_t)o.history_cap));
     if (p.kind == RT_PUMP_ARRAY) {
         RT_CREATE_TRY(cudaMalloc(&h->profile, sizeof(double) * P));
         RT_CREATE_TRY(cudaMemcpyAsync(h->profile, p.profile, sizeof(double) * P, cudaMemcpyDefault, h->stream));
     }
+    // Aperture phase: a full table when the mirror is rough (lens folded in),
+    // else per-axis lens factors when it is curved, else nothing.
+    const double c = lens_curvature(h->alpha, o.z_over_F);
+    const double g0s = g0 / h->slices;   // pump of one slice: N0/m
+    double *psi = nullptr;
+    if (o.roughness) {
+        RT_CREATE_TRY(cudaMalloc(&h->phase, P * h->esz()));
+        RT_CREATE_TRY(cudaMalloc(&psi, sizeof(double) * P));
+        cudaError_t e = cudaMemcpyAsync(psi, o.roughness, sizeof(double) * P, cudaMemcpyDefault, h->stream);
+        if (e == cudaSuccess)
+            e = h->precision == RT_FP32 ? launch_phase32(n, c, psi, static_cast<float2 *>(h->phase), h->stream)
+                                        : launch_phase64(n, c, psi, static_cast<double2 *>(h->phase), h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        cudaFree(psi);
+        RT_CREATE_TRY(e);
+    } else if (o.z_over_F != 0.0) {
+        RT_CREATE_TRY(cudaMalloc(&h->lens, (size_t)n * h->esz()));
+        RT_CREATE_TRY(h->precision == RT_FP32 ? launch_lens32(n, c, static_cast<float2 *>(h->lens), h->stream)
+                                              : launch_lens64(n, c, static_cast<double2 *>(h->lens), h->stream));
+    }
 
     if (h->precision == RT_FP32) {
-        RT_CREATE_TRY(launch_tables32(n, h->alpha, static_cast<float2 *>(h->tw), static_cast<float2 *>(h->h), h->stream));
+        RT_CREATE_TRY(launch_tables32(n, h->alpha / h->slices, static_cast<float2 *>(h->tw), static_cast<float2 *>(h->h),
+                                      h->stream));
         RT_CREATE_TRY(make_col_tensor_map(h->tmap, static_cast<float2 *>(h->E), n, h->colC));
         RT_CREATE_TRY(launch_noise32(n, o.seed, o.noise_amp, static_cast<float2 *>(h->E), h->stream));
-        RT_CREATE_TRY(launch_pump32(n, p.kind, g0, p.order, p.radius, h->profile, static_cast<float *>(h->N), h->stream));
+        RT_CREATE_TRY(launch_pump32(n, p.kind, g0s, p.order, p.radius, h->profile, static_cast<float *>(h->N), h->stream));
         if (h->pe == 2) {
             RT_CREATE_TRY(cudaMalloc(&h->pump_tab, sizeof(float) * P));
             RT_CREATE_TRY(cudaMemcpyAsync(h->pump_tab, h->N, sizeof(float) * P, cudaMemcpyDeviceToDevice, h->stream));
         }
     } else {
-        RT_CREATE_TRY(launch_tables64(n, h->alpha, static_cast<double2 *>(h->tw), static_cast<double2 *>(h->h), h->stream));
+        RT_CREATE_TRY(launch_tables64(n, h->alpha / h->slices, static_cast<double2 *>(h->tw),
+                                      static_cast<double2 *>(h->h), h->stream));
         RT_CREATE_TRY(launch_noise64(n, o.seed, o.noise_amp, static_cast<double2 *>(h->E), h->stream));
-        RT_CREATE_TRY(launch_pump64(n, p.kind, g0, p.order, p.radius, h->profile, static_cast<double *>(h->N), h->stream));
+        RT_CREATE_TRY(launch_pump64(n, p.kind, g0s, p.order, p.radius, h->profile, static_cast<double *>(h->N), h->stream));
         if (h->pe == 2) {
             RT_CREATE_TRY(cudaMalloc(&h->pump_tab, sizeof(double) * P));
             RT_CREATE_TRY(cudaMemcpyAsync(h->pump_tab, h->N, sizeof(double) * P, cudaMemcpyDeviceToDevice, h->stream));
         }
     }
+    // every slice starts fully pumped: N0/m
+    for (int k = 1; k < h->slices; ++k)
+        RT_CREATE_TRY(cudaMemcpyAsync(static_cast<char *>(h->N) + k * P * h->rsz(), h->N, P * h->rsz(),
+                                      cudaMemcpyDeviceToDevice, h->stream));
     RT_CREATE_TRY(cudaStreamSynchronize(h->stream));
 #undef RT_CREATE_TRY
     *out = h;
@@ -382,7 +440,8 @@ rt_status rt_step(rt_handle *h, long long nb)
 
 rt_status rt_sweep(rt_handle *h, int which)
 {
-    if (!h || h->precision != RT_FP32 || (which != RT_SWEEP_COLUMNS && which != RT_SWEEP_ROWS)) return RT_EINVAL;
+    if (!h || h->precision != RT_FP32 || h->slices > 1 || (which != RT_SWEEP_COLUMNS && which != RT_SWEEP_ROWS))
+        return RT_EINVAL;
     DeviceGuard dg(h->device);
     float2 *E = static_cast<float2 *>(h->E);
     const float2 *tw = static_cast<const float2 *>(h->tw), *hh = static_cast<const float2 *>(h->h);
@@ -421,7 +480,7 @@ rt_status rt_read_field(rt_handle *h, void *dst, size_t bytes)
 rt_status rt_read_inversion(rt_handle *h, void *dst, size_t bytes)
 {
     if (!h) return RT_EINVAL;
-    return copy_out(h, dst, h->N, bytes, h->points() * h->rsz());
+    return copy_out(h, dst, h->N, bytes, h->inv_points() * h->rsz());
 }
 
 static rt_status copy_in(rt_handle *h, void *dst, const void *src, size_t bytes, size_t want)
@@ -442,7 +501,7 @@ rt_status rt_write_field(rt_handle *h, const void *src, size_t bytes)
 rt_status rt_write_inversion(rt_handle *h, const void *src, size_t bytes)
 {
     if (!h) return RT_EINVAL;
-    return copy_in(h, h->N, src, bytes, h->points() * h->rsz());
+    return copy_in(h, h->N, src, bytes, h->inv_points() * h->rsz());
 }
 
 rt_status rt_set_bounces(rt_handle *h, long long bounces)
@@ -507,6 +566,32 @@ rt_status rt_read_spectrum(rt_handle *h, void *dst, size_t bytes)
     rt_status st = compute_spectrum(h);
     if (st != RT_OK) return st;
     RT_TRY(cudaMemcpyAsync(dst, h->S, bytes, cudaMemcpyDefault, h->stream));
+    return check_device_error(h);
+}
+
+rt_status rt_read_field_at(rt_handle *h, double zeta, void *dst, size_t bytes)
+{
+    if (!h || !dst || !std::isfinite(zeta)) return RT_EINVAL;
+    if (bytes != h->points() * h->esz()) return RT_EINVAL;
+    DeviceGuard dg(h->device);
+    rt_status st = ensure_spectrum_scratch(h);
+    if (st != RT_OK) return st;
+    if (!h->hz) RT_TRY(cudaMalloc(&h->hz, (size_t)h->n * h->esz()));
+    const double a = h->alpha * zeta;
+    if (h->precision == RT_FP32) {
+        const float2 *tw = static_cast<const float2 *>(h->tw);
+        float2 *X = static_cast<float2 *>(h->X), *hz = static_cast<float2 *>(h->hz);
+        RT_TRY(launch_prop32(h->n, a, hz, h->stream));
+        RT_TRY(launch_row_diffract_plain32(h->logn, static_cast<const float2 *>(h->E), X, tw, hz, h->stream));
+        RT_TRY(launch_col_diffract_plain32(h->logn, X, tw, hz, h->stream));
+    } else {
+        const double2 *tw = static_cast<const double2 *>(h->tw);
+        double2 *X = static_cast<double2 *>(h->X), *hz = static_cast<double2 *>(h->hz);
+        RT_TRY(launch_prop64(h->n, a, hz, h->stream));
+        RT_TRY(launch_row_diffract_plain64(h->logn, static_cast<const double2 *>(h->E), X, tw, hz, h->stream));
+        RT_TRY(launch_col_diffract_plain64(h->logn, X, tw, hz, h->stream));
+    }
+    RT_TRY(cudaMemcpyAsync(dst, h->X, bytes, cudaMemcpyDefault, h->stream));
     return check_device_error(h);
 }
 

@@ -168,7 +168,7 @@ rt_status rt_batch_create(const rt_job *jobs, int count, const rt_opts *opts, rt
     rt_opts o;
     if (opts) o = *opts;
     else rt_opts_default(&o);
-    if (o.precision != RT_FP32 || o.history_cap < 0 || o.chunk < 0) return RT_EINVAL;
+    if (o.precision != RT_FP32 || o.history_cap < 0 || o.chunk < 0 || o.slices > 1) return RT_EINVAL;
     for (int i = 0; i < count; ++i)
         if (!job_ok(jobs[i])) return RT_EINVAL;
     rt_batch *b = new (std::nothrow) rt_batch();
@@ -213,7 +213,7 @@ rt_status rt_batch_create(const rt_job *jobs, int count, const rt_opts *opts, rt
     }
     for (int i = 0; i < count; ++i) {
         Slot &s = b->slots[i];
-        cudaError_t e = slot_alloc(s.job.n, hist_cap(b), pump_eval(s.job.pump) == PE_TABLE, &s.buf);
+        cudaError_t e = slot_alloc(s.job.n, hist_cap(b), pump_eval(s.job.pump) == PE_TABLE, job_rough(s.job), &s.buf);
         if (e != cudaSuccess) return fail(cuda_to_status(e));
         if ((e = start_slot(b, i)) != cudaSuccess) return fail(cuda_to_status(e));
     }
@@ -256,8 +256,9 @@ rt_status rt_batch_set_job(rt_batch *b, int i, const rt_job *job, long long n_bo
 {
     if (!valid_slot(b, i) || !job || !job_ok(*job)) return RT_EINVAL;
     Slot &s = b->slots[i];
-    // Same grid size only; a table pump needs a slot created with one.
+    // Same grid size only; a table pump or a rough mirror needs a slot created with one.
     if (job->n != s.job.n || (pump_eval(job->pump) == PE_TABLE && !s.buf.pump_tab)) return RT_EINVAL;
+    if (job_rough(*job) && !s.buf.phase) return RT_EINVAL;
     DeviceGuard g(b->device);
     s.job = *job;
     s.target = n_bounces < 0 ? LLONG_MAX : n_bounces;

@@ -15,8 +15,15 @@ enum PumpKind { PUMP_SUPERGAUSS = 0, PUMP_UNIFORM = 1, PUMP_ARRAY = 2 };
 // any other super-Gaussian order).
 enum PumpEval { PE_SG10 = 0, PE_UNIFORM = 1, PE_TABLE = 2 };
 
-// Local map parameters: E <- sqrtR * A * exp(N/2) * E',
-// N <- N + (N0 - N (1 + I invIsat)) invT1, N0 = g0 * P(x, y).
+template <typename R> struct cplx_of;
+template <> struct cplx_of<float> { using type = float2; };
+template <> struct cplx_of<double> { using type = double2; };
+
+// Local map parameters: E <- sqrtR * A * D * exp(N/2) * E',
+// N <- N + (N0 - N (1 + I invIsat)) invT1, N0 = g0 * P(x, y).  D is the
+// phase of the complex aperture (curved mirror and roughness, eq.
+// complex_aperture2): either a separable lens, D = lens[x] lens[y], or a full
+// table D = phase[y n + x]; neither pointer set means D = 1.
 template <typename R>
 struct GainParams {
     R sqrtR, invT1, invIsat, g0;
@@ -26,6 +33,8 @@ struct GainParams {
     int edge;
     int pump_kind;
     const R *pump_tab;  // n*n N0 values when pump_kind == PUMP_ARRAY
+    const typename cplx_of<R>::type *lens;   // n per-axis factors exp(-i c x_j^2), or null
+    const typename cplx_of<R>::type *phase;  // n*n factors exp(-i (c (x^2 + y^2) + psi)), or null (wins over lens)
 };
 
 // Per-bounce mean intensity: block partials, reduced by the last block to
@@ -80,21 +89,37 @@ cudaError_t launch_col_diffract32(int logn, int colC, float2 *E, const float2 *t
 // tiles of colC columns (copy-engine loads of the column sweep).
 cudaError_t make_col_tensor_map(void *map, float2 *E, int n, int colC);
 // Row sweep: per row, forward FFT, x h(mx), inverse FFT, then the local map
-// (gain, mirror, edge, inversion update) and the mean-intensity reduction.
-// pe selects how N0 is evaluated: 0 super-Gaussian of order 10 on the fly,
-// 1 uniform, 2 from GainParams::pump_tab.
+// (gain, mirror phase, edge, inversion update) and the mean-intensity
+// reduction.  pe selects how N0 is evaluated: 0 super-Gaussian of order 10
+// on the fly, 1 uniform, 2 from GainParams::pump_tab.  The aperture-phase
+// form of the kernel runs when g.lens or g.phase is set.
 cudaError_t launch_row_diffract_gain32(int logn, int pe, float2 *E, float *N, const float2 *tw, const float2 *h,
                                        const GainParams<float> &g, const StatParams &st, cudaStream_t s);
-int row_blocks32(int logn);            // blocks of the row sweep (size of StatParams::part)
+int row_blocks32(int logn);            // most blocks of a row sweep (size of StatParams::part)
 // Set kernel attributes (shared-memory opt-in) of a bounce's kernels on the
 // current device; done before capturing a bounce into a CUDA graph.
-cudaError_t prepare_bounce32(int logn, int colC, int pe);
+// ap: the row sweep applies an aperture phase.
+cudaError_t prepare_bounce32(int logn, int colC, int pe, bool ap);
+cudaError_t prepare_row32(int logn, int pe, bool ap);
+cudaError_t prepare_col32(int logn, int colC);
 cudaError_t prepare_bounce64(int logn);
 int col_tile_ok32(int logn, int colC); // 1 if that column tile width is instantiated and fits
 int default_col_tile32(int logn);      // column tile width used when none is requested (tuned or built in)
 int builtin_col_tile32(int logn);      // the built-in choice
 int set_tuned_col_tile32(int logn, int colC);  // record a tuned width (0 clears); 1 on success
 int tuned_col_tile32(int logn);        // tuned width or 0
+
+// Plain diffraction of a copy of the field (intracavity readout): rows out
+// of place (in -> out), then columns in place, each forward FFT, x h,
+// inverse FFT; h from launch_prop32/64 for the distance wanted.
+cudaError_t launch_row_diffract_plain32(int logn, const float2 *in, float2 *out, const float2 *tw, const float2 *h,
+                                        cudaStream_t s);
+cudaError_t launch_col_diffract_plain32(int logn, float2 *X, const float2 *tw, const float2 *h, cudaStream_t s);
+cudaError_t launch_row_diffract_plain64(int logn, const double2 *in, double2 *out, const double2 *tw,
+                                        const double2 *h, cudaStream_t s);
+cudaError_t launch_col_diffract_plain64(int logn, double2 *X, const double2 *tw, const double2 *h, cudaStream_t s);
+cudaError_t launch_prop32(int n, double alpha, float2 *h, cudaStream_t s);
+cudaError_t launch_prop64(int n, double alpha, double2 *h, cudaStream_t s);
 
 // Forward 2-D transform helpers (spectrum readout), FP32: rows out of place, columns in place.
 cudaError_t launch_row_fft32(int logn, const float2 *in, float2 *out, const float2 *tw, int dir, cudaStream_t s);
@@ -117,6 +142,16 @@ cudaError_t launch_tables32(int n, double alpha, float2 *tw, float2 *h, cudaStre
 cudaError_t launch_tables64(int n, double alpha, double2 *tw, double2 *h, cudaStream_t s);
 cudaError_t launch_noise32(int n, unsigned long long seed, double amp, float2 *E, cudaStream_t s);
 cudaError_t launch_noise64(int n, unsigned long long seed, double amp, double2 *E, cudaStream_t s);
+// Aperture phase factors, FP64 arithmetic (eq. complex_aperture2 conjugated
+// like the propagator): theta = c (x^2 + y^2) + psi(x, y) with
+// c = (pi / (4 alpha)) (z / F), factor exp(-i theta).  lens: the n per-axis
+// factors exp(-i c x_j^2); phase: the n*n factors with psi (device array of
+// n*n doubles, or null for psi = 0).
+double lens_curvature(double alpha, double z_over_F);
+cudaError_t launch_lens32(int n, double c, float2 *lens, cudaStream_t s);
+cudaError_t launch_lens64(int n, double c, double2 *lens, cudaStream_t s);
+cudaError_t launch_phase32(int n, double c, const double *psi, float2 *phase, cudaStream_t s);
+cudaError_t launch_phase64(int n, double c, const double *psi, double2 *phase, cudaStream_t s);
 // N0 = g0 * P in FP64 (profile: device array of n*n doubles or null), stored as R.
 cudaError_t launch_pump32(int n, int kind, double g0, double order, double radius, const double *profile,
                           float *out, cudaStream_t s);

@@ -8,6 +8,7 @@
 //   [256, +kMaxN*8)           per-axis propagator table h (n complex64)
 //   [.., +kTwMax*8)           pass-major twiddle table (complex64)
 //   [.., +kPartMax*8)         block partial sums of the mean intensity
+//   [.., +kMaxN*8)            per-axis curved-mirror factors (n complex64)
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -24,7 +25,8 @@ constexpr size_t kTwMax = 4096;    // >= twiddle_entries(log2 n) for n <= 4096
 constexpr size_t kPartMax = 4096;  // >= blocks of any row-sweep launch
 constexpr size_t kTwBytes = kTwMax * sizeof(float2);
 constexpr size_t kPartBytes = kPartMax * sizeof(double);
-constexpr size_t kScratchBytes = kCtlBytes + kHBytes + kTwBytes + kPartBytes;
+constexpr size_t kLensBytes = (size_t)kMaxN * sizeof(float2);
+constexpr size_t kScratchBytes = kCtlBytes + kHBytes + kTwBytes + kPartBytes + kLensBytes;
 
 struct NoAllocCtl {
     unsigned int count;
@@ -84,7 +86,7 @@ extern "C" rt_status rt_step_noalloc(int n, double fresnel, const rt_pump *pump,
     if (!fpos(fresnel) || !std::isfinite(g0) || g0 < 0.0 || !std::isfinite(T1) || T1 < 1.0) return RT_EINVAL;
     if (!std::isfinite(R) || R <= 0.0 || R > 1.0 || n_bounces < 0) return RT_EINVAL;
     if (!fpos(o.Isat) || o.edge_px < 0 || o.edge_px > n / 2 || !fpos(o.pump_diam_over_window)) return RT_EINVAL;
-    if (o.precision != RT_FP32) return RT_EINVAL;
+    if (o.precision != RT_FP32 || !std::isfinite(o.z_over_F) || o.roughness || o.slices > 1) return RT_EINVAL;
     const bool sg10 = p.kind == RT_PUMP_SUPERGAUSS && p.order == 10.0 && fpos(p.radius);
     if (!sg10 && p.kind != RT_PUMP_UNIFORM) return RT_EINVAL;
     if (!field || !inversion) return RT_EINVAL;
@@ -103,6 +105,7 @@ extern "C" rt_status rt_step_noalloc(int n, double fresnel, const rt_pump *pump,
     float2 *h = reinterpret_cast<float2 *>(base + kCtlBytes);
     float2 *tw = reinterpret_cast<float2 *>(base + kCtlBytes + kHBytes);
     double *part = reinterpret_cast<double *>(base + kCtlBytes + kHBytes + kTwBytes);
+    float2 *lens = reinterpret_cast<float2 *>(base + kCtlBytes + kHBytes + kTwBytes + kPartBytes);
 
     cudaStream_t s = static_cast<cudaStream_t>(o.cuda_stream);
     float2 *E = static_cast<float2 *>(field);
@@ -114,6 +117,9 @@ extern "C" rt_status rt_step_noalloc(int n, double fresnel, const rt_pump *pump,
     // The array keeps whatever the previous call left: the counters must start at zero.
     if (cudaMemsetAsync(ctl, 0, sizeof(NoAllocCtl), s) != cudaSuccess) return RT_ECUDA;
     if (rtk::launch_tables32(n, alpha, tw, h, s) != cudaSuccess) return RT_ECUDA;
+    const bool curved = o.z_over_F != 0.0;
+    if (curved && rtk::launch_lens32(n, rtk::lens_curvature(alpha, o.z_over_F), lens, s) != cudaSuccess)
+        return RT_ECUDA;
 
     rtk::GainParams<float> g{};
     g.sqrtR = (float)std::sqrt(R);
@@ -126,6 +132,8 @@ extern "C" rt_status rt_step_noalloc(int n, double fresnel, const rt_pump *pump,
     g.edge = o.edge_px;
     g.pump_kind = p.kind;
     g.pump_tab = nullptr;
+    g.lens = curved ? lens : nullptr;
+    g.phase = nullptr;
     rtk::StatParams sp{};
     sp.part = part;
     sp.count = &ctl->count;

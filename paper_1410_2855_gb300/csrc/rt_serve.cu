@@ -84,7 +84,7 @@ namespace {
 
 constexpr long long kHistCap = 0;
 
-size_t request_bytes(const rt_job &j) { return slot_bytes(j.n, kHistCap, false); }
+size_t request_bytes(const rt_job &j) { return slot_bytes(j.n, kHistCap, false, false); }
 
 cudaError_t class_init(rt_server *s, SClass &c, int logn)
 {
@@ -136,7 +136,7 @@ bool admit(rt_server *s, Request &r)
         if (s->resident + need > s->opts.budget_bytes) make_room(s, need, logn);
         if (s->resident + need > s->opts.budget_bytes) return false;
         SSlot ns;
-        if (slot_alloc(r.job.n, kHistCap, false, &ns.buf) != cudaSuccess) return false;
+        if (slot_alloc(r.job.n, kHistCap, false, false, &ns.buf) != cudaSuccess) return false;
         s->resident += (long long)ns.buf.bytes;
         c.slots.push_back(ns);
         idx = (int)c.slots.size() - 1;
@@ -359,7 +359,7 @@ rt_status rt_serve_create(const rt_serve_opts *opts, rt_server **out)
 rt_status rt_serve_submit(rt_server *s, const rt_job *job, long long n_bounces, void *field_out, long long *id)
 {
     if (!s || !job || !id || n_bounces <= 0 || !job_ok(*job)) return RT_EINVAL;
-    if (pump_eval(job->pump) == PE_TABLE) return RT_EINVAL;
+    if (pump_eval(job->pump) == PE_TABLE || job_rough(*job)) return RT_EINVAL;
     if ((long long)request_bytes(*job) > s->opts.budget_bytes) return RT_EINVAL;
     Request r;
     r.job = *job;

@@ -33,6 +33,49 @@ __global__ void k_prop_table(int n, double alpha, V *h)
     h[k] = cmk<V>(cp * inv, -sp * inv);
 }
 
+// Phase of the complex aperture (eq. complex_aperture2) as the library
+// applies it: theta(x, y) = c (x^2 + y^2) + psi(x, y), factor exp(-i theta)
+// (the conjugate of the printed exp(+i theta), matching the propagator's
+// sign), with x_j = (j - n/2) / (n/2).  c / pi times x^2 (exact: x is a
+// short dyadic fraction) is split into a rounded product and its FMA
+// residual and reduced modulo 2 before sincospi, like the propagator.
+__device__ __forceinline__ double lens_turns(double c_over_pi, double q)
+{
+    const double hi = c_over_pi * q;
+    const double lo = fma(c_over_pi, q, -hi);
+    return fmod(hi, 2.0) + lo;
+}
+
+// Separable lens factors lens[j] = exp(-i c x_j^2), one axis.
+template <typename V>
+__global__ void k_lens_table(int n, double c_over_pi, V *lens)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double x = (double)(j - n / 2) / (double)(n / 2);
+    double sp, cp;
+    sincospi(lens_turns(c_over_pi, x * x), &sp, &cp);
+    lens[j] = cmk<V>(cp, -sp);
+}
+
+// Full aperture factors exp(-i (c (x^2 + y^2) + psi[y n + x])); psi may be null.
+template <typename V>
+__global__ void k_phase_table(int n, double c_over_pi, const double *psi, V *phase)
+{
+    const size_t P = (size_t)n * n;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < P; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % n), y = (int)(i / n);
+        const double xc = (double)(x - n / 2) / (double)(n / 2);
+        const double yc = (double)(y - n / 2) / (double)(n / 2);
+        double sl, cl;
+        sincospi(lens_turns(c_over_pi, xc * xc + yc * yc), &sl, &cl);
+        double sr = 0.0, cr = 1.0;
+        if (psi) sincos(psi[i], &sr, &cr);
+        // exp(-i (a + b)) = (cos a cos b - sin a sin b) - i (sin a cos b + cos a sin b)
+        phase[i] = cmk<V>(cl * cr - sl * sr, -(sl * cr + cl * sr));
+    }
+}
+
 // Pass-major twiddle table of the line FFT of length 2^logn (layout in
 // fft_core.cuh): for each pass after the first, with span Ns and radix R,
 // entry (r-1)*Ns + j holds exp(-2 pi i r j / (Ns R)).  FP64 sincospi on the

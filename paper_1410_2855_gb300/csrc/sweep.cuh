@@ -19,7 +19,7 @@
 
 namespace rtk {
 
-enum SweepMode { MODE_FWD = 0, MODE_INV = 1, MODE_DIFF = 2, MODE_DIFF_GAIN = 3 };
+enum SweepMode { MODE_FWD = 0, MODE_INV = 1, MODE_DIFF = 2 };
 
 // Lines per block of a row sweep: about 256 threads.
 template <int LOGN> constexpr int row_lpc()
@@ -97,16 +97,16 @@ __device__ __forceinline__ void finish_mean(double v, const StatParams &st, doub
     }
 }
 
-// Row sweep.  Each group of T threads owns one row.  `in` and `out` may alias
-// (in-place): a block reads all its rows before it writes any.
-template <typename R, int LOGN, int MODE, int PE>
+// Row transforms (readout and the plain FP64 path).  Each group of T threads
+// owns one row.  `in` and `out` may alias (in-place): a block reads all its
+// rows before it writes any.
+template <typename R, int LOGN, int MODE>
 __global__ void __launch_bounds__(row_lpc<LOGN>() * Plan<LOGN>::T, min_blocks(row_lpc<LOGN>() * Plan<LOGN>::T))
-k_row(const cv<R> *in, cv<R> *out, R *__restrict__ Nv, const cv<R> *__restrict__ tw,
-      const cv<R> *__restrict__ h, GainParams<R> g, StatParams st)
+k_row(const cv<R> *in, cv<R> *out, const cv<R> *__restrict__ tw, const cv<R> *__restrict__ h)
 {
     using V = cv<R>;
     using P = Plan<LOGN>;
-    constexpr int N = P::N, T = P::T, LPC = row_lpc<LOGN>(), NT = LPC * T, LS = padded_len(N);
+    constexpr int N = P::N, T = P::T, LPC = row_lpc<LOGN>(), LS = padded_len(N);
     extern __shared__ __align__(16) unsigned char smraw[];
     V *line = reinterpret_cast<V *>(smraw) + (threadIdx.x / T) * LS;
     const int t = threadIdx.x % T;
@@ -131,42 +131,8 @@ k_row(const cv<R> *in, cv<R> *out, R *__restrict__ Nv, const cv<R> *__restrict__
         fft_line<LOGN, +1, 1>(v, t, lb, tw, sync);
     }
     V *dst = out + (size_t)row * N + t;
-    if constexpr (MODE == MODE_DIFF_GAIN) {
-        const R step = R(2) / R(N);
-        const R yc = R(row - N / 2) * step;
-        const R yq = yc * yc * g.inv_rp2;
-        const R xc0 = R(t - N / 2) * step;
-        const bool row_in = row >= g.edge && row < N - g.edge;
-        R *Nrow = Nv + (size_t)row * N + t;
-        R acc = R(0);
 #pragma unroll
-        for (int s = 0; s < 16; ++s) {
-            const int x = t + s * T;
-            const R nn = Nrow[s * T];
-            V e = v[s];
-            const R inten = e.x * e.x + e.y * e.y;
-            const bool inside = row_in && x >= g.edge && x < N - g.edge;
-            e = cscale(e, inside ? g.sqrtR * fexp(R(0.5) * nn) : R(0));
-            R n0;
-            if constexpr (PE == PE_UNIFORM) {
-                n0 = g.g0;
-            } else if constexpr (PE == PE_TABLE) {
-                n0 = __ldg(g.pump_tab + (size_t)row * N + x);
-            } else {
-                const R xc = xc0 + R(s * T) * step;
-                const R q = xc * xc * g.inv_rp2 + yq;
-                const R q2 = q * q;
-                n0 = g.g0 * fexp(-(q2 * q2 * q));
-            }
-            Nrow[s * T] = nn + (n0 - nn * (R(1) + inten * g.invIsat)) * g.invT1;
-            dst[s * T] = e;
-            acc += e.x * e.x + e.y * e.y;
-        }
-        finish_mean<NT>((double)acc, st, 1.0 / ((double)N * (double)N));
-    } else {
-#pragma unroll
-        for (int s = 0; s < 16; ++s) dst[s * T] = v[s];
-    }
+    for (int s = 0; s < 16; ++s) dst[s * T] = v[s];
 }
 
 // Column sweep on a tile of C adjacent columns.  Thread (c, t) with c the
@@ -229,11 +195,11 @@ inline cudaError_t ensure_smem(K kernel, size_t bytes, std::atomic<unsigned long
     return e;
 }
 
-template <typename R, int LOGN, int MODE, int PE = PE_SG10>
+template <typename R, int LOGN, int MODE>
 inline cudaError_t row_attr()
 {
     static std::atomic<unsigned long long> mask{0};
-    return ensure_smem(k_row<R, LOGN, MODE, PE>, row_smem_bytes<R, LOGN>(), mask);
+    return ensure_smem(k_row<R, LOGN, MODE>, row_smem_bytes<R, LOGN>(), mask);
 }
 
 template <typename R, int LOGN, int C, int MODE>

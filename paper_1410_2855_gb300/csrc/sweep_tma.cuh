@@ -126,8 +126,10 @@ __device__ __forceinline__ void init_stage_barriers(uint64_t *bar)
 
 // Local map of one row held in registers (slot s = column t + T s):
 // gain against the frozen inversion, mirror, absorbing edge, inversion
-// relaxation.  Returns sum |E_new|^2 over the thread's 16 elements.
-template <int LOGN, int PE, bool STAGED_N0 = false>
+// relaxation; with AP also the aperture phase D (curved mirror, roughness),
+// from g.phase when set, else the separable g.lens (one of them must be set).
+// Returns sum |E_new|^2 over the thread's 16 elements.
+template <int LOGN, int PE, bool STAGED_N0 = false, bool AP = false>
 __device__ __forceinline__ float row_local_map(float2 (&v)[16], int t, int row, const float *nrow, float2 *erow,
                                                float *ngl, const GainParams<float> &g, const float *n0row = nullptr)
 {
@@ -137,6 +139,17 @@ __device__ __forceinline__ float row_local_map(float2 (&v)[16], int t, int row, 
     const float yc = (float)(row - N / 2) * step;
     const float yq = yc * yc * g.inv_rp2;
     const bool row_in = row >= g.edge && row < N - g.edge;
+    // Aperture factor of element x: drow * dtab[x] (sqrtR folded into drow).
+    const float2 *dtab = nullptr;
+    float2 drow = make_float2(g.sqrtR, 0.0f);
+    if constexpr (AP) {
+        if (g.phase) {
+            dtab = g.phase + (size_t)row * N + t;
+        } else {
+            dtab = g.lens + t;
+            drow = cscale(__ldg(g.lens + row), g.sqrtR);
+        }
+    }
     float acc = 0.0f;
 #pragma unroll
     for (int si = 0; si < 16; ++si) {
@@ -145,7 +158,11 @@ __device__ __forceinline__ float row_local_map(float2 (&v)[16], int t, int row, 
         float2 e = v[si];
         const float inten = e.x * e.x + e.y * e.y;
         const bool inside = row_in && x >= g.edge && x < N - g.edge;
-        e = cscale(e, inside ? g.sqrtR * fexp(0.5f * nn) : 0.0f);
+        if constexpr (AP) {
+            e = cscale(cmul(e, cmul(drow, __ldg(dtab + si * T))), inside ? fexp(0.5f * nn) : 0.0f);
+        } else {
+            e = cscale(e, inside ? g.sqrtR * fexp(0.5f * nn) : 0.0f);
+        }
         float n0;
         if constexpr (PE == PE_UNIFORM) {
             n0 = g.g0;
@@ -229,7 +246,7 @@ __device__ __forceinline__ void item_finish(double v, const StatParams &st, int 
 
 // Row sweep: LPC rows per group, T = n/16 threads per row.  With a pump
 // table (PE_TABLE) the rows' N0 values are staged by the copy engine too.
-template <int LOGN, int LPC, int PE, bool PP = RTK_ROW_PP>
+template <int LOGN, int LPC, int PE, bool AP = false, bool PP = RTK_ROW_PP>
 __global__ void __launch_bounds__(LPC * Plan<LOGN>::T, smem_blocks(RowStage<LOGN, LPC, PP, PE == PE_TABLE>::total))
 k_row_tma(float2 *E, float *Nv, const float2 *__restrict__ tw, const float2 *__restrict__ h, GainParams<float> g,
           StatParams st, int ngroups)
@@ -279,7 +296,7 @@ k_row_tma(float2 *E, float *Nv, const float2 *__restrict__ tw, const float2 *__r
         float2 *extra = reinterpret_cast<float2 *>(sm + 128 + 2 * L::stage) + lig * LS;
         LineBufs<float2, PP> lb{{PP ? extra : line, line}, 0};
         diffract_line<LOGN, 1>(v, t, lb, tw, h, sync);
-        dacc += (double)row_local_map<LOGN, PE, TAB>(v, t, row, stage_n(s) + lig * N + t, E + (size_t)row * N + t,
+        dacc += (double)row_local_map<LOGN, PE, TAB, AP>(v, t, row, stage_n(s) + lig * N + t, E + (size_t)row * N + t,
                                                      Nv + (size_t)row * N + t, g, stage_t(s) + lig * N + t);
         __syncthreads();  // stage s fully consumed before it is refilled
     }
@@ -335,7 +352,8 @@ k_col_tma(float2 *E, const float2 *__restrict__ tw, const float2 *__restrict__ h
 // ---- batches of resonators of one grid size -----------------------------------
 
 // Row sweep over nres resonators: item i is row group i % G of resonator
-// i / G, G = n / LPC.  The pump evaluation is chosen per resonator.
+// i / G, G = n / LPC.  The pump evaluation and the aperture phase are chosen
+// per resonator.
 template <int LOGN, int LPC, bool PP = RTK_ROW_PP>
 __global__ void __launch_bounds__(LPC * Plan<LOGN>::T, smem_blocks(RowStage<LOGN, LPC, PP>::total))
 k_row_tma_batch(const BatchRes *__restrict__ res, int nres, const float2 *__restrict__ tw, int *err)
@@ -391,9 +409,15 @@ k_row_tma_batch(const BatchRes *__restrict__ res, int nres, const float2 *__rest
         float2 *erow = R.E + (size_t)row * N + t;
         float *ngl = R.N + (size_t)row * N + t;
         float acc;
-        if (R.pe == PE_UNIFORM) acc = row_local_map<LOGN, PE_UNIFORM>(v, t, row, nrow, erow, ngl, g);
-        else if (R.pe == PE_TABLE) acc = row_local_map<LOGN, PE_TABLE>(v, t, row, nrow, erow, ngl, g);
-        else acc = row_local_map<LOGN, PE_SG10>(v, t, row, nrow, erow, ngl, g);
+        if (g.lens || g.phase) {
+            if (R.pe == PE_UNIFORM) acc = row_local_map<LOGN, PE_UNIFORM, false, true>(v, t, row, nrow, erow, ngl, g);
+            else if (R.pe == PE_TABLE) acc = row_local_map<LOGN, PE_TABLE, false, true>(v, t, row, nrow, erow, ngl, g);
+            else acc = row_local_map<LOGN, PE_SG10, false, true>(v, t, row, nrow, erow, ngl, g);
+        } else {
+            if (R.pe == PE_UNIFORM) acc = row_local_map<LOGN, PE_UNIFORM>(v, t, row, nrow, erow, ngl, g);
+            else if (R.pe == PE_TABLE) acc = row_local_map<LOGN, PE_TABLE>(v, t, row, nrow, erow, ngl, g);
+            else acc = row_local_map<LOGN, PE_SG10>(v, t, row, nrow, erow, ngl, g);
+        }
         item_finish<NT>((double)acc, R.st, grp, G, 1.0 / ((double)N * (double)N));  // barriers inside
         item = nxt;
     }

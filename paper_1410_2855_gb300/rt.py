@@ -35,14 +35,16 @@ class rt_opts(ctypes.Structure):
     _fields_ = [("Isat", ctypes.c_double), ("edge_px", ctypes.c_int), ("precision", ctypes.c_int),
                 ("seed", ctypes.c_ulonglong), ("noise_amp", ctypes.c_double),
                 ("pump_diam_over_window", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
-                ("history_cap", ctypes.c_longlong), ("chunk", ctypes.c_int), ("col_tile", ctypes.c_int)]
+                ("history_cap", ctypes.c_longlong), ("chunk", ctypes.c_int), ("col_tile", ctypes.c_int),
+                ("z_over_F", ctypes.c_double), ("roughness", ctypes.c_void_p), ("slices", ctypes.c_int)]
 
 
 class rt_job(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("fresnel", ctypes.c_double), ("g0", ctypes.c_double), ("T1", ctypes.c_double),
                 ("R", ctypes.c_double), ("pump", rt_pump), ("Isat", ctypes.c_double), ("edge_px", ctypes.c_int),
                 ("seed", ctypes.c_ulonglong), ("noise_amp", ctypes.c_double),
-                ("pump_diam_over_window", ctypes.c_double)]
+                ("pump_diam_over_window", ctypes.c_double), ("z_over_F", ctypes.c_double),
+                ("roughness", ctypes.c_void_p)]
 
 
 class rt_serve_opts(ctypes.Structure):
@@ -94,6 +96,7 @@ def lib() -> ctypes.CDLL:
             "rt_stats": [vp, ctypes.POINTER(rt_stats_t)],
             "rt_read_history": [vp, vp, ll, ctypes.POINTER(ll)],
             "rt_read_spectrum": [vp, vp, sz],
+            "rt_read_field_at": [vp, d, vp, sz],
             "rt_spectrum_peak": [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(d)],
             "rt_destroy": [vp],
             "rt_step_noalloc": [i, d, ctypes.POINTER(rt_pump), d, d, d, ctypes.POINTER(rt_opts), vp, vp, ll,
@@ -237,6 +240,11 @@ def rt_read_spectrum(h, dst):
     return dst
 
 
+def rt_read_field_at(h, zeta: float, dst):
+    _check(lib().rt_read_field_at(h, float(zeta), _ptr(dst), _nbytes(dst)), "rt_read_field_at")
+    return dst
+
+
 def rt_spectrum_peak(h, ring: int = 0):
     mx, my, pw = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
     _check(lib().rt_spectrum_peak(h, ring, ctypes.byref(mx), ctypes.byref(my), ctypes.byref(pw)),
@@ -271,35 +279,41 @@ class Resonator:
 
     ``Resonator(n, fresnel, g0, T1, R, precision=RT_FP32, **opts)``; keyword
     options are the rt_opts fields (Isat, edge_px, seed, noise_amp,
-    pump_diam_over_window, cuda_stream, history_cap, chunk) plus pump_kind,
-    pump_order, pump_radius, pump_profile.
+    pump_diam_over_window, cuda_stream, history_cap, chunk, col_tile,
+    z_over_F) plus pump_kind, pump_order, pump_radius, pump_profile and
+    roughness (an n x n array of the mirror's phase psi in radians).
     """
 
     def __init__(self, n, fresnel, g0, T1, R, precision=RT_FP32, pump_kind=RT_PUMP_SUPERGAUSS,
-                 pump_order=10.0, pump_radius=0.8, pump_profile=None, **opts):
+                 pump_order=10.0, pump_radius=0.8, pump_profile=None, roughness=None, **opts):
         o = rt_opts_default()
         o.precision = precision
         for k, v in opts.items():
             if not hasattr(o, k):
                 raise TypeError(f"unknown option {k}")
             setattr(o, k, v)
+        psi = None
+        if roughness is not None:
+            psi = np.ascontiguousarray(roughness, np.float64).reshape(n, n)
+            o.roughness = psi.ctypes.data
         self._profile = None
         p = rt_pump(kind=pump_kind, order=pump_order, radius=pump_radius, profile=None)
         if pump_kind == RT_PUMP_ARRAY:
             self._profile = np.ascontiguousarray(pump_profile, np.float64).reshape(n, n)
             p.profile = self._profile.ctypes.data
         self.n = n
+        self.slices = max(o.slices, 1)
         self.precision = precision
         self.cdtype = np.complex128 if precision == RT_FP64 else np.complex64
         self.rdtype = np.float64 if precision == RT_FP64 else np.float32
-        self.h = rt_create(n, fresnel, p, g0, T1, R, o)
+        self.h = rt_create(n, fresnel, p, g0, T1, R, o)  # psi is copied by rt_create
 
     @classmethod
     def from_params(cls, p, precision=RT_FP32, **opts):
         """From a workloads.Resonator parameter record."""
         return cls(p.n, p.fresnel, p.g0, p.T1, p.R, precision=precision, pump_order=p.pump_order,
                    pump_radius=p.pump_radius, Isat=p.Isat, edge_px=p.edge, seed=p.seed, noise_amp=p.noise_amp,
-                   pump_diam_over_window=p.d_over_w, **opts)
+                   pump_diam_over_window=p.d_over_w, z_over_F=p.z_over_F, roughness=p.roughness(), **opts)
 
     def step(self, n_bounces: int):
         rt_step(self.h, n_bounces)
@@ -312,7 +326,9 @@ class Resonator:
         return rt_read_field(self.h, np.empty((self.n, self.n), self.cdtype))
 
     def inversion(self) -> np.ndarray:
-        return rt_read_inversion(self.h, np.empty((self.n, self.n), self.rdtype))
+        """n x n, or slices x n x n for a sliced gain medium."""
+        shape = (self.n, self.n) if self.slices == 1 else (self.slices, self.n, self.n)
+        return rt_read_inversion(self.h, np.empty(shape, self.rdtype))
 
     def set_field(self, E):
         rt_write_field(self.h, np.ascontiguousarray(E, self.cdtype))
@@ -324,6 +340,10 @@ class Resonator:
 
     def spectrum(self) -> np.ndarray:
         return rt_read_spectrum(self.h, np.empty((self.n, self.n), self.rdtype))
+
+    def field_at(self, zeta: float) -> np.ndarray:
+        """The field diffracted a further zeta bounces' distance (intracavity plane)."""
+        return rt_read_field_at(self.h, zeta, np.empty((self.n, self.n), self.cdtype))
 
     def peak(self, ring: int = 0):
         return rt_spectrum_peak(self.h, ring)
@@ -361,11 +381,18 @@ def rt_job_default(n: int) -> rt_job:
 
 
 def job_from_params(p) -> rt_job:
-    """rt_job from a workloads.Resonator parameter record (super-Gaussian pump)."""
+    """rt_job from a workloads.Resonator parameter record (super-Gaussian
+    pump).  A roughness array is referenced, not copied: the record's job
+    keeps it alive (``job._psi``) until the library has copied it."""
     j = rt_job_default(p.n)
     j.fresnel, j.g0, j.T1, j.R = p.fresnel, p.g0, p.T1, p.R
     j.pump = rt_pump(kind=RT_PUMP_SUPERGAUSS, order=p.pump_order, radius=p.pump_radius, profile=None)
     j.Isat, j.edge_px, j.seed, j.noise_amp, j.pump_diam_over_window = p.Isat, p.edge, p.seed, p.noise_amp, p.d_over_w
+    j.z_over_F = p.z_over_F
+    psi = p.roughness()
+    if psi is not None:
+        j._psi = np.ascontiguousarray(psi, np.float64)
+        j.roughness = j._psi.ctypes.data
     return j
 
 

@@ -38,6 +38,15 @@ class Resonator:
     d_over_w: float = D_OVER_W
     seed: int = BASE_SEED
     noise_amp: float = NOISE_AMP
+    z_over_F: float = 0.0        # curved mirror: distance per bounce over focal length (0 = flat)
+    roughness_rms: float = 0.0   # mirror roughness phase, rms radians (0 = smooth)
+    roughness_corr: float = 0.05  # its correlation length, fraction of the window half-width
+
+    def roughness(self):
+        """The mirror's roughness phase psi (n x n float64), or None."""
+        if self.roughness_rms == 0.0:
+            return None
+        return roughness_field(self.n, self.seed, self.roughness_rms, self.roughness_corr)
 
 
 # Plain FP64 map on a 128^2 complex128 grid, N_F = 20, 500 round trips.
@@ -50,6 +59,10 @@ C2_BOUNCES = 10_000
 C3 = tuple(Resonator(n=2048, fresnel=1000.0, g0=g, T1=1e4, R=0.9, seed=BASE_SEED + i)
            for i, g in enumerate((0.1, 0.3)))
 C3_BOUNCES = 10_000
+# The 2048^2 resonator with the paper's curved mirror (radius 50 mm at
+# L = 2 mm: z/F = 4L/Rc = 0.16) and a weakly rough surface (0.05 rad rms).
+CURVED = Resonator(n=2048, fresnel=1000.0, g0=0.3, T1=1e4, R=0.9, seed=BASE_SEED + 7, z_over_F=0.16,
+                   roughness_rms=0.05)
 
 
 def batch_sweep(count: int = 256, seed: int = BASE_SEED, sides=(256, 512, 1024)) -> list[Resonator]:
@@ -122,3 +135,18 @@ def random_inversion(n: int, seed: int, lo: float = 0.0, hi: float = 0.3, dtype=
     """Seeded inversion field, uniform in [lo, hi)."""
     rng = np.random.default_rng(seed)
     return rng.uniform(lo, hi, (n, n)).astype(dtype)
+
+
+def roughness_field(n: int, seed: int, rms: float, corr: float) -> np.ndarray:
+    """Seeded random phase screen: white Gaussian noise (PCG64, stream
+    seed ^ 0x5eed) smoothed periodically by a Gaussian of width `corr`
+    window half-widths and scaled to `rms` radians."""
+    rng = np.random.default_rng(seed ^ 0x5EED)
+    w = rng.standard_normal((n, n))
+    k = np.fft.fftfreq(n) * n                        # cycles per window
+    sigma = corr * n / 2.0                           # pixels
+    g = np.exp(-0.5 * (2.0 * np.pi * k / n * sigma) ** 2)
+    psi = np.fft.ifft2(np.fft.fft2(w) * g[:, None] * g[None, :]).real
+    psi -= psi.mean()
+    return psi * (rms / psi.std())
+

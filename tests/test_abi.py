@@ -50,6 +50,7 @@ def test_default_options(lib):
     o = rt.rt_opts_default()
     assert (o.Isat, o.edge_px, o.precision, o.seed, o.noise_amp) == (1.0, 8, 0, 14102855, 1e-6)
     assert o.pump_diam_over_window == 0.8 and o.history_cap == 65536 and o.chunk == 500
+    assert o.z_over_F == 0.0 and not o.roughness
 
 
 @pytest.mark.parametrize("args", [
@@ -66,7 +67,8 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib, args):
 
 def test_create_rejects_bad_options(lib):
     h = ctypes.c_void_p()
-    for field, value in [("precision", 3), ("edge_px", -1), ("Isat", 0.0), ("history_cap", -5), ("chunk", -1)]:
+    for field, value in [("precision", 3), ("edge_px", -1), ("Isat", 0.0), ("history_cap", -5), ("chunk", -1),
+                         ("z_over_F", float("inf")), ("z_over_F", float("nan"))]:
         o = rt.rt_opts_default()
         setattr(o, field, value)
         assert lib.rt_create(64, 100.0, None, 0.2, 1000.0, 0.95, ctypes.byref(o), ctypes.byref(h)) == rt.RT_EINVAL
@@ -81,10 +83,16 @@ def test_noalloc_rejects_oversize_and_unsupported_requests_on_the_host(lib):
     o.precision = rt.RT_FP64
     assert lib.rt_step_noalloc(64, 100.0, None, 0.2, 1000.0, 0.95, ctypes.byref(o), big, big, 1, None) == rt.RT_EINVAL
     assert lib.rt_step_noalloc(64, 100.0, None, 0.2, 1000.0, 0.95, None, None, big, 1, None) == rt.RT_EINVAL
+    # A rough mirror needs an n x n table: not available without allocating.
+    o = rt.rt_opts_default()
+    psi = (ctypes.c_double * (64 * 64))()
+    o.roughness = ctypes.cast(psi, ctypes.c_void_p)
+    assert lib.rt_step_noalloc(64, 100.0, None, 0.2, 1000.0, 0.95, ctypes.byref(o), big, big, 1, None) == rt.RT_EINVAL
 
 
 def test_null_handles_are_rejected(lib):
     assert lib.rt_step(None, 1) == rt.RT_EINVAL
+    assert lib.rt_read_field_at(None, 0.5, None, 0) == rt.RT_EINVAL
     assert lib.rt_sync(None) == rt.RT_EINVAL
     assert lib.rt_read_field(None, None, 0) == rt.RT_EINVAL
     assert lib.rt_destroy(None) == rt.RT_OK
@@ -99,6 +107,9 @@ def test_struct_layouts_match_the_header(tmp_path, lib):
         int main(void) {
             printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(rt_opts), sizeof(rt_pump), sizeof(rt_stats_t),
                    offsetof(rt_opts, chunk), offsetof(rt_stats_t, history_len), offsetof(rt_opts, cuda_stream));
+            printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", offsetof(rt_opts, z_over_F), offsetof(rt_opts, roughness),
+                   sizeof(rt_job), offsetof(rt_job, pump), offsetof(rt_job, z_over_F), offsetof(rt_job, roughness),
+                   sizeof(rt_serve_opts), sizeof(rt_result));
             return 0;
         }
     """))
@@ -106,5 +117,8 @@ def test_struct_layouts_match_the_header(tmp_path, lib):
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()))
     want = [ctypes.sizeof(rt.rt_opts), ctypes.sizeof(rt.rt_pump), ctypes.sizeof(rt.rt_stats_t),
-            rt.rt_opts.chunk.offset, rt.rt_stats_t.history_len.offset, rt.rt_opts.cuda_stream.offset]
+            rt.rt_opts.chunk.offset, rt.rt_stats_t.history_len.offset, rt.rt_opts.cuda_stream.offset,
+            rt.rt_opts.z_over_F.offset, rt.rt_opts.roughness.offset, ctypes.sizeof(rt.rt_job), rt.rt_job.pump.offset,
+            rt.rt_job.z_over_F.offset, rt.rt_job.roughness.offset, ctypes.sizeof(rt.rt_serve_opts),
+            ctypes.sizeof(rt.rt_result)]
     assert got == want

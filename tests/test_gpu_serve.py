@@ -64,10 +64,10 @@ def test_budget_bounds_residency_and_queued_requests_finish():
         res = sorted(srv.poll(), key=lambda r: r.id)
     assert [r.id for r in res] == ids and all(r.status == 0 and r.bounces == 40 for r in res)
     assert 0 < peak <= budget
-    # at most two requests overlap in time
+    # at most two requests are resident at any moment (checked at every admission)
     for r in res:
-        overlapping = sum(1 for q in res if q.admit_s < r.finish_s and r.admit_s < q.finish_s)
-        assert overlapping <= 2
+        live = sum(1 for q in res if q.admit_s <= r.admit_s < q.finish_s)
+        assert live <= 2
     ref, _ = alone(p, 40)
     assert all(np.array_equal(o, ref) for o in outs)
 
