@@ -30,6 +30,16 @@
  * above.  The inversion of such a handle is m n x n arrays, slice-major, in
  * rt_read_inversion / rt_write_inversion; it starts at N0/m per slice.
  *
+ * Aperture modulus.  A(j) = 0 on the outer edge_px pixels; with
+ * taper_px = w > 0 it then rises over w pixels as sin^2((pi/2) (d+1)/(w+1)),
+ * d = 0 .. w-1 the distance from the absorbing band, and is 1 inside
+ * (a smooth, separable D_0 of eq. complex_aperture2).
+ *
+ * Inversion update.  RT_RELAX_EXACT replaces the explicit Euler step by the
+ * exact solution of the rate equation dN/dt = (N0 - N (1 + I/Isat)) / T1 over
+ * one bounce with I frozen: N <- Nss + (N - Nss) exp(-(1 + I/Isat)/T1),
+ * Nss = N0 / (1 + I/Isat).  Both have the same fixed points.
+ *
  * D is the phase of the complex aperture of eq. complex_aperture2 (a curved
  * mirror of focal length F and a random roughness phase psi):
  *
@@ -82,6 +92,7 @@ typedef enum {
 
 enum { RT_PUMP_SUPERGAUSS = 0, RT_PUMP_UNIFORM = 1, RT_PUMP_ARRAY = 2 };
 enum { RT_FP32 = 0, RT_FP64 = 1 };
+enum { RT_RELAX_EULER = 0, RT_RELAX_EXACT = 1 };
 
 /* Pump, i.e. the unsaturated inversion N0 = g0 * P(x, y):
  *   RT_PUMP_SUPERGAUSS  P = exp(-(r / radius)^order), r = sqrt(x^2 + y^2),
@@ -115,6 +126,10 @@ typedef struct {
                                      copied at creation; NULL = smooth (NULL) */
     int slices;                   /* gain medium as m thin slices per bounce, 1 <= m <= 64 (0 or 1: one
                                      slice at the mirror; handles only, see below) (0) */
+    int taper_px;                 /* smooth aperture: width in pixels of the sin^2 ramp inside the
+                                     absorbing edge, 0 = hard edge (0) */
+    int relax;                    /* inversion update: RT_RELAX_EULER (the map above) or RT_RELAX_EXACT
+                                     (the rate equation solved over the bounce, see below) (EULER) */
 } rt_opts;
 
 rt_status rt_opts_default(rt_opts *opts);
@@ -241,6 +256,8 @@ typedef struct {
     double pump_diam_over_window; /* D/W */
     double z_over_F;              /* curved mirror z / F (0 = flat) */
     const double *roughness;      /* n*n roughness phase psi, host, copied at set-up; NULL = smooth */
+    int taper_px;                 /* smooth aperture ramp width (0 = hard edge) */
+    int relax;                    /* RT_RELAX_EULER or RT_RELAX_EXACT */
 } rt_job;
 
 /* Fill a job with the defaults of rt_opts_default / rt_create for side n. */
@@ -370,7 +387,7 @@ rt_status rt_serve_destroy(rt_server *s);
  * Supported: RT_FP32 only, super-Gaussian pump of order 10 or uniform pump,
  * flat or curved mirror without roughness (anything else returns
  * RT_EINVAL).  Options used: Isat, edge_px, pump_diam_over_window,
- * cuda_stream, col_tile, z_over_F (NULL opts = defaults).
+ * cuda_stream, col_tile, z_over_F, taper_px, relax (NULL opts = defaults).
  *
  * The first call on each device looks up the array's device address, with
  * that device current; make that first call before any stream capture.

@@ -60,6 +60,8 @@ class Params(ctypes.Structure):
         ("z_over_F", ctypes.c_double),
         ("roughness", ctypes.c_void_p),
         ("slices", ctypes.c_int),
+        ("taper", ctypes.c_int),
+        ("relax", ctypes.c_int),
     ]
 
 
@@ -113,10 +115,11 @@ def alpha_from_fresnel(fresnel: float, d_over_w: float) -> float:
 
 
 def make_params(n, alpha, g0, T1, R, Isat=1.0, edge=8, pump_kind=PUMP_SUPERGAUSS,
-                pump_order=10.0, pump_radius=0.8, pump_profile=None, z_over_F=0.0, roughness=None, slices=1):
+                pump_order=10.0, pump_radius=0.8, pump_profile=None, z_over_F=0.0, roughness=None, slices=1,
+                taper=0, relax=0):
     p = Params(n=n, alpha=alpha, g0=g0, T1=T1, R=R, Isat=Isat, edge=edge, pump_kind=pump_kind,
                pump_order=pump_order, pump_radius=pump_radius, pump_profile=None, z_over_F=z_over_F,
-               roughness=None, slices=slices)
+               roughness=None, slices=slices, taper=taper, relax=relax)
     keep = []
     if pump_kind == PUMP_ARRAY:
         prof = _f64(pump_profile).reshape(n, n)

@@ -29,7 +29,13 @@
  *         I = |E'|^2
  *         E_{n+1} = sqrt(R) * A(x) A(y) * D(x, y) * exp(N_n / 2) * E'
  *         N_{n+1} = N_n + (N0 - N_n (1 + I / Isat)) / T1
- *     A = 0 on the outer `edge` pixels of each axis, 1 inside.
+ *     A = 0 on the outer `edge` pixels of each axis, 1 inside; with a taper
+ *     of w pixels A rises inside the band as sin^2((pi/2) (d+1)/(w+1)),
+ *     d = 0 .. w-1 pixels from the band (a smooth modulus D_0).
+ *   - Inversion update, exact variant (relax = 1): the rate equation
+ *     dN/dt = (N0 - N (1 + I/Isat)) / T1 integrated over one bounce with I
+ *     held fixed, N <- Nss + (N - Nss) exp(-(1 + I/Isat)/T1),
+ *     Nss = N0 / (1 + I/Isat).
  *   - Argument of the complex aperture (eq. complex_aperture2: a mirror of
  *     focal length F, phase k r^2 / 2F, and a roughness phase psi), applied
  *     complex-conjugated because the propagator above is the conjugate of
@@ -83,6 +89,8 @@ typedef struct {
     double z_over_F;       /* propagation distance per bounce over the mirror's focal length (0: flat) */
     const double *roughness; /* n*n roughness phase psi in radians, or NULL */
     int slices;            /* thin gain slices per bounce (0 or 1: one) */
+    int taper;             /* width of the sin^2 ramp of the aperture modulus inside the edge (0: hard) */
+    int relax;             /* inversion update: 0 explicit Euler step, 1 exact over the bounce */
 } orc_params;
 
 int orc_version(void) { return 1; }
@@ -276,6 +284,16 @@ void orc_noise(int n, uint64_t seed, double amp, cplx *E)
 
 static int inside_edge(int j, int n, int edge) { return j >= edge && j < n - edge; }
 
+/* Aperture modulus along one axis (hard edge, optional sin^2 taper). */
+static double edge_modulus(int j, int n, int edge, int taper)
+{
+    if (!inside_edge(j, n, edge)) return 0.0;
+    int d = j - edge < n - 1 - edge - j ? j - edge : n - 1 - edge - j;
+    if (d >= taper) return 1.0;
+    double s = sin(0.5 * ORC_PI * (double)(d + 1) / (double)(taper + 1));
+    return s * s;
+}
+
 /* Argument k r^2/(2F) + psi of the complex aperture at pixel (x, y), in
  * window units (see the conventions above). */
 static double aperture_argument(const orc_params *p, int x, int y)
@@ -302,14 +320,21 @@ static void gain_step(cplx *E, double *N, const double *N0, const orc_params *p,
             size_t i = (size_t)y * n + x;
             double inten = creal(E[i]) * creal(E[i]) + cimag(E[i]) * cimag(E[i]);
             double Nn = N[i];
-            double A = (!mirror || (inside_edge(x, n, p->edge) && inside_edge(y, n, p->edge))) ? 1.0 : 0.0;
+            double A = mirror ? edge_modulus(x, n, p->edge, p->taper) * edge_modulus(y, n, p->edge, p->taper) : 1.0;
             cplx D = A;
             if (phased) {
                 double theta = aperture_argument(p, x, y);
                 D = A * (cos(theta) - sin(theta) * _Complex_I);
             }
             E[i] = sqrtR * exp(0.5 * Nn) * D * E[i];
-            N[i] = Nn + (N0[i] / (double)m - Nn * (1.0 + inten / p->Isat)) / p->T1;
+            double a = 1.0 + inten / p->Isat;
+            double pump = N0[i] / (double)m;
+            if (p->relax) {
+                double Nss = pump / a;
+                N[i] = Nss + (Nn - Nss) * exp(-a / p->T1);
+            } else {
+                N[i] = Nn + (pump - Nn * a) / p->T1;
+            }
         }
     }
 }

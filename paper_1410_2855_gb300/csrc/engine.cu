@@ -30,6 +30,7 @@ bool job_ok(const rt_job &j)
     if (j.pump.kind == RT_PUMP_SUPERGAUSS && (!fpos(j.pump.order) || !fpos(j.pump.radius))) return false;
     if (j.pump.kind == RT_PUMP_ARRAY && !j.pump.profile) return false;
     if (!std::isfinite(j.z_over_F)) return false;
+    if (j.taper_px < 0 || j.taper_px > j.n / 2 || (j.relax != RT_RELAX_EULER && j.relax != RT_RELAX_EXACT)) return false;
     return true;
 }
 
@@ -120,8 +121,9 @@ BatchRes slot_descriptor(const rt_job &job, const SlotBufs &b, SlotCtl *ctl, lon
     g.edge = job.edge_px;
     g.pump_kind = job.pump.kind;
     g.pump_tab = b.pump_tab;
-    g.lens = (!job_rough(job) && job.z_over_F != 0.0) ? b.lens : nullptr;
+    g.lens = (!job_rough(job) && (job.z_over_F != 0.0 || job.taper_px > 0)) ? b.lens : nullptr;
     g.phase = job_rough(job) ? b.phase : nullptr;
+    g.relax_exact = job.relax == RT_RELAX_EXACT;
     r.pe = pe;
     r.target = target;
     r.st.part = b.part;
@@ -162,11 +164,11 @@ cudaError_t slot_start(const rt_job &job, const SlotBufs &b, int colC, float2 *c
         double *psi = nullptr;
         if ((e = cudaMallocAsync(reinterpret_cast<void **>(&psi), P * sizeof(double), s)) != cudaSuccess) return e;
         e = cudaMemcpyAsync(psi, job.roughness, P * sizeof(double), cudaMemcpyDefault, s);
-        if (e == cudaSuccess) e = launch_phase32(n, c, psi, b.phase, s);
+        if (e == cudaSuccess) e = launch_phase32(n, c, job.edge_px, job.taper_px, psi, b.phase, s);
         cudaFreeAsync(psi, s);
         if (e != cudaSuccess) return e;
-    } else if (job.z_over_F != 0.0) {
-        if ((e = launch_lens32(n, c, b.lens, s)) != cudaSuccess) return e;
+    } else if (job.z_over_F != 0.0 || job.taper_px > 0) {
+        if ((e = launch_lens32(n, c, job.edge_px, job.taper_px, b.lens, s)) != cudaSuccess) return e;
     }
     alignas(64) unsigned char map[128];
     if ((e = make_col_tensor_map(map, b.E, n, colC)) != cudaSuccess) return e;

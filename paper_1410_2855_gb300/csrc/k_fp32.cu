@@ -116,15 +116,16 @@ cudaError_t launch_noise32(int n, unsigned long long seed, double amp, float2 *E
 
 double lens_curvature(double alpha, double z_over_F) { return 3.14159265358979323846 / (4.0 * alpha) * z_over_F; }
 
-cudaError_t launch_lens32(int n, double c, float2 *lens, cudaStream_t s)
+cudaError_t launch_lens32(int n, double c, int edge, int taper, float2 *lens, cudaStream_t s)
 {
-    k_lens_table<float2><<<(n + 255) / 256, 256, 0, s>>>(n, c / 3.14159265358979323846, lens);
+    k_lens_table<float2><<<(n + 255) / 256, 256, 0, s>>>(n, c / 3.14159265358979323846, edge, taper, lens);
     return cudaGetLastError();
 }
 
-cudaError_t launch_phase32(int n, double c, const double *psi, float2 *phase, cudaStream_t s)
+cudaError_t launch_phase32(int n, double c, int edge, int taper, const double *psi, float2 *phase, cudaStream_t s)
 {
-    k_phase_table<float2><<<grid_for((size_t)n * n, 256, 2048), 256, 0, s>>>(n, c / 3.14159265358979323846, psi, phase);
+    k_phase_table<float2><<<grid_for((size_t)n * n, 256, 2048), 256, 0, s>>>(n, c / 3.14159265358979323846, edge,
+                                                                              taper, psi, phase);
     return cudaGetLastError();
 }
 

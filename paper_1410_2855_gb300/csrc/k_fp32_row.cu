@@ -25,7 +25,7 @@ template <int LOGN, int PE>
 static cudaError_t row_dg32_pe(float2 *E, float *N, const float2 *tw, const float2 *h, const GainParams<float> &g,
                                const StatParams &st, cudaStream_t s)
 {
-    if (g.lens || g.phase) return row_dg32_k<LOGN, PE, true>(E, N, tw, h, g, st, s);
+    if (needs_general(g)) return row_dg32_k<LOGN, PE, true>(E, N, tw, h, g, st, s);
     return row_dg32_k<LOGN, PE, false>(E, N, tw, h, g, st, s);
 }
 

@@ -141,7 +141,13 @@ __global__ void __launch_bounds__(256) k_gain64(int n, double2 *E, double *__res
         else if (g.lens) e = cmul(e, cmul(g.lens[x], g.lens[y]));
         const double yc = (double)(y - n / 2) * (2.0 / (double)n);
         const double n0 = pump_value(g, x, y, n, yc * yc);
-        N[i] = nn + (n0 - nn * (1.0 + inten * g.invIsat)) * g.invT1;
+        const double a = 1.0 + inten * g.invIsat;
+        if (g.relax_exact) {
+            const double nss = n0 / a;
+            N[i] = nss + (nn - nss) * exp(-a * g.invT1);
+        } else {
+            N[i] = nn + (n0 - nn * a) * g.invT1;
+        }
         E[i] = e;
         acc += e.x * e.x + e.y * e.y;
     }
@@ -181,16 +187,17 @@ cudaError_t launch_noise64(int n, unsigned long long seed, double amp, double2 *
     return cudaGetLastError();
 }
 
-cudaError_t launch_lens64(int n, double c, double2 *lens, cudaStream_t s)
+cudaError_t launch_lens64(int n, double c, int edge, int taper, double2 *lens, cudaStream_t s)
 {
-    k_lens_table<double2><<<(n + 255) / 256, 256, 0, s>>>(n, c / 3.14159265358979323846, lens);
+    k_lens_table<double2><<<(n + 255) / 256, 256, 0, s>>>(n, c / 3.14159265358979323846, edge, taper, lens);
     return cudaGetLastError();
 }
 
-cudaError_t launch_phase64(int n, double c, const double *psi, double2 *phase, cudaStream_t s)
+cudaError_t launch_phase64(int n, double c, int edge, int taper, const double *psi, double2 *phase,
+                           cudaStream_t s)
 {
-    k_phase_table<double2><<<grid_for((size_t)n * n, 256, 2048), 256, 0, s>>>(n, c / 3.14159265358979323846, psi,
-                                                                               phase);
+    k_phase_table<double2><<<grid_for((size_t)n * n, 256, 2048), 256, 0, s>>>(n, c / 3.14159265358979323846, edge,
+                                                                               taper, psi, phase);
     return cudaGetLastError();
 }
 

@@ -140,6 +140,7 @@ GainParams<R> gain_params(rt_handle *h, bool last = true)
     using C = typename cplx_of<R>::type;
     g.lens = last ? static_cast<const C *>(h->lens) : nullptr;
     g.phase = last ? static_cast<const C *>(h->phase) : nullptr;
+    g.relax_exact = h->opts.relax == RT_RELAX_EXACT;
     return g;
 }
 
@@ -181,9 +182,10 @@ cudaError_t get_graph(rt_handle *h, long long k, cudaGraphExec_t *out)
         *out = it->second;
         return cudaSuccess;
     }
-    cudaError_t e = h->precision == RT_FP32 ? prepare_bounce32(h->logn, h->colC, h->pe, h->lens || h->phase)
+    const bool exact = h->opts.relax == RT_RELAX_EXACT;
+    cudaError_t e = h->precision == RT_FP32 ? prepare_bounce32(h->logn, h->colC, h->pe, h->lens || h->phase || exact)
                                             : prepare_bounce64(h->logn);
-    if (e == cudaSuccess && h->precision == RT_FP32 && h->slices > 1) e = prepare_row32(h->logn, h->pe, false);
+    if (e == cudaSuccess && h->precision == RT_FP32 && h->slices > 1) e = prepare_row32(h->logn, h->pe, exact);
     if (e != cudaSuccess) return e;
     e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
@@ -310,6 +312,8 @@ rt_status rt_create(int n, double fresnel, const rt_pump *pump, double g0, doubl
     if (o.precision != RT_FP32 && o.precision != RT_FP64) return RT_EINVAL;
     if (!std::isfinite(o.noise_amp) || o.noise_amp < 0.0 || !finite_pos(o.pump_diam_over_window)) return RT_EINVAL;
     if (!std::isfinite(o.z_over_F) || o.slices < 0 || o.slices > 64) return RT_EINVAL;
+    if (o.taper_px < 0 || o.taper_px > n / 2 || (o.relax != RT_RELAX_EULER && o.relax != RT_RELAX_EXACT))
+        return RT_EINVAL;
     if (o.history_cap < 0 || o.chunk < 0) return RT_EINVAL;
     if (o.col_tile != 0 && (o.precision != RT_FP32 || !col_tile_ok32(ilog2(n), o.col_tile))) return RT_EINVAL;
     if (p.kind == RT_PUMP_SUPERGAUSS && (!finite_pos(p.order) || !finite_pos(p.radius))) return RT_EINVAL;
@@ -370,8 +374,9 @@ rt_status rt_create(int n, double fresnel, const rt_pump *pump, double g0, doubl
         RT_CREATE_TRY(cudaMalloc(&h->profile, sizeof(double) * P));
         RT_CREATE_TRY(cudaMemcpyAsync(h->profile, p.profile, sizeof(double) * P, cudaMemcpyDefault, h->stream));
     }
-    // Aperture phase: a full table when the mirror is rough (lens folded in),
-    // else per-axis lens factors when it is curved, else nothing.
+    // Complex aperture beyond the hard edge: a full table when the mirror is
+    // rough (lens and taper folded in), else per-axis factors when it is
+    // curved or the edge tapered, else nothing.
     const double c = lens_curvature(h->alpha, o.z_over_F);
     const double g0s = g0 / h->slices;   // pump of one slice: N0/m
     double *psi = nullptr;
@@ -380,15 +385,17 @@ rt_status rt_create(int n, double fresnel, const rt_pump *pump, double g0, doubl
         RT_CREATE_TRY(cudaMalloc(&psi, sizeof(double) * P));
         cudaError_t e = cudaMemcpyAsync(psi, o.roughness, sizeof(double) * P, cudaMemcpyDefault, h->stream);
         if (e == cudaSuccess)
-            e = h->precision == RT_FP32 ? launch_phase32(n, c, psi, static_cast<float2 *>(h->phase), h->stream)
-                                        : launch_phase64(n, c, psi, static_cast<double2 *>(h->phase), h->stream);
+            e = h->precision == RT_FP32
+                    ? launch_phase32(n, c, o.edge_px, o.taper_px, psi, static_cast<float2 *>(h->phase), h->stream)
+                    : launch_phase64(n, c, o.edge_px, o.taper_px, psi, static_cast<double2 *>(h->phase), h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         cudaFree(psi);
         RT_CREATE_TRY(e);
-    } else if (o.z_over_F != 0.0) {
+    } else if (o.z_over_F != 0.0 || o.taper_px > 0) {
         RT_CREATE_TRY(cudaMalloc(&h->lens, (size_t)n * h->esz()));
-        RT_CREATE_TRY(h->precision == RT_FP32 ? launch_lens32(n, c, static_cast<float2 *>(h->lens), h->stream)
-                                              : launch_lens64(n, c, static_cast<double2 *>(h->lens), h->stream));
+        RT_CREATE_TRY(h->precision == RT_FP32
+                          ? launch_lens32(n, c, o.edge_px, o.taper_px, static_cast<float2 *>(h->lens), h->stream)
+                          : launch_lens64(n, c, o.edge_px, o.taper_px, static_cast<double2 *>(h->lens), h->stream));
     }
 
     if (h->precision == RT_FP32) {

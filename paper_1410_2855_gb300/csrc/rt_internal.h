@@ -13,17 +13,18 @@ enum PumpKind { PUMP_SUPERGAUSS = 0, PUMP_UNIFORM = 1, PUMP_ARRAY = 2 };
 // Pump evaluation inside the FP32 row sweep: super-Gaussian of order 10
 // computed on the fly, uniform, or a precomputed N0 table (array pumps and
 // any other super-Gaussian order).
-enum PumpEval { PE_SG10 = 0, PE_UNIFORM = 1, PE_TABLE = 2 };
+enum PumpEval { PE_SG10 = 0, PE_UNIFORM = 1, PE_TABLE = 2, PE_RUNTIME = 3 /* chosen per call */ };
 
 template <typename R> struct cplx_of;
 template <> struct cplx_of<float> { using type = float2; };
 template <> struct cplx_of<double> { using type = double2; };
 
 // Local map parameters: E <- sqrtR * A * D * exp(N/2) * E',
-// N <- N + (N0 - N (1 + I invIsat)) invT1, N0 = g0 * P(x, y).  D is the
-// phase of the complex aperture (curved mirror and roughness, eq.
-// complex_aperture2): either a separable lens, D = lens[x] lens[y], or a full
-// table D = phase[y n + x]; neither pointer set means D = 1.
+// N <- N + (N0 - N (1 + I invIsat)) invT1, N0 = g0 * P(x, y) (or, with
+// relax_exact, the rate equation solved over the bounce).  D is the complex
+// aperture beyond the hard edge (smooth taper, curved mirror, roughness, eq.
+// complex_aperture2): either separable, D = lens[x] lens[y], or a full table
+// D = phase[y n + x]; neither pointer set means D = 1.
 template <typename R>
 struct GainParams {
     R sqrtR, invT1, invIsat, g0;
@@ -33,8 +34,9 @@ struct GainParams {
     int edge;
     int pump_kind;
     const R *pump_tab;  // n*n N0 values when pump_kind == PUMP_ARRAY
-    const typename cplx_of<R>::type *lens;   // n per-axis factors exp(-i c x_j^2), or null
-    const typename cplx_of<R>::type *phase;  // n*n factors exp(-i (c (x^2 + y^2) + psi)), or null (wins over lens)
+    const typename cplx_of<R>::type *lens;   // n per-axis factors A(j) exp(-i c x_j^2), or null
+    const typename cplx_of<R>::type *phase;  // n*n factors A(x) A(y) exp(-i (c (x^2 + y^2) + psi)), or null
+    int relax_exact;                         // 1: exponential inversion update
 };
 
 // Per-bounce mean intensity: block partials, reduced by the last block to
@@ -91,8 +93,8 @@ cudaError_t make_col_tensor_map(void *map, float2 *E, int n, int colC);
 // Row sweep: per row, forward FFT, x h(mx), inverse FFT, then the local map
 // (gain, mirror phase, edge, inversion update) and the mean-intensity
 // reduction.  pe selects how N0 is evaluated: 0 super-Gaussian of order 10
-// on the fly, 1 uniform, 2 from GainParams::pump_tab.  The aperture-phase
-// form of the kernel runs when g.lens or g.phase is set.
+// on the fly, 1 uniform, 2 from GainParams::pump_tab.  The general form of
+// the kernel (aperture table, exact relaxation) runs when needs_general(g).
 cudaError_t launch_row_diffract_gain32(int logn, int pe, float2 *E, float *N, const float2 *tw, const float2 *h,
                                        const GainParams<float> &g, const StatParams &st, cudaStream_t s);
 int row_blocks32(int logn);            // most blocks of a row sweep (size of StatParams::part)
@@ -142,16 +144,25 @@ cudaError_t launch_tables32(int n, double alpha, float2 *tw, float2 *h, cudaStre
 cudaError_t launch_tables64(int n, double alpha, double2 *tw, double2 *h, cudaStream_t s);
 cudaError_t launch_noise32(int n, unsigned long long seed, double amp, float2 *E, cudaStream_t s);
 cudaError_t launch_noise64(int n, unsigned long long seed, double amp, double2 *E, cudaStream_t s);
-// Aperture phase factors, FP64 arithmetic (eq. complex_aperture2 conjugated
-// like the propagator): theta = c (x^2 + y^2) + psi(x, y) with
-// c = (pi / (4 alpha)) (z / F), factor exp(-i theta).  lens: the n per-axis
-// factors exp(-i c x_j^2); phase: the n*n factors with psi (device array of
-// n*n doubles, or null for psi = 0).
+// Complex aperture factors, FP64 arithmetic (eq. complex_aperture2, its
+// phase conjugated like the propagator): A(x) A(y) exp(-i theta),
+// theta = c (x^2 + y^2) + psi(x, y), c = (pi / (4 alpha)) (z / F), A the
+// per-axis modulus (0 in the edge band, a sin^2 ramp of `taper` pixels, 1
+// inside).  lens: the n per-axis factors A(j) exp(-i c x_j^2); phase: the
+// n*n factors with psi (device array of n*n doubles, or null for psi = 0).
 double lens_curvature(double alpha, double z_over_F);
-cudaError_t launch_lens32(int n, double c, float2 *lens, cudaStream_t s);
-cudaError_t launch_lens64(int n, double c, double2 *lens, cudaStream_t s);
-cudaError_t launch_phase32(int n, double c, const double *psi, float2 *phase, cudaStream_t s);
-cudaError_t launch_phase64(int n, double c, const double *psi, double2 *phase, cudaStream_t s);
+cudaError_t launch_lens32(int n, double c, int edge, int taper, float2 *lens, cudaStream_t s);
+cudaError_t launch_lens64(int n, double c, int edge, int taper, double2 *lens, cudaStream_t s);
+cudaError_t launch_phase32(int n, double c, int edge, int taper, const double *psi, float2 *phase, cudaStream_t s);
+cudaError_t launch_phase64(int n, double c, int edge, int taper, const double *psi, double2 *phase,
+                           cudaStream_t s);
+
+// The row sweep needs its general form: an aperture table or the exact
+// inversion update.
+template <typename R> __host__ __device__ inline bool needs_general(const GainParams<R> &g)
+{
+    return g.lens || g.phase || g.relax_exact;
+}
 // N0 = g0 * P in FP64 (profile: device array of n*n doubles or null), stored as R.
 cudaError_t launch_pump32(int n, int kind, double g0, double order, double radius, const double *profile,
                           float *out, cudaStream_t s);

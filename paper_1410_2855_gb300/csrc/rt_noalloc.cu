@@ -87,6 +87,8 @@ extern "C" rt_status rt_step_noalloc(int n, double fresnel, const rt_pump *pump,
     if (!std::isfinite(R) || R <= 0.0 || R > 1.0 || n_bounces < 0) return RT_EINVAL;
     if (!fpos(o.Isat) || o.edge_px < 0 || o.edge_px > n / 2 || !fpos(o.pump_diam_over_window)) return RT_EINVAL;
     if (o.precision != RT_FP32 || !std::isfinite(o.z_over_F) || o.roughness || o.slices > 1) return RT_EINVAL;
+    if (o.taper_px < 0 || o.taper_px > n / 2 || (o.relax != RT_RELAX_EULER && o.relax != RT_RELAX_EXACT))
+        return RT_EINVAL;
     const bool sg10 = p.kind == RT_PUMP_SUPERGAUSS && p.order == 10.0 && fpos(p.radius);
     if (!sg10 && p.kind != RT_PUMP_UNIFORM) return RT_EINVAL;
     if (!field || !inversion) return RT_EINVAL;
@@ -117,8 +119,9 @@ extern "C" rt_status rt_step_noalloc(int n, double fresnel, const rt_pump *pump,
     // The array keeps whatever the previous call left: the counters must start at zero.
     if (cudaMemsetAsync(ctl, 0, sizeof(NoAllocCtl), s) != cudaSuccess) return RT_ECUDA;
     if (rtk::launch_tables32(n, alpha, tw, h, s) != cudaSuccess) return RT_ECUDA;
-    const bool curved = o.z_over_F != 0.0;
-    if (curved && rtk::launch_lens32(n, rtk::lens_curvature(alpha, o.z_over_F), lens, s) != cudaSuccess)
+    const bool curved = o.z_over_F != 0.0 || o.taper_px > 0;
+    if (curved &&
+        rtk::launch_lens32(n, rtk::lens_curvature(alpha, o.z_over_F), o.edge_px, o.taper_px, lens, s) != cudaSuccess)
         return RT_ECUDA;
 
     rtk::GainParams<float> g{};
@@ -134,6 +137,7 @@ extern "C" rt_status rt_step_noalloc(int n, double fresnel, const rt_pump *pump,
     g.pump_tab = nullptr;
     g.lens = curved ? lens : nullptr;
     g.phase = nullptr;
+    g.relax_exact = o.relax == RT_RELAX_EXACT;
     rtk::StatParams sp{};
     sp.part = part;
     sp.count = &ctl->count;

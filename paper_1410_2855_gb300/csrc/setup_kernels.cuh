@@ -46,21 +46,33 @@ __device__ __forceinline__ double lens_turns(double c_over_pi, double q)
     return fmod(hi, 2.0) + lo;
 }
 
-// Separable lens factors lens[j] = exp(-i c x_j^2), one axis.
+// Aperture modulus along one axis: 0 in the absorbing band of `edge`
+// pixels, then a sin^2 ramp over `taper` pixels, then 1.
+__device__ __forceinline__ double aperture_modulus(int j, int n, int edge, int taper)
+{
+    if (j < edge || j >= n - edge) return 0.0;
+    const int d = min(j - edge, n - 1 - edge - j);
+    if (d >= taper) return 1.0;
+    const double s = sinpi(0.5 * (double)(d + 1) / (double)(taper + 1));
+    return s * s;
+}
+
+// Separable aperture factors lens[j] = A(j) exp(-i c x_j^2), one axis.
 template <typename V>
-__global__ void k_lens_table(int n, double c_over_pi, V *lens)
+__global__ void k_lens_table(int n, double c_over_pi, int edge, int taper, V *lens)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const double x = (double)(j - n / 2) / (double)(n / 2);
     double sp, cp;
     sincospi(lens_turns(c_over_pi, x * x), &sp, &cp);
-    lens[j] = cmk<V>(cp, -sp);
+    const double a = aperture_modulus(j, n, edge, taper);
+    lens[j] = cmk<V>(a * cp, -a * sp);
 }
 
-// Full aperture factors exp(-i (c (x^2 + y^2) + psi[y n + x])); psi may be null.
+// Full aperture factors A(x) A(y) exp(-i (c (x^2 + y^2) + psi[y n + x])); psi may be null.
 template <typename V>
-__global__ void k_phase_table(int n, double c_over_pi, const double *psi, V *phase)
+__global__ void k_phase_table(int n, double c_over_pi, int edge, int taper, const double *psi, V *phase)
 {
     const size_t P = (size_t)n * n;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < P; i += (size_t)gridDim.x * blockDim.x) {
@@ -71,8 +83,9 @@ __global__ void k_phase_table(int n, double c_over_pi, const double *psi, V *pha
         sincospi(lens_turns(c_over_pi, xc * xc + yc * yc), &sl, &cl);
         double sr = 0.0, cr = 1.0;
         if (psi) sincos(psi[i], &sr, &cr);
+        const double a = aperture_modulus(x, n, edge, taper) * aperture_modulus(y, n, edge, taper);
         // exp(-i (a + b)) = (cos a cos b - sin a sin b) - i (sin a cos b + cos a sin b)
-        phase[i] = cmk<V>(cl * cr - sl * sr, -(sl * cr + cl * sr));
+        phase[i] = cmk<V>(a * (cl * cr - sl * sr), -a * (sl * cr + cl * sr));
     }
 }
 

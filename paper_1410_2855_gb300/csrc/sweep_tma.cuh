@@ -126,12 +126,15 @@ __device__ __forceinline__ void init_stage_barriers(uint64_t *bar)
 
 // Local map of one row held in registers (slot s = column t + T s):
 // gain against the frozen inversion, mirror, absorbing edge, inversion
-// relaxation; with AP also the aperture phase D (curved mirror, roughness),
-// from g.phase when set, else the separable g.lens (one of them must be set).
+// relaxation.  The general form (AP) also applies the complex aperture D
+// (smooth taper, curved mirror, roughness) from g.phase when set, else from
+// the separable g.lens when set, and takes the exact inversion update when
+// g.relax_exact is set.  PE_RUNTIME takes the pump evaluation from pe_rt.
 // Returns sum |E_new|^2 over the thread's 16 elements.
 template <int LOGN, int PE, bool STAGED_N0 = false, bool AP = false>
 __device__ __forceinline__ float row_local_map(float2 (&v)[16], int t, int row, const float *nrow, float2 *erow,
-                                               float *ngl, const GainParams<float> &g, const float *n0row = nullptr)
+                                               float *ngl, const GainParams<float> &g, const float *n0row = nullptr,
+                                               int pe_rt = PE_SG10)
 {
     constexpr int N = 1 << LOGN, T = Plan<LOGN>::T;
     const float step = 2.0f / (float)N;
@@ -145,7 +148,7 @@ __device__ __forceinline__ float row_local_map(float2 (&v)[16], int t, int row, 
     if constexpr (AP) {
         if (g.phase) {
             dtab = g.phase + (size_t)row * N + t;
-        } else {
+        } else if (g.lens) {
             dtab = g.lens + t;
             drow = cscale(__ldg(g.lens + row), g.sqrtR);
         }
@@ -159,12 +162,24 @@ __device__ __forceinline__ float row_local_map(float2 (&v)[16], int t, int row, 
         const float inten = e.x * e.x + e.y * e.y;
         const bool inside = row_in && x >= g.edge && x < N - g.edge;
         if constexpr (AP) {
-            e = cscale(cmul(e, cmul(drow, __ldg(dtab + si * T))), inside ? fexp(0.5f * nn) : 0.0f);
+            const float2 d = dtab ? cmul(drow, __ldg(dtab + si * T)) : drow;
+            e = cscale(cmul(e, d), inside ? fexp(0.5f * nn) : 0.0f);
         } else {
             e = cscale(e, inside ? g.sqrtR * fexp(0.5f * nn) : 0.0f);
         }
         float n0;
-        if constexpr (PE == PE_UNIFORM) {
+        if constexpr (PE == PE_RUNTIME) {
+            if (pe_rt == PE_UNIFORM) {
+                n0 = g.g0;
+            } else if (pe_rt == PE_TABLE) {
+                n0 = __ldg(g.pump_tab + (size_t)row * N + x);
+            } else {
+                const float xc = xc0 + (float)(si * T) * step;
+                const float q = xc * xc * g.inv_rp2 + yq;
+                const float q2 = q * q;
+                n0 = g.g0 * fexp(-(q2 * q2 * q));
+            }
+        } else if constexpr (PE == PE_UNIFORM) {
             n0 = g.g0;
         } else if constexpr (PE == PE_TABLE && STAGED_N0) {
             n0 = n0row[si * T];
@@ -176,7 +191,17 @@ __device__ __forceinline__ float row_local_map(float2 (&v)[16], int t, int row, 
             const float q2 = q * q;
             n0 = g.g0 * fexp(-(q2 * q2 * q));
         }
-        ngl[si * T] = nn + (n0 - nn * (1.0f + inten * g.invIsat)) * g.invT1;
+        if constexpr (AP) {
+            const float a = 1.0f + inten * g.invIsat;
+            if (g.relax_exact) {
+                const float nss = n0 / a;
+                ngl[si * T] = nss + (nn - nss) * fexp(-a * g.invT1);
+            } else {
+                ngl[si * T] = nn + (n0 - nn * a) * g.invT1;
+            }
+        } else {
+            ngl[si * T] = nn + (n0 - nn * (1.0f + inten * g.invIsat)) * g.invT1;
+        }
         erow[si * T] = e;
         acc += e.x * e.x + e.y * e.y;
     }
@@ -409,10 +434,8 @@ k_row_tma_batch(const BatchRes *__restrict__ res, int nres, const float2 *__rest
         float2 *erow = R.E + (size_t)row * N + t;
         float *ngl = R.N + (size_t)row * N + t;
         float acc;
-        if (g.lens || g.phase) {
-            if (R.pe == PE_UNIFORM) acc = row_local_map<LOGN, PE_UNIFORM, false, true>(v, t, row, nrow, erow, ngl, g);
-            else if (R.pe == PE_TABLE) acc = row_local_map<LOGN, PE_TABLE, false, true>(v, t, row, nrow, erow, ngl, g);
-            else acc = row_local_map<LOGN, PE_SG10, false, true>(v, t, row, nrow, erow, ngl, g);
+        if (needs_general(g)) {
+            acc = row_local_map<LOGN, PE_RUNTIME, false, true>(v, t, row, nrow, erow, ngl, g, nullptr, R.pe);
         } else {
             if (R.pe == PE_UNIFORM) acc = row_local_map<LOGN, PE_UNIFORM>(v, t, row, nrow, erow, ngl, g);
             else if (R.pe == PE_TABLE) acc = row_local_map<LOGN, PE_TABLE>(v, t, row, nrow, erow, ngl, g);

@@ -18,6 +18,7 @@ LIB_PATH = os.environ.get("RT_LIBRARY") or os.path.join(HERE, "_lib", f"libbounc
 RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENUMERIC, RT_ETIMEOUT, RT_EBUSY = 0, -1, -2, -3, -4, -5, -6
 RT_PUMP_SUPERGAUSS, RT_PUMP_UNIFORM, RT_PUMP_ARRAY = 0, 1, 2
 RT_FP32, RT_FP64 = 0, 1
+RT_RELAX_EULER, RT_RELAX_EXACT = 0, 1
 
 
 class RtError(RuntimeError):
@@ -36,7 +37,8 @@ class rt_opts(ctypes.Structure):
                 ("seed", ctypes.c_ulonglong), ("noise_amp", ctypes.c_double),
                 ("pump_diam_over_window", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
                 ("history_cap", ctypes.c_longlong), ("chunk", ctypes.c_int), ("col_tile", ctypes.c_int),
-                ("z_over_F", ctypes.c_double), ("roughness", ctypes.c_void_p), ("slices", ctypes.c_int)]
+                ("z_over_F", ctypes.c_double), ("roughness", ctypes.c_void_p), ("slices", ctypes.c_int),
+                ("taper_px", ctypes.c_int), ("relax", ctypes.c_int)]
 
 
 class rt_job(ctypes.Structure):
@@ -44,7 +46,7 @@ class rt_job(ctypes.Structure):
                 ("R", ctypes.c_double), ("pump", rt_pump), ("Isat", ctypes.c_double), ("edge_px", ctypes.c_int),
                 ("seed", ctypes.c_ulonglong), ("noise_amp", ctypes.c_double),
                 ("pump_diam_over_window", ctypes.c_double), ("z_over_F", ctypes.c_double),
-                ("roughness", ctypes.c_void_p)]
+                ("roughness", ctypes.c_void_p), ("taper_px", ctypes.c_int), ("relax", ctypes.c_int)]
 
 
 class rt_serve_opts(ctypes.Structure):
@@ -313,7 +315,8 @@ class Resonator:
         """From a workloads.Resonator parameter record."""
         return cls(p.n, p.fresnel, p.g0, p.T1, p.R, precision=precision, pump_order=p.pump_order,
                    pump_radius=p.pump_radius, Isat=p.Isat, edge_px=p.edge, seed=p.seed, noise_amp=p.noise_amp,
-                   pump_diam_over_window=p.d_over_w, z_over_F=p.z_over_F, roughness=p.roughness(), **opts)
+                   pump_diam_over_window=p.d_over_w, z_over_F=p.z_over_F, roughness=p.roughness(),
+                   taper_px=p.taper_px, relax=p.relax, **opts)
 
     def step(self, n_bounces: int):
         rt_step(self.h, n_bounces)
@@ -388,7 +391,7 @@ def job_from_params(p) -> rt_job:
     j.fresnel, j.g0, j.T1, j.R = p.fresnel, p.g0, p.T1, p.R
     j.pump = rt_pump(kind=RT_PUMP_SUPERGAUSS, order=p.pump_order, radius=p.pump_radius, profile=None)
     j.Isat, j.edge_px, j.seed, j.noise_amp, j.pump_diam_over_window = p.Isat, p.edge, p.seed, p.noise_amp, p.d_over_w
-    j.z_over_F = p.z_over_F
+    j.z_over_F, j.taper_px, j.relax = p.z_over_F, p.taper_px, p.relax
     psi = p.roughness()
     if psi is not None:
         j._psi = np.ascontiguousarray(psi, np.float64)

@@ -41,6 +41,8 @@ class Resonator:
     z_over_F: float = 0.0        # curved mirror: distance per bounce over focal length (0 = flat)
     roughness_rms: float = 0.0   # mirror roughness phase, rms radians (0 = smooth)
     roughness_corr: float = 0.05  # its correlation length, fraction of the window half-width
+    taper_px: int = 0             # smooth aperture ramp inside the absorbing edge (0 = hard edge)
+    relax: int = 0                # inversion update: 0 explicit Euler step, 1 exact over the bounce
 
     def roughness(self):
         """The mirror's roughness phase psi (n x n float64), or None."""

@@ -68,7 +68,8 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib, args):
 def test_create_rejects_bad_options(lib):
     h = ctypes.c_void_p()
     for field, value in [("precision", 3), ("edge_px", -1), ("Isat", 0.0), ("history_cap", -5), ("chunk", -1),
-                         ("z_over_F", float("inf")), ("z_over_F", float("nan"))]:
+                         ("z_over_F", float("inf")), ("z_over_F", float("nan")), ("slices", -1), ("slices", 65),
+                         ("taper_px", -1), ("taper_px", 33), ("relax", 2)]:
         o = rt.rt_opts_default()
         setattr(o, field, value)
         assert lib.rt_create(64, 100.0, None, 0.2, 1000.0, 0.95, ctypes.byref(o), ctypes.byref(h)) == rt.RT_EINVAL
@@ -122,3 +123,14 @@ def test_struct_layouts_match_the_header(tmp_path, lib):
             rt.rt_job.z_over_F.offset, rt.rt_job.roughness.offset, ctypes.sizeof(rt.rt_serve_opts),
             ctypes.sizeof(rt.rt_result)]
     assert got == want
+
+
+def test_sliced_gain_medium_is_refused_where_unsupported(lib):
+    # Batches, serving and the allocation-free entry run single-slice bounces.
+    o = rt.rt_opts_default()
+    o.slices = 2
+    big = ctypes.c_void_p(16)
+    assert lib.rt_step_noalloc(64, 100.0, None, 0.2, 1000.0, 0.95, ctypes.byref(o), big, big, 1, None) == rt.RT_EINVAL
+    jobs = (rt.rt_job * 1)(rt.rt_job_default(64))
+    h = ctypes.c_void_p()
+    assert lib.rt_batch_create(jobs, 1, ctypes.byref(o), ctypes.byref(h)) == rt.RT_EINVAL and not h.value

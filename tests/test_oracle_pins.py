@@ -465,3 +465,135 @@ def test_paper_cavity_mirror_is_a_stable_lens_guide():
     u = 4.0 * g["cavity_length_m"] / g["mirror_radius_of_curvature_m"]
     assert abs(u - 0.16) < 1e-12
     assert abs(1.0 - u / 2.0) < 1.0
+
+
+# ----------------------------------------------------- multi-slice gain medium
+
+def test_slices_without_gain_compose_to_one_bounce():
+    # With no gain the m sub-steps of z/m compose to the diffraction over z
+    # (the propagator is a one-parameter group), and the mirror acts once:
+    # the m-slice map then equals the single-slice map.  Using z instead of
+    # z/m per slice, or the mirror in every slice, breaks this.
+    n = 64
+    rng = np.random.default_rng(4)
+    E0 = crandn(rng, (n, n))
+    psi = rng.normal(0.0, 0.5, (n, n))
+    kw = dict(edge=3, pump_kind=orc.PUMP_UNIFORM, z_over_F=0.3, roughness=psi)
+    one = orc.make_params(n, 0.03, 0.0, 50.0, 0.9, **kw)
+    four = orc.make_params(n, 0.03, 0.0, 50.0, 0.9, slices=4, **kw)
+    E1, _, h1 = orc.run(one, E0, np.zeros((n, n)), 3)
+    E4, N4, h4 = orc.run(four, E0, np.zeros((4, n, n)), 3)
+    assert rel_l2(E4, E1) < 1e-13
+    assert np.allclose(h4, h1, rtol=1e-13)
+    assert not np.any(N4)
+
+
+def test_slices_small_signal_gain_per_pass_is_g0():
+    # Each slice is pumped to N0/m, so a weak field gains exp(g0) in
+    # intensity per bounce whatever m (alpha = 2m makes every z/m step the
+    # identity on the grid; R = 1, no edge).
+    n, g0 = 16, 0.3
+    for m in (1, 2, 5):
+        p = orc.make_params(n, 2.0 * m, g0, 1e12, 1.0, edge=0, pump_kind=orc.PUMP_UNIFORM, slices=m)
+        E0 = np.full((n, n), 1e-6 + 0j)
+        E, N, _ = orc.run(p, E0, orc.initial_inversion(p), 1)
+        assert np.max(np.abs(E - math.exp(g0 / 2) * E0)) < 1e-20
+        assert np.max(np.abs(N - g0 / m)) < 1e-15
+
+
+@pytest.mark.parametrize("m", [2, 3])
+def test_slices_reach_the_saturated_amplifier_fixed_point(m):
+    # Uniform field and pump, identity diffraction: in steady state slice s
+    # holds N_s = (g0/m) / (1 + I_s/Isat) for the intensity I_s arriving at
+    # it, I_{s+1} = I_s exp(N_s), and the round trip closes with
+    # R exp(sum_s N_s) = 1.  The arriving intensity I_1 solves that scalar
+    # equation (bracketed root); the iterated map must converge to it.
+    from scipy.optimize import brentq
+
+    n, g0, R, Isat, T1 = 8, 0.3, 0.9, 1.5, 10.0
+
+    def chain(I1):
+        I, Ns = I1, []
+        for _ in range(m):
+            Ns.append((g0 / m) / (1.0 + I / Isat))
+            I *= math.exp(Ns[-1])
+        return Ns
+
+    I1 = brentq(lambda I: math.log(R) + sum(chain(I)), 1e-9, 100.0, xtol=1e-15)
+    p = orc.make_params(n, 2.0 * m, g0, T1, R, Isat=Isat, edge=0, pump_kind=orc.PUMP_UNIFORM, slices=m)
+    E, N, hist = orc.run(p, np.full((n, n), 0.5 + 0.2j), orc.initial_inversion(p), 4000)
+    assert abs(hist[-1] - I1) < 1e-10 * I1
+    for s, Ns in enumerate(chain(I1)):
+        assert np.max(np.abs(N[s] - Ns)) < 1e-10
+    # ... which is not the single-slice fixed point I* = Isat (g0 / N* - 1).
+    assert abs(I1 - Isat * (g0 / -math.log(R) - 1.0)) > 1e-3
+
+
+# -------------------------------------------- smooth aperture, exact relaxation
+
+def _aperture_after_one_bounce(n, edge, taper):
+    # alpha = 2: every diffraction phase is a multiple of 2 pi, so one bounce
+    # of a uniform field with no gain and R = 1 leaves exactly A(x) A(y).
+    p = orc.make_params(n, 2.0, 0.0, 1e9, 1.0, edge=edge, pump_kind=orc.PUMP_UNIFORM, taper=taper)
+    E, _, _ = orc.run(p, np.ones((n, n), np.complex128), np.zeros((n, n)), 1)
+    return E
+
+
+def test_taper_zero_is_the_hard_edge_and_the_ramp_is_a_sin2_profile():
+    n, edge = 64, 4
+    hard = _aperture_after_one_bounce(n, edge, 0)
+    band = np.zeros(n, bool)
+    band[:edge] = band[n - edge:] = True
+    assert np.all(hard[band, :] == 0) and np.all(hard[:, band] == 0) and np.all(hard[~band][:, ~band] == 1)
+    for w in (1, 3, 6):
+        E = _aperture_after_one_bounce(n, edge, w)
+        assert np.max(np.abs(E.imag)) == 0.0
+        A = E.real[n // 2]                        # the row through the centre: A(x) A(y_c), A(y_c) = 1
+        ramp = A[edge:edge + w]
+        assert np.all(A[band] == 0) and np.all(A[edge + w:n - edge - w] == 1)
+        assert np.allclose(A, A[::-1], atol=0, rtol=0)         # symmetric
+        assert np.all(np.diff(ramp) > 0) and ramp[-1] < 1.0     # rising, below 1
+        assert np.allclose(ramp + ramp[::-1], 1.0, atol=1e-15)  # sin^2 t + sin^2(pi/2 - t) = 1
+        assert abs(ramp[0] - math.sin(math.pi / (2 * (w + 1))) ** 2) < 1e-15
+        assert np.allclose(E.real, np.outer(A, A), atol=1e-15)  # separable
+    assert abs(_aperture_after_one_bounce(n, edge, 1).real[n // 2, edge] - 0.5) < 1e-15
+
+
+def test_exact_relaxation_field_free_closed_form():
+    # No field: dN/dt = (N0 - N)/T1 has N_b = N0 + (N_init - N0) exp(-b/T1),
+    # where the Euler step gives (1 - 1/T1)^b instead.
+    n, g0, T1, b = 8, 0.25, 7.0, 30
+    p = orc.make_params(n, 0.02, g0, T1, 0.9, edge=0, pump_kind=orc.PUMP_UNIFORM, relax=1)
+    _, N, _ = orc.run(p, np.zeros((n, n), np.complex128), np.full((n, n), 0.05), b)
+    assert np.max(np.abs(N - (g0 + (0.05 - g0) * math.exp(-b / T1)))) < 1e-15
+    q = orc.make_params(n, 0.02, g0, T1, 0.9, edge=0, pump_kind=orc.PUMP_UNIFORM, relax=0)
+    _, Ne, _ = orc.run(q, np.zeros((n, n), np.complex128), np.full((n, n), 0.05), b)
+    assert np.max(np.abs(Ne - (g0 + (0.05 - g0) * (1 - 1 / T1) ** b))) < 1e-15
+
+
+def test_exact_relaxation_differs_from_euler_by_the_second_order_term():
+    # One step with intensity I: exact minus Euler is
+    # (N - Nss) (exp(-h) - 1 + h), h = (1 + I/Isat)/T1, i.e. between
+    # (N - Nss) h^2/2 (1 - h/3) and (N - Nss) h^2/2.
+    n, g0, T1, Isat = 16, 0.3, 40.0, 1.3
+    rng = np.random.default_rng(8)
+    E0 = crandn(rng, (n, n))
+    N0 = rng.uniform(0.0, 0.5, (n, n))
+    kw = dict(Isat=Isat, edge=0, pump_kind=orc.PUMP_UNIFORM)
+    _, Nx, _ = orc.run(orc.make_params(n, 2.0, g0, T1, 0.9, relax=1, **kw), E0, N0, 1)
+    _, Ne, _ = orc.run(orc.make_params(n, 2.0, g0, T1, 0.9, relax=0, **kw), E0, N0, 1)
+    I = np.abs(E0) ** 2                        # alpha = 2: the field arriving at the gain is E0
+    h = (1 + I / Isat) / T1
+    dev = (N0 - g0 / (1 + I / Isat)) * h * h / 2
+    d = Nx - Ne
+    lo, hi = np.minimum(dev * (1 - h / 3), dev), np.maximum(dev * (1 - h / 3), dev)
+    assert np.all(d >= lo - 1e-16) and np.all(d <= hi + 1e-16)
+
+
+def test_exact_relaxation_keeps_the_saturation_fixed_point():
+    g0, R, Isat = 0.2, 0.95, 1.0
+    p = orc.make_params(8, 0.01, g0, 10.0, R, Isat=Isat, edge=0, pump_kind=orc.PUMP_UNIFORM, relax=1)
+    E, N, hist = orc.run(p, np.full((8, 8), 0.3 + 0.1j), np.full((8, 8), g0), 3000)
+    Nstar = -math.log(R)
+    assert np.max(np.abs(N - Nstar)) < 1e-12
+    assert abs(hist[-1] - Isat * (g0 / Nstar - 1.0)) < 1e-10

@@ -22,15 +22,16 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a, np.complex128) - b) / np.linalg.norm(b))
 
 
-@pytest.mark.parametrize("n, fresnel, g0, T1, R, z_over_F", [(256, 100.0, 0.3, 1000.0, 0.9, 0.0),
-                                                              (256, 100.0, 0.3, 1000.0, 0.9, 0.3),
-                                                              (2048, 1000.0, 0.3, 1e4, 0.9, 0.0)])
-def test_noalloc_matches_handle_path_on_two_calls(n, fresnel, g0, T1, R, z_over_F):
+@pytest.mark.parametrize("n, fresnel, g0, T1, R, z_over_F, taper_px, relax",
+                         [(256, 100.0, 0.3, 1000.0, 0.9, 0.0, 0, 0),
+                          (256, 100.0, 0.3, 1000.0, 0.9, 0.3, 5, 1),
+                          (2048, 1000.0, 0.3, 1e4, 0.9, 0.0, 0, 0)])
+def test_noalloc_matches_handle_path_on_two_calls(n, fresnel, g0, T1, R, z_over_F, taper_px, relax):
     import torch
 
     build.build()
     E0 = wl.smooth_field(n, 21, 1.0, dtype=np.complex64)
-    with rt.Resonator(n, fresnel, g0, T1, R, chunk=0, z_over_F=z_over_F) as ref:
+    with rt.Resonator(n, fresnel, g0, T1, R, chunk=0, z_over_F=z_over_F, taper_px=taper_px, relax=relax) as ref:
         N0 = ref.inversion()
         ref.set_field(E0)
         # Buffers owned by the caller (here allocated by the test, not by the entry point).
@@ -38,7 +39,8 @@ def test_noalloc_matches_handle_path_on_two_calls(n, fresnel, g0, T1, R, z_over_
         N_dev = torch.from_numpy(N0.copy()).cuda()
         opts = rt.rt_opts_default()
         opts.cuda_stream = torch.cuda.current_stream().cuda_stream
-        opts.z_over_F = z_over_F  # a curved mirror needs only per-axis factors: no allocation
+        # a curved mirror and a taper need only per-axis factors: no allocation
+        opts.z_over_F, opts.taper_px, opts.relax = z_over_F, taper_px, relax
         for nb in (7, 5):
             ref.step(nb)
             mean = rt.rt_step_noalloc(n, fresnel, None, g0, T1, R, opts, E_dev, N_dev, nb)
