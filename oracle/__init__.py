@@ -66,6 +66,21 @@ class Params(ctypes.Structure):
 
 
 PUMP_SUPERGAUSS, PUMP_UNIFORM, PUMP_ARRAY = 0, 1, 2
+PATTERN_GAUSSIAN, PATTERN_BEAM_ARRAY, PATTERN_VORTEX_ARRAY = 0, 1, 2
+
+
+class Pattern(ctypes.Structure):
+    """Field-for-field mirror of ``orc_pattern_t`` in bouncemap_oracle.c."""
+
+    _fields_ = [
+        ("kind", ctypes.c_int),
+        ("periods", ctypes.c_int),
+        ("out_of_phase", ctypes.c_int),
+        ("width", ctypes.c_double),
+        ("envelope", ctypes.c_double),
+        ("curvature", ctypes.c_double),
+        ("amplitude", ctypes.c_double),
+    ]
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -90,6 +105,8 @@ def lib() -> ctypes.CDLL:
             L.orc_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
             L.orc_splitmix64.restype = ctypes.c_uint64
             L.orc_noise.argtypes = [i, ctypes.c_uint64, d, vp]
+            L.orc_pattern.argtypes = [i, ctypes.POINTER(Pattern), vp]
+            L.orc_pattern.restype = i
             L.orc_run.argtypes = [ctypes.POINTER(Params), vp, vp, ctypes.c_longlong, vp, i]
             L.orc_run.restype = i
             L.orc_spectrum.argtypes = [vp, i, vp, i]
@@ -183,6 +200,17 @@ def initial_inversion(params: Params) -> np.ndarray:
 
 def splitmix64(seed: int, c: int) -> int:
     return int(lib().orc_splitmix64(seed, c))
+
+
+def pattern(n, kind, width, periods=1, out_of_phase=False, envelope=0.0, curvature=0.0,
+            amplitude=1.0) -> np.ndarray:
+    """Structured starting field (Gaussian beam, beam array, vortex array)."""
+    pt = Pattern(kind=kind, periods=periods, out_of_phase=int(bool(out_of_phase)), width=width, envelope=envelope,
+                 curvature=curvature, amplitude=amplitude)
+    E = np.empty((n, n), np.complex128)
+    if lib().orc_pattern(n, ctypes.byref(pt), E.ctypes.data) != 0:
+        raise ValueError("invalid pattern")
+    return E
 
 
 def noise(n, seed, amp) -> np.ndarray:

@@ -279,6 +279,73 @@ void orc_noise(int n, uint64_t seed, double amp, cplx *E)
 }
 
 /* ------------------------------------------------------------------------
+ * Structured starting fields: the Gaussian beam, the periodic array of
+ * Gaussian beams and the array of first-order vortices of the exact
+ * solutions (eqs. Field_exact11, Field_exact112), on the periodic window.
+ * ---------------------------------------------------------------------- */
+
+/* Mirrored field by field by the ctypes structure in oracle/__init__.py. */
+typedef struct {
+    int kind;            /* 0 Gaussian beam, 1 array of Gaussian beams, 2 array of vortices */
+    int periods;         /* q lattice periods across the window (period p = 2/q) */
+    int out_of_phase;    /* alternate neighbours: beam sign (kind 1) or vortex charge (kind 2) */
+    double width;        /* Gaussian radius w of a beam or vortex core */
+    double envelope;     /* radius of the common Gaussian envelope (0: none) */
+    double curvature;    /* common phase front exp(-i c r^2) */
+    double amplitude;
+} orc_pattern_t;
+
+static double pixel_coord_of(int j, int n) { return (double)(j - n / 2) / (double)(n / 2); }
+
+/* Shortest signed displacement on the periodic window of width 2. */
+static double wrap2(double u) { return u - 2.0 * floor(u / 2.0 + 0.5); }
+
+/* E(x, y) = amplitude * exp(-r^2 / (2 envelope^2)) * exp(-i c r^2) * S(x, y)
+ * with S = exp(-r^2/(2w^2)) for the single beam, and for the arrays the sum
+ * over the q*q lattice points (a p, b p), a, b = 0..q-1, of
+ *   beams:    s_ab exp(-d^2/(2w^2)),                 s_ab = (-1)^(a+b) or 1
+ *   vortices: ((dx + i k_ab dy)/w) exp(-d^2/(2w^2)),  k_ab = (-1)^(a+b) or 1
+ * (k_ab the topological charge), with (dx, dy) the shortest displacement
+ * from the lattice point on the periodic window; points whose Gaussian
+ * exponent d^2/(2w^2) exceeds 50 are left out.  Returns -1 on bad input. */
+int orc_pattern(int n, const orc_pattern_t *pt, cplx *E)
+{
+    if (!is_pow2(n) || pt->width <= 0.0 || pt->envelope < 0.0 || pt->kind < 0 || pt->kind > 2) return -1;
+    if (pt->kind > 0 && (pt->periods < 1 || (pt->out_of_phase && pt->periods % 2))) return -1;
+    int q = pt->periods;
+    double p = 2.0 / (double)q, w2 = pt->width * pt->width;
+    for (int y = 0; y < n; ++y) {
+        double yc = pixel_coord_of(y, n);
+        for (int x = 0; x < n; ++x) {
+            double xc = pixel_coord_of(x, n);
+            double r2 = xc * xc + yc * yc;
+            cplx S = 0.0;
+            if (pt->kind == 0) {
+                S = exp(-r2 / (2.0 * w2));
+            } else {
+                for (int b = 0; b < q; ++b) {
+                    double dy = wrap2(yc - b * p);
+                    for (int a = 0; a < q; ++a) {
+                        double dx = wrap2(xc - a * p);
+                        double e = (dx * dx + dy * dy) / (2.0 * w2);
+                        if (e > 50.0) continue;
+                        double alt = pt->out_of_phase && ((a + b) & 1) ? -1.0 : 1.0;
+                        if (pt->kind == 1)
+                            S += alt * exp(-e);
+                        else
+                            S += (dx + alt * dy * _Complex_I) / pt->width * exp(-e);
+                    }
+                }
+            }
+            double env = pt->envelope > 0.0 ? exp(-r2 / (2.0 * pt->envelope * pt->envelope)) : 1.0;
+            double ph = -pt->curvature * r2;
+            E[(size_t)y * n + x] = pt->amplitude * env * (cos(ph) + sin(ph) * _Complex_I) * S;
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
  * The bounce map.
  * ---------------------------------------------------------------------- */
 

@@ -597,3 +597,77 @@ def test_exact_relaxation_keeps_the_saturation_fixed_point():
     Nstar = -math.log(R)
     assert np.max(np.abs(N - Nstar)) < 1e-12
     assert abs(hist[-1] - Isat * (g0 / Nstar - 1.0)) < 1e-10
+
+
+# ------------------------------------------------------ structured starting fields
+
+def _winding(E, j, i):
+    # total phase change, in turns, around the 8 pixels surrounding (row j, column i)
+    ring = [(-1, -1), (-1, 0), (-1, 1), (0, 1), (1, 1), (1, 0), (1, -1), (0, -1), (-1, -1)]
+    ph = [np.angle(E[j + dj, i + di]) for dj, di in ring]
+    d = np.diff(ph)
+    d = (d + np.pi) % (2 * np.pi) - np.pi
+    return d.sum() / (2 * np.pi)
+
+
+@pytest.mark.parametrize("out_of_phase", [False, True])
+def test_vortex_array_has_unit_charges_on_the_lattice(out_of_phase):
+    # A lattice of first-order vortices (the vortex-array solution): the
+    # phase winds once around every lattice point, with alternating sign for
+    # the out-of-phase array (antiparallel charges) and the same sign for the
+    # in-phase one; the intensity vanishes there.
+    n, q, w = 128, 8, 0.06
+    E = orc.pattern(n, orc.PATTERN_VORTEX_ARRAY, w, periods=q, out_of_phase=out_of_phase)
+    step = n // q                                  # lattice points fall on pixel centres
+    for b in range(q):
+        for a in range(q):
+            j, i = (n // 2 + b * step) % n, (n // 2 + a * step) % n
+            want = (-1) ** (a + b) if out_of_phase else 1
+            assert abs(_winding(E, j, i) - want) < 1e-9, (a, b)
+            assert abs(E[j, i]) < 1e-12
+
+
+def test_beam_array_is_periodic_and_self_images_at_the_talbot_length():
+    # The array of Gaussian beams is periodic with p = 2/q on the window, so
+    # (with no envelope) it returns after the Talbot length, alpha q^2 = 2,
+    # and is shifted by half a period at half of it.
+    n, q, w = 128, 8, 0.04
+    E = orc.pattern(n, orc.PATTERN_BEAM_ARRAY, w, periods=q)
+    step = n // q
+    assert rel_l2(np.roll(E, (step, step), axis=(0, 1)), E) < 1e-15
+    assert rel_l2(orc.diffract(E, 2.0 / q ** 2), E) < 1e-12
+    assert rel_l2(orc.diffract(E, 1.0 / q ** 2), np.roll(E, (step // 2, step // 2), axis=(0, 1))) < 1e-12
+    # out of phase: the sign alternates between neighbours, period 2p
+    F = orc.pattern(n, orc.PATTERN_BEAM_ARRAY, w, periods=q, out_of_phase=True)
+    assert rel_l2(np.roll(F, step, axis=1), -F) < 1e-15
+    tail = 4 * math.exp(-(2.0 / q) ** 2 / (2 * w * w))    # the four nearest neighbours' tails
+    assert abs(F[n // 2, n // 2] - 1.0) < 1.01 * tail and abs(F[n // 2, n // 2 + step] + 1.0) < 1.01 * tail
+
+
+def test_gaussian_envelope_multiplies_like_a_narrower_gaussian():
+    # exp(-r^2/(2w^2)) exp(-r^2/(2D^2)) = exp(-r^2/(2 w'^2)), 1/w'^2 = 1/w^2 + 1/D^2
+    n, w, D = 64, 0.2, 0.3
+    a = orc.pattern(n, orc.PATTERN_GAUSSIAN, w, envelope=D, amplitude=2.5)
+    b = orc.pattern(n, orc.PATTERN_GAUSSIAN, 1.0 / math.sqrt(1 / w ** 2 + 1 / D ** 2), amplitude=2.5)
+    assert np.max(np.abs(a - b)) < 1e-14
+
+
+def test_gaussian_pattern_with_curvature_is_the_lens_guide_eigenmode():
+    # exp(-r^2/(2 w^2) - i c r^2) = exp(-r^2/(2 s)) with 1/s = 1/w^2 + 2 i c:
+    # built from the eigenmode s of the flat/curved-mirror cavity it returns
+    # each bounce with the Gouy phase exp(-i arccos(1 - z/2F)).
+    n, u, beta = 128, 1.0, 0.008
+    alpha = math.pi * beta / 2.0
+    s = _lens_guide_eigenmode(u, beta)
+    w, c = 1.0 / math.sqrt((1 / s).real), (1 / s).imag / 2.0
+    E0 = orc.pattern(n, orc.PATTERN_GAUSSIAN, w, curvature=c)
+    p = orc.make_params(n, alpha, 0.0, 1e9, 1.0, edge=0, pump_kind=orc.PUMP_UNIFORM, z_over_F=u)
+    E3, _, _ = orc.run(p, E0, np.zeros((n, n)), 3)
+    assert np.max(np.abs(E3 - np.exp(-3j * math.acos(1 - u / 2)) * E0)) < 1e-11
+
+
+def test_pattern_rejects_bad_input():
+    with pytest.raises(ValueError):
+        orc.pattern(64, orc.PATTERN_BEAM_ARRAY, 0.05, periods=7, out_of_phase=True)   # odd q cannot alternate
+    with pytest.raises(ValueError):
+        orc.pattern(64, orc.PATTERN_GAUSSIAN, 0.0)
