@@ -205,6 +205,41 @@ rt_status rt_read_history(rt_handle *h, double *dst, long long max, long long *g
  * double, unnormalised) to dst (host or device).  Blocks. */
 rt_status rt_read_spectrum(rt_handle *h, void *dst, size_t bytes);
 
+/* Structured starting fields of the exact solutions (section "Exact
+ * solutions", eqs. Field_exact11 and Field_exact112), evaluated in FP64 on
+ * the periodic window (x, y in [-1, 1), period 2):
+ *
+ *   E = amplitude * exp(-r^2 / (2 envelope^2)) * exp(-i curvature r^2) * S,
+ *
+ * envelope 0 meaning no envelope, and S
+ *   RT_PATTERN_GAUSSIAN      exp(-r^2 / (2 width^2)), one beam on the axis;
+ *   RT_PATTERN_BEAM_ARRAY    sum over the periods^2 lattice points (a p, b p),
+ *                            p = 2 / periods, a, b = 0 .. periods-1, of
+ *                            s_ab exp(-d^2 / (2 width^2));
+ *   RT_PATTERN_VORTEX_ARRAY  the same sum of first-order vortices
+ *                            ((dx + i k_ab dy) / width) exp(-d^2 / (2 width^2)),
+ * with (dx, dy) the shortest displacement from the lattice point on the
+ * periodic window, d^2 = dx^2 + dy^2, terms with d^2 / (2 width^2) > 50
+ * left out, and s_ab (beam sign) or k_ab (vortex charge) = (-1)^(a+b) when
+ * out_of_phase is set (periods must then be even), else 1.
+ * The Talbot condition of eq. Field_exact11 (cavity length m p^2 / lambda)
+ * is alpha * periods^2 = 2m in the units of this library. */
+enum { RT_PATTERN_GAUSSIAN = 0, RT_PATTERN_BEAM_ARRAY = 1, RT_PATTERN_VORTEX_ARRAY = 2 };
+typedef struct {
+    int kind;             /* RT_PATTERN_* */
+    int periods;          /* arrays: lattice periods across the window (>= 1) */
+    int out_of_phase;     /* arrays: neighbours alternate in sign (beams) or charge (vortices) */
+    double width;         /* beam or vortex-core radius, window units (> 0) */
+    double envelope;      /* radius of the common Gaussian envelope (>= 0; 0 = none) */
+    double curvature;     /* common phase front exp(-i curvature r^2) (finite) */
+    double amplitude;     /* overall factor (finite) */
+} rt_pattern;
+
+/* Replace the handle's field with a structured field (ordered on the
+ * handle's stream; the inversion and counters are left as they are).
+ * RT_EINVAL for an invalid pattern. */
+rt_status rt_set_field_pattern(rt_handle *h, const rt_pattern *pattern);
+
 /* The field at an intracavity plane: the current field (at the mirror and
  * gain plane) diffracted a further zeta * z, zeta any finite real (negative
  * values propagate backwards; zeta = 1 is one bounce's diffraction without

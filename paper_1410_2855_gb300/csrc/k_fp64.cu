@@ -201,6 +201,13 @@ cudaError_t launch_phase64(int n, double c, int edge, int taper, const double *p
     return cudaGetLastError();
 }
 
+cudaError_t launch_pattern64(int n, int kind, int q, int alt, double w, double env, double curv, double amp,
+                             double2 *E, cudaStream_t s)
+{
+    k_pattern<double2><<<grid_for((size_t)n * n, 256, 2048), 256, 0, s>>>(n, kind, q, alt, w, env, curv, amp, E);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pump64(int n, int kind, double g0, double order, double radius, const double *profile,
                           double *out, cudaStream_t s)
 {

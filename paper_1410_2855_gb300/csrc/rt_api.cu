@@ -576,6 +576,26 @@ rt_status rt_read_spectrum(rt_handle *h, void *dst, size_t bytes)
     return check_device_error(h);
 }
 
+rt_status rt_set_field_pattern(rt_handle *h, const rt_pattern *pt)
+{
+    if (!h || !pt) return RT_EINVAL;
+    if (pt->kind < RT_PATTERN_GAUSSIAN || pt->kind > RT_PATTERN_VORTEX_ARRAY) return RT_EINVAL;
+    if (!finite_pos(pt->width) || !std::isfinite(pt->envelope) || pt->envelope < 0.0) return RT_EINVAL;
+    if (!std::isfinite(pt->curvature) || !std::isfinite(pt->amplitude)) return RT_EINVAL;
+    if (pt->kind != RT_PATTERN_GAUSSIAN &&
+        (pt->periods < 1 || pt->periods > 4096 || (pt->out_of_phase && (pt->periods & 1))))
+        return RT_EINVAL;
+    DeviceGuard dg(h->device);
+    const int q = pt->kind == RT_PATTERN_GAUSSIAN ? 1 : pt->periods, alt = pt->out_of_phase ? 1 : 0;
+    if (h->precision == RT_FP32)
+        RT_TRY(launch_pattern32(h->n, pt->kind, q, alt, pt->width, pt->envelope, pt->curvature, pt->amplitude,
+                                static_cast<float2 *>(h->E), h->stream));
+    else
+        RT_TRY(launch_pattern64(h->n, pt->kind, q, alt, pt->width, pt->envelope, pt->curvature, pt->amplitude,
+                                static_cast<double2 *>(h->E), h->stream));
+    return RT_OK;
+}
+
 rt_status rt_read_field_at(rt_handle *h, double zeta, void *dst, size_t bytes)
 {
     if (!h || !dst || !std::isfinite(zeta)) return RT_EINVAL;

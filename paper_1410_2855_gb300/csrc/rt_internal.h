@@ -163,6 +163,11 @@ template <typename R> __host__ __device__ inline bool needs_general(const GainPa
 {
     return g.lens || g.phase || g.relax_exact;
 }
+// Structured starting field (rt_set_field_pattern), FP64 arithmetic.
+cudaError_t launch_pattern32(int n, int kind, int q, int alt, double w, double env, double curv, double amp,
+                             float2 *E, cudaStream_t s);
+cudaError_t launch_pattern64(int n, int kind, int q, int alt, double w, double env, double curv, double amp,
+                             double2 *E, cudaStream_t s);
 // N0 = g0 * P in FP64 (profile: device array of n*n doubles or null), stored as R.
 cudaError_t launch_pump32(int n, int kind, double g0, double order, double radius, const double *profile,
                           float *out, cudaStream_t s);

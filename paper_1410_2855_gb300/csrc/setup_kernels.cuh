@@ -89,6 +89,58 @@ __global__ void k_phase_table(int n, double c_over_pi, int edge, int taper, cons
     }
 }
 
+// Structured starting fields (rt_set_field_pattern): a Gaussian beam, or a
+// q x q lattice of Gaussian beams or first-order vortices on the periodic
+// window, times a Gaussian envelope and a phase front; FP64 arithmetic.
+// Only lattice points within 10 widths can pass the cutoff, so each pixel
+// visits the 2K+1 nearest indices per axis (all q when that covers them).
+__device__ __forceinline__ double wrap_window(double u) { return u - 2.0 * floor(u / 2.0 + 0.5); }
+
+template <typename V>
+__global__ void k_pattern(int n, int kind, int q, int alt, double w, double env, double curv, double amp, V *E)
+{
+    const size_t P = (size_t)n * n;
+    const double p = 2.0 / (double)q, inv2w2 = 1.0 / (2.0 * w * w);
+    const int K = (int)ceil(10.0 * w / p) + 1;
+    const bool all = 2 * K + 1 >= q;
+    const int cnt = all ? q : 2 * K + 1;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < P; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % n), y = (int)(i / n);
+        const double xc = (double)(x - n / 2) / (double)(n / 2);
+        const double yc = (double)(y - n / 2) / (double)(n / 2);
+        const double r2 = xc * xc + yc * yc;
+        double sr = 0.0, si = 0.0;
+        if (kind == 0) {
+            sr = exp(-r2 * inv2w2);
+        } else {
+            const int ax = all ? 0 : (int)floor(xc / p + 0.5) - K;
+            const int by = all ? 0 : (int)floor(yc / p + 0.5) - K;
+            for (int bj = 0; bj < cnt; ++bj) {
+                const int b = ((by + bj) % q + q) % q;
+                const double dy = wrap_window(yc - b * p);
+                for (int aj = 0; aj < cnt; ++aj) {
+                    const int a = ((ax + aj) % q + q) % q;
+                    const double dx = wrap_window(xc - a * p);
+                    const double e = (dx * dx + dy * dy) * inv2w2;
+                    if (e > 50.0) continue;
+                    const double sgn = (alt && ((a + b) & 1)) ? -1.0 : 1.0;
+                    const double g = exp(-e);
+                    if (kind == 1) {
+                        sr += sgn * g;
+                    } else {
+                        sr += dx / w * g;
+                        si += sgn * dy / w * g;
+                    }
+                }
+            }
+        }
+        const double f = amp * (env > 0.0 ? exp(-r2 / (2.0 * env * env)) : 1.0);
+        double sp, cp;
+        sincos(-curv * r2, &sp, &cp);
+        E[i] = cmk<V>(f * (cp * sr - sp * si), f * (cp * si + sp * sr));
+    }
+}
+
 // Pass-major twiddle table of the line FFT of length 2^logn (layout in
 // fft_core.cuh): for each pass after the first, with span Ns and radix R,
 // entry (r-1)*Ns + j holds exp(-2 pi i r j / (Ns R)).  FP64 sincospi on the

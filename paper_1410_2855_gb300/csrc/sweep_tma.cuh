@@ -222,11 +222,13 @@ __device__ __forceinline__ void diffract_line(float2 (&v)[16], int t, LineBufs<f
     fft_line<LOGN, +1, CS>(v, t, lb, tw, sync);
 }
 
-// Per-resonator mean intensity of a batched row sweep: each item (row group)
-// stores its block sum; the last item of a resonator to arrive adds them up
-// in item order and records the mean (deterministic).
+// Per-resonator mean intensity of a batched row sweep.  A block keeps one
+// running sum per resonator while it works through that resonator's items
+// and, when it moves on, stores the block sum in slot k of the resonator's
+// partials; the last of the `arrivals` blocks to do so adds the partials up
+// in slot order and records the mean (deterministic for a given grid).
 template <int NT>
-__device__ __forceinline__ void item_finish(double v, const StatParams &st, int item, int nitems, double inv_points)
+__device__ __forceinline__ void res_finish(double v, const StatParams &st, int k, int arrivals, double inv_points)
 {
     static_assert(NT % 32 == 0, "whole warps");
     __shared__ double red[NT / 32];
@@ -240,15 +242,15 @@ __device__ __forceinline__ void item_finish(double v, const StatParams &st, int 
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < NT / 32; ++w) s += red[w];
-        st.part[item] = s;
+        st.part[k] = s;
         __threadfence();
-        is_last = (atomicAdd(st.count, 1u) == (unsigned)nitems - 1u);
+        is_last = (atomicAdd(st.count, 1u) == (unsigned)arrivals - 1u);
     }
     __syncthreads();
     if (!is_last) return;
     __threadfence();
     double s = 0.0;
-    for (int i = threadIdx.x; i < nitems; i += NT) s += __ldcg(st.part + i);
+    for (int i = threadIdx.x; i < arrivals; i += NT) s += __ldcg(st.part + i);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     __syncthreads();
@@ -411,15 +413,22 @@ k_row_tma_batch(const BatchRes *__restrict__ res, int nres, const float2 *__rest
     init_stage_barriers(bar);
     int item = next_active(blockIdx.x);
     if (threadIdx.x == 0 && item < nitems) issue(0, item);
+    // The blocks that touch an active resonator r are the residues modulo
+    // the grid of its items [rG, rG + G): min(G, grid) of them, and block b
+    // files its partial under slot (b - rG) mod grid, which is < min(G, grid).
+    const int grid = (int)gridDim.x;
+    const int arrivals = G < grid ? G : grid;
+    double dacc = 0.0;
     for (int it = 0; item < nitems; ++it) {
         const int s = it & 1;
-        const int nxt = next_active(item + (int)gridDim.x);
+        const int nxt = next_active(item + grid);
         if (threadIdx.x == 0 && nxt < nitems) {
             fence_proxy_async_smem();
             issue(s ^ 1, nxt);
         }
         if (stage_wait_or_abort(bar, it, nxt < nitems, err)) break;
-        const BatchRes &R = res[item / G];
+        const int r = item / G;
+        const BatchRes &R = res[r];
         const int grp = item % G;
         const int row = grp * LPC + lig;
         float2 *line = stage_e(s) + lig * LS;
@@ -441,7 +450,13 @@ k_row_tma_batch(const BatchRes *__restrict__ res, int nres, const float2 *__rest
             else if (R.pe == PE_TABLE) acc = row_local_map<LOGN, PE_TABLE>(v, t, row, nrow, erow, ngl, g);
             else acc = row_local_map<LOGN, PE_SG10>(v, t, row, nrow, erow, ngl, g);
         }
-        item_finish<NT>((double)acc, R.st, grp, G, 1.0 / ((double)N * (double)N));  // barriers inside
+        dacc += (double)acc;
+        __syncthreads();  // stage s fully consumed before it is refilled
+        if (nxt >= nitems || nxt / G != r) {
+            const int k = (int)((((long long)blockIdx.x - (long long)r * G) % grid + grid) % grid);
+            res_finish<NT>(dacc, R.st, k, arrivals, 1.0 / ((double)N * (double)N));
+            dacc = 0.0;
+        }
         item = nxt;
     }
 }

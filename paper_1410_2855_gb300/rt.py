@@ -19,6 +19,7 @@ RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENUMERIC, RT_ETIMEOUT, RT_EBUSY = 0, -
 RT_PUMP_SUPERGAUSS, RT_PUMP_UNIFORM, RT_PUMP_ARRAY = 0, 1, 2
 RT_FP32, RT_FP64 = 0, 1
 RT_RELAX_EULER, RT_RELAX_EXACT = 0, 1
+RT_PATTERN_GAUSSIAN, RT_PATTERN_BEAM_ARRAY, RT_PATTERN_VORTEX_ARRAY = 0, 1, 2
 
 
 class RtError(RuntimeError):
@@ -39,6 +40,12 @@ class rt_opts(ctypes.Structure):
                 ("history_cap", ctypes.c_longlong), ("chunk", ctypes.c_int), ("col_tile", ctypes.c_int),
                 ("z_over_F", ctypes.c_double), ("roughness", ctypes.c_void_p), ("slices", ctypes.c_int),
                 ("taper_px", ctypes.c_int), ("relax", ctypes.c_int)]
+
+
+class rt_pattern(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("periods", ctypes.c_int), ("out_of_phase", ctypes.c_int),
+                ("width", ctypes.c_double), ("envelope", ctypes.c_double), ("curvature", ctypes.c_double),
+                ("amplitude", ctypes.c_double)]
 
 
 class rt_job(ctypes.Structure):
@@ -99,6 +106,7 @@ def lib() -> ctypes.CDLL:
             "rt_read_history": [vp, vp, ll, ctypes.POINTER(ll)],
             "rt_read_spectrum": [vp, vp, sz],
             "rt_read_field_at": [vp, d, vp, sz],
+            "rt_set_field_pattern": [vp, ctypes.POINTER(rt_pattern)],
             "rt_spectrum_peak": [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(d)],
             "rt_destroy": [vp],
             "rt_step_noalloc": [i, d, ctypes.POINTER(rt_pump), d, d, d, ctypes.POINTER(rt_opts), vp, vp, ll,
@@ -242,6 +250,10 @@ def rt_read_spectrum(h, dst):
     return dst
 
 
+def rt_set_field_pattern(h, pattern: rt_pattern):
+    _check(lib().rt_set_field_pattern(h, ctypes.byref(pattern)), "rt_set_field_pattern")
+
+
 def rt_read_field_at(h, zeta: float, dst):
     _check(lib().rt_read_field_at(h, float(zeta), _ptr(dst), _nbytes(dst)), "rt_read_field_at")
     return dst
@@ -343,6 +355,13 @@ class Resonator:
 
     def spectrum(self) -> np.ndarray:
         return rt_read_spectrum(self.h, np.empty((self.n, self.n), self.rdtype))
+
+    def set_pattern(self, kind, width, periods=1, out_of_phase=False, envelope=0.0, curvature=0.0, amplitude=1.0):
+        """Replace the field with a structured field (rt_set_field_pattern)."""
+        rt_set_field_pattern(self.h, rt_pattern(kind=kind, periods=periods, out_of_phase=int(bool(out_of_phase)),
+                                                width=width, envelope=envelope, curvature=curvature,
+                                                amplitude=amplitude))
+        rt_sync(self.h)
 
     def field_at(self, zeta: float) -> np.ndarray:
         """The field diffracted a further zeta bounces' distance (intracavity plane)."""

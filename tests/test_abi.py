@@ -94,6 +94,7 @@ def test_noalloc_rejects_oversize_and_unsupported_requests_on_the_host(lib):
 def test_null_handles_are_rejected(lib):
     assert lib.rt_step(None, 1) == rt.RT_EINVAL
     assert lib.rt_read_field_at(None, 0.5, None, 0) == rt.RT_EINVAL
+    assert lib.rt_set_field_pattern(None, None) == rt.RT_EINVAL
     assert lib.rt_sync(None) == rt.RT_EINVAL
     assert lib.rt_read_field(None, None, 0) == rt.RT_EINVAL
     assert lib.rt_destroy(None) == rt.RT_OK
