@@ -60,6 +60,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--bounces-per-step", type=int, default=500)
     ap.add_argument("--no-comparisons", action="store_true", help="skip the comparison legs")
+    ap.add_argument("--col-tile", type=int, default=0, help="fixed column-sweep tile width (0: autotune)")
     return ap.parse_args()
 
 
@@ -350,7 +351,12 @@ def run_ours(args):
     B, K, W = args.bounces_per_step, args.steps, args.warmup
     params = workload(rank)
     from paper_1410_2855_gb300 import tune
-    col_tile, col_us = tune.rt_autotune(params[0].n, reps=50)   # column-sweep tile width for this GPU
+    if args.col_tile:
+        tune.rt_tune_set(params[0].n, args.col_tile)
+        col_tile, tile_source = args.col_tile, "fixed on the command line"
+    else:
+        col_tile, _ = tune.rt_autotune(params[0].n, reps=50)   # column-sweep tile width for this GPU
+        tile_source = "autotuned at start-up"
     streams = [torch.cuda.Stream(device=dev) for _ in params]
     res = [rt.Resonator.from_params(p, precision=rt.RT_FP32, cuda_stream=s.cuda_stream, chunk=B)
            for p, s in zip(params, streams)]
@@ -422,7 +428,7 @@ def run_ours(args):
                                          "stays L2-resident within a step",
                                    "graph": f"one CUDA graph per {B} bounces per resonator",
                                    "streams": "one per resonator, concurrent",
-                                   "col_tile": col_tile, "col_tile_source": "autotuned at start-up"}),
+                                   "col_tile": col_tile, "col_tile_source": tile_source}),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": dom_gbs, "peak": peak, "unit": "GB/s",
                      "frac": dom_gbs / peak, "peak_kind": f"of {peak_kind}",
                      "traffic": profiled_traffic(dom, params[0].n),
@@ -523,6 +529,37 @@ def comparisons(args, rt, torch, main, streams, params, res, E0, N0, rank, world
                     "row_sweep_ms": ev[0].elapsed_time(ev[50]) / 50}
     extra["curved_mirror"]["workload"] = ("2048^2, N_F 1000, g0 0.3, R 0.9; z/F 0.16 (50 mm mirror, L 2 mm); "
                                           "roughness 0.05 rad rms; one stream, graphs of %d bounces" % B)
+
+    # ---- the other extensions of the map on the same 2048^2 resonator, one stream
+    base = params[1]
+    variants = {"slices_4": dict(slices=4), "taper16_exact_relax": dict(taper_px=16, relax=rt.RT_RELAX_EXACT)}
+    extra["extensions"] = {}
+    for name, kw in variants.items():
+        with torch.cuda.stream(main):
+            with rt.Resonator.from_params(base, cuda_stream=main.cuda_stream, chunk=100, **kw) as r:
+                r.step(100)
+                torch.cuda.synchronize()
+                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s.record(main)
+                r.step(400)
+                e.record(main)
+                torch.cuda.synchronize()
+                r.sync()
+                extra["extensions"][name] = {"round_trips_per_s": 400 / (s.elapsed_time(e) / 1e3)}
+    with rt.Resonator.from_params(base, cuda_stream=main.cuda_stream, chunk=0) as r:
+        buf = np.empty((base.n, base.n), np.complex64)
+        r.field_at(0.5)
+        t0 = time.perf_counter()
+        for _ in range(5):
+            rt.rt_read_field_at(r.h, 0.5, buf)
+        extra["extensions"]["field_at_ms"] = (time.perf_counter() - t0) / 5 * 1e3
+        r.set_pattern(rt.RT_PATTERN_VORTEX_ARRAY, 0.01, periods=64, out_of_phase=True, envelope=0.6)
+        t0 = time.perf_counter()
+        for _ in range(5):
+            r.set_pattern(rt.RT_PATTERN_VORTEX_ARRAY, 0.01, periods=64, out_of_phase=True, envelope=0.6)
+        extra["extensions"]["vortex_pattern_ms"] = (time.perf_counter() - t0) / 5 * 1e3
+    extra["extensions"]["workload"] = ("2048^2, N_F 1000, g0 0.3, R 0.9, one stream; field_at and the pattern "
+                                       "include the host copy / synchronisation (wall clock)")
 
     # ---- batched parameter sweep: 256 resonators of side 256/512/1024 in one graph per 100 bounces
     jobs = wl.batch_sweep(count=256, sides=(256, 512, 1024))
