@@ -532,11 +532,12 @@ def comparisons(args, rt, torch, main, streams, params, res, E0, N0, rank, world
 
     # ---- the other extensions of the map on the same 2048^2 resonator, one stream
     base = params[1]
-    variants = {"slices_4": dict(slices=4), "taper16_exact_relax": dict(taper_px=16, relax=rt.RT_RELAX_EXACT)}
+    variants = {"slices_4": (base, dict(slices=4)),
+                "taper16_exact_relax": (dataclasses.replace(base, taper_px=16, relax=rt.RT_RELAX_EXACT), {})}
     extra["extensions"] = {}
-    for name, kw in variants.items():
+    for name, (q, kw) in variants.items():
         with torch.cuda.stream(main):
-            with rt.Resonator.from_params(base, cuda_stream=main.cuda_stream, chunk=100, **kw) as r:
+            with rt.Resonator.from_params(q, cuda_stream=main.cuda_stream, chunk=100, **kw) as r:
                 r.step(100)
                 torch.cuda.synchronize()
                 s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
