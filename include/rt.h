@@ -87,7 +87,8 @@ typedef enum {
     RT_ECUDA = -3,     /* a CUDA runtime call failed */
     RT_ENUMERIC = -4,  /* the field's mean intensity became NaN or Inf */
     RT_ETIMEOUT = -5,  /* a bounded wait ran out */
-    RT_EBUSY = -6      /* the handle or server cannot take the request now */
+    RT_EBUSY = -6,     /* the handle or server cannot take the request now */
+    RT_EBOUNDS = -7    /* an index left its buffer (bounds-checked builds only; the access was skipped) */
 } rt_status;
 
 enum { RT_PUMP_SUPERGAUSS = 0, RT_PUMP_UNIFORM = 1, RT_PUMP_ARRAY = 2 };
@@ -436,6 +437,14 @@ rt_status rt_serve_destroy(rt_server *s);
 rt_status rt_step_noalloc(int n, double fresnel, const rt_pump *pump, double g0, double T1, double R,
                           const rt_opts *opts, void *field, void *inversion, long long n_bounces,
                           double *mean_intensity);
+
+/* ---- test hook -----------------------------------------------------------
+ * Fault injection for tests of the out-of-memory paths (not part of the
+ * method): the after-th device allocation the library makes from now on
+ * (0 = the next one) fails once as if the device were out of memory; a
+ * negative value cancels a pending failure.  The failure is produced on the
+ * host before any device call.  Process-wide; returns RT_OK. */
+rt_status rt_debug_fail_alloc(int after);
 
 /* Release every device buffer and graph of the handle (NULL is accepted). */
 rt_status rt_destroy(rt_handle *h);

@@ -80,7 +80,7 @@ cudaError_t slot_alloc(int n, long long hist_cap, bool table, bool rough, SlotBu
     size_t off[kParts], total;
     slot_layout(n, hist_cap, table, rough, off, &total);
     SlotBufs b;
-    cudaError_t e = cudaMalloc(&b.mem, total);
+    cudaError_t e = dev_alloc(&b.mem, total);
     if (e != cudaSuccess) return e;
     b.bytes = total;
     b.E = reinterpret_cast<float2 *>(b.mem + off[0]);
@@ -121,7 +121,8 @@ BatchRes slot_descriptor(const rt_job &job, const SlotBufs &b, SlotCtl *ctl, lon
     g.edge = job.edge_px;
     g.pump_kind = job.pump.kind;
     g.pump_tab = b.pump_tab;
-    g.lens = (!job_rough(job) && (job.z_over_F != 0.0 || job.taper_px > 0)) ? b.lens : nullptr;
+    g.lens = (!job_rough(job) && (job.z_over_F != 0.0 || job.taper_px > 0 || job.relax == RT_RELAX_EXACT)) ? b.lens
+                                                                                                         : nullptr;
     g.phase = job_rough(job) ? b.phase : nullptr;
     g.relax_exact = job.relax == RT_RELAX_EXACT;
     r.pe = pe;
@@ -167,7 +168,7 @@ cudaError_t slot_start(const rt_job &job, const SlotBufs &b, int colC, float2 *c
         if (e == cudaSuccess) e = launch_phase32(n, c, job.edge_px, job.taper_px, psi, b.phase, s);
         cudaFreeAsync(psi, s);
         if (e != cudaSuccess) return e;
-    } else if (job.z_over_F != 0.0 || job.taper_px > 0) {
+    } else if (job.z_over_F != 0.0 || job.taper_px > 0 || job.relax == RT_RELAX_EXACT) {
         if ((e = launch_lens32(n, c, job.edge_px, job.taper_px, b.lens, s)) != cudaSuccess) return e;
     }
     alignas(64) unsigned char map[128];

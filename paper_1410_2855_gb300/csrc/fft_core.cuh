@@ -21,7 +21,28 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+// 1: bounds-checked build.  Every shared-memory access of the line FFT and
+// the sweeps' row, column and item indices are checked; a violation stores
+// RT_EBOUNDS (-7) in the kernel's error word and the access is skipped.
+#ifndef RTK_CHECKED
+#define RTK_CHECKED 0
+#endif
+
 namespace rtk {
+
+constexpr int ERR_BOUNDS = -7;
+
+// Checked builds: record a violation in *err (first writer wins) and report it.
+__device__ __forceinline__ bool check_index(bool ok, int *err)
+{
+#if RTK_CHECKED
+    if (!ok && err) atomicCAS(err, 0, ERR_BOUNDS);
+    return ok;
+#else
+    (void)err;
+    return true;
+#endif
+}
 
 template <typename R> struct cvec;
 template <> struct cvec<float> { using type = float2; };
@@ -162,6 +183,7 @@ template <int CS, typename V> __device__ __forceinline__ V &sm_at(V *line, int i
 template <typename V, bool PP> struct LineBufs {
     V *buf[2];
     int next;
+    int *chk;  // error word of bounds-checked builds (may be null)
     __device__ __forceinline__ V *take()
     {
         V *b = buf[PP ? next : 0];
@@ -169,6 +191,20 @@ template <typename V, bool PP> struct LineBufs {
         return b;
     }
 };
+
+// A shared access at p is element padi(i) * CS of the line at base, 0 <= i < N
+// (checked builds; always true otherwise).
+template <int LOGN, int CS, typename V>
+__device__ __forceinline__ bool sm_in(const V *base, const V *p, int *chk)
+{
+#if RTK_CHECKED
+    const long long off = (long long)(p - base);
+    return check_index(off >= 0 && off % CS == 0 && off / CS <= padi((1 << LOGN) - 1), chk);
+#else
+    (void)base, (void)p, (void)chk;
+    return true;
+#endif
+}
 
 // One Stockham FFT of a line.  On entry v[s] = x[t + T s]; on exit
 // v[s] = X[t + T s], X[k] = sum_j x[j] exp(DIR 2 pi i jk / N) (unnormalised).
@@ -195,20 +231,26 @@ __device__ __forceinline__ void fft_line(V (&v)[16], const int t, LineBufs<V, PP
         if (NsPrev == 1) {
             V *w = line + 17 * t * CS;
 #pragma unroll
-            for (int r = 0; r < 16; ++r) w[r * CS] = v[r];
+            for (int r = 0; r < 16; ++r)
+                if (sm_in<LOGN, CS>(line, &w[r * CS], lb.chk)) w[r * CS] = v[r];
         } else {
             const int idxD = (t / NsPrev) * NsPrev * 16 + (t % NsPrev);
             V *w = line + padi(idxD) * CS;
 #pragma unroll
-            for (int r = 0; r < 16; ++r) w[r * (17 * NsPrev / 16) * CS] = v[r];
+            for (int r = 0; r < 16; ++r)
+                if (sm_in<LOGN, CS>(line, &w[r * (17 * NsPrev / 16) * CS], lb.chk))
+                    w[r * (17 * NsPrev / 16) * CS] = v[r];
         }
         sync();
         if constexpr (T16) {
 #pragma unroll
-            for (int r = 0; r < 16; ++r) v[r] = rd_base[r * (17 * T / 16) * CS];
+            for (int r = 0; r < 16; ++r)
+                if (sm_in<LOGN, CS>(line, &rd_base[r * (17 * T / 16) * CS], lb.chk))
+                    v[r] = rd_base[r * (17 * T / 16) * CS];
         } else {
 #pragma unroll
-            for (int r = 0; r < 16; ++r) v[r] = sm_at<CS>(line, t + r * T);
+            for (int r = 0; r < 16; ++r)
+                if (sm_in<LOGN, CS>(line, &sm_at<CS>(line, t + r * T), lb.chk)) v[r] = sm_at<CS>(line, t + r * T);
         }
         const V *twp = tw + off + (t & (Ns - 1));
 #pragma unroll
@@ -225,12 +267,15 @@ __device__ __forceinline__ void fft_line(V (&v)[16], const int t, LineBufs<V, PP
         if constexpr (NsPrev == 1) {
             V *w = line + 17 * t * CS;
 #pragma unroll
-            for (int r = 0; r < 16; ++r) w[r * CS] = v[r];
+            for (int r = 0; r < 16; ++r)
+                if (sm_in<LOGN, CS>(line, &w[r * CS], lb.chk)) w[r * CS] = v[r];
         } else {
             const int idxD = (t / NsPrev) * NsPrev * 16 + (t % NsPrev);
             V *w = line + padi(idxD) * CS;
 #pragma unroll
-            for (int r = 0; r < 16; ++r) w[r * (17 * NsPrev / 16) * CS] = v[r];
+            for (int r = 0; r < 16; ++r)
+                if (sm_in<LOGN, CS>(line, &w[r * (17 * NsPrev / 16) * CS], lb.chk))
+                    w[r * (17 * NsPrev / 16) * CS] = v[r];
         }
         sync();
 #pragma unroll
@@ -239,7 +284,9 @@ __device__ __forceinline__ void fft_line(V (&v)[16], const int t, LineBufs<V, PP
             V *rb = T16 ? rd_base + i * (17 * T / 16) * CS : line + padi(j) * CS;
             V u[RL];
 #pragma unroll
-            for (int r = 0; r < RL; ++r) u[r] = rb[r * (17 * NsL / 16) * CS];
+            for (int r = 0; r < RL; ++r)
+                u[r] = sm_in<LOGN, CS>(line, &rb[r * (17 * NsL / 16) * CS], lb.chk) ? rb[r * (17 * NsL / 16) * CS]
+                                                                                   : v[i];
             const V *twp = tw + off + j;
 #pragma unroll
             for (int r = 1; r < RL; ++r) u[r] = twmul<DIR, TWS>(u[r], twp, (r - 1) * NsL);

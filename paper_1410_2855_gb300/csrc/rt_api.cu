@@ -10,6 +10,7 @@
 
 #include "rt.h"
 #include "rt_internal.h"
+#include "trace.h"
 
 // 1: FP32 handles with the order-10 super-Gaussian pump read N0 from a table
 // staged with each row (4 more bytes per point, no exp per point).
@@ -80,6 +81,7 @@ struct rt_handle {
     void *pump_tab = nullptr;     // N0 table (array pump, FP32 path)
     void *lens = nullptr;         // per-axis curved-mirror factors (no roughness)
     void *phase = nullptr;        // n*n aperture factors (roughness, with the lens folded in)
+    void *ones = nullptr;         // n unit factors: the slices before the last under the exact inversion update
     double *profile = nullptr;    // device copy of the array pump profile
     void *X = nullptr, *S = nullptr;  // spectrum scratch (lazily allocated)
     void *hz = nullptr;               // propagator of the last intracavity readout distance (lazily allocated)
@@ -138,9 +140,9 @@ GainParams<R> gain_params(rt_handle *h, bool last = true)
     g.pump_kind = h->pump.kind;
     g.pump_tab = reinterpret_cast<const R *>(h->pump_tab);
     using C = typename cplx_of<R>::type;
-    g.lens = last ? static_cast<const C *>(h->lens) : nullptr;
-    g.phase = last ? static_cast<const C *>(h->phase) : nullptr;
     g.relax_exact = h->opts.relax == RT_RELAX_EXACT;
+    g.lens = last ? static_cast<const C *>(h->lens) : (g.relax_exact ? static_cast<const C *>(h->ones) : nullptr);
+    g.phase = last ? static_cast<const C *>(h->phase) : nullptr;
     return g;
 }
 
@@ -182,10 +184,11 @@ cudaError_t get_graph(rt_handle *h, long long k, cudaGraphExec_t *out)
         *out = it->second;
         return cudaSuccess;
     }
-    const bool exact = h->opts.relax == RT_RELAX_EXACT;
-    cudaError_t e = h->precision == RT_FP32 ? prepare_bounce32(h->logn, h->colC, h->pe, h->lens || h->phase || exact)
-                                            : prepare_bounce64(h->logn);
-    if (e == cudaSuccess && h->precision == RT_FP32 && h->slices > 1) e = prepare_row32(h->logn, h->pe, exact);
+    cudaError_t e = h->precision == RT_FP32
+                        ? prepare_bounce32(h->logn, h->colC, h->pe, feature_form(gain_params<float>(h, true)))
+                        : prepare_bounce64(h->logn);
+    if (e == cudaSuccess && h->precision == RT_FP32 && h->slices > 1)
+        e = prepare_row32(h->logn, h->pe, feature_form(gain_params<float>(h, false)));
     if (e != cudaSuccess) return e;
     e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
@@ -222,7 +225,7 @@ void release(rt_handle *h)
 {
     for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
-    void *bufs[] = {h->E, h->N, h->tw, h->h, h->pump_tab, h->lens, h->phase, h->profile, h->X, h->S, h->hz,
+    void *bufs[] = {h->E, h->N, h->tw, h->h, h->pump_tab, h->lens, h->phase, h->ones, h->profile, h->X, h->S, h->hz,
                     h->part, h->peak_val, h->peak_idx, h->hist, h->ctl, h->slice_ctl};
     for (void *p : bufs)
         if (p) cudaFree(p);
@@ -231,10 +234,10 @@ void release(rt_handle *h)
 
 rt_status ensure_spectrum_scratch(rt_handle *h)
 {
-    if (!h->X) RT_TRY(cudaMalloc(&h->X, h->points() * h->esz()));
-    if (!h->S) RT_TRY(cudaMalloc(&h->S, h->points() * h->rsz()));
-    if (!h->peak_val) RT_TRY(cudaMalloc(&h->peak_val, sizeof(double) * kMaxPart));
-    if (!h->peak_idx) RT_TRY(cudaMalloc(&h->peak_idx, sizeof(long long) * kMaxPart));
+    if (!h->X) RT_TRY(dev_alloc(&h->X, h->points() * h->esz()));
+    if (!h->S) RT_TRY(dev_alloc(&h->S, h->points() * h->rsz()));
+    if (!h->peak_val) RT_TRY(dev_alloc(&h->peak_val, sizeof(double) * kMaxPart));
+    if (!h->peak_idx) RT_TRY(dev_alloc(&h->peak_idx, sizeof(long long) * kMaxPart));
     return RT_OK;
 }
 
@@ -275,6 +278,7 @@ const char *rt_status_string(rt_status s)
     case RT_ENUMERIC: return "non-finite field intensity";
     case RT_ETIMEOUT: return "bounded wait timed out";
     case RT_EBUSY: return "busy";
+    case RT_EBOUNDS: return "index out of bounds (checked build)";
     default: return "unknown status";
     }
 }
@@ -320,6 +324,7 @@ rt_status rt_create(int n, double fresnel, const rt_pump *pump, double g0, doubl
     if (p.kind == RT_PUMP_ARRAY && !p.profile) return RT_EINVAL;
     if (p.kind < RT_PUMP_SUPERGAUSS || p.kind > RT_PUMP_ARRAY) return RT_EINVAL;
 
+    TraceRange tr("rt_create");
     rt_handle *h = new (std::nothrow) rt_handle();
     if (!h) return RT_ENOMEM;
     h->n = n;
@@ -358,31 +363,32 @@ rt_status rt_create(int n, double fresnel, const rt_pump *pump, double g0, doubl
 
     const size_t P = h->points();
     RT_CREATE_TRY(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
-    RT_CREATE_TRY(cudaMalloc(&h->E, P * h->esz()));
-    RT_CREATE_TRY(cudaMalloc(&h->N, h->inv_points() * h->rsz()));
-    RT_CREATE_TRY(cudaMalloc(&h->tw, (size_t)(twiddle_entries(h->logn) + 1) * h->esz()));
-    RT_CREATE_TRY(cudaMalloc(&h->h, (size_t)n * h->esz()));
-    RT_CREATE_TRY(cudaMalloc(&h->part, sizeof(double) * kMaxPart));
-    RT_CREATE_TRY(cudaMalloc(reinterpret_cast<void **>(&h->ctl), sizeof(Ctl)));
+    RT_CREATE_TRY(dev_alloc(&h->E, P * h->esz()));
+    RT_CREATE_TRY(dev_alloc(&h->N, h->inv_points() * h->rsz()));
+    RT_CREATE_TRY(dev_alloc(&h->tw, (size_t)(twiddle_entries(h->logn) + 1) * h->esz()));
+    RT_CREATE_TRY(dev_alloc(&h->h, (size_t)n * h->esz()));
+    RT_CREATE_TRY(dev_alloc(&h->part, sizeof(double) * kMaxPart));
+    RT_CREATE_TRY(dev_alloc(reinterpret_cast<void **>(&h->ctl), sizeof(Ctl)));
     RT_CREATE_TRY(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->stream));
     if (h->slices > 1) {
-        RT_CREATE_TRY(cudaMalloc(reinterpret_cast<void **>(&h->slice_ctl), sizeof(Ctl)));
+        RT_CREATE_TRY(dev_alloc(reinterpret_cast<void **>(&h->slice_ctl), sizeof(Ctl)));
         RT_CREATE_TRY(cudaMemsetAsync(h->slice_ctl, 0, sizeof(Ctl), h->stream));
     }
-    if (o.history_cap > 0) RT_CREATE_TRY(cudaMalloc(&h->hist, sizeof(double) * (size_t)o.history_cap));
+    if (o.history_cap > 0) RT_CREATE_TRY(dev_alloc(&h->hist, sizeof(double) * (size_t)o.history_cap));
     if (p.kind == RT_PUMP_ARRAY) {
-        RT_CREATE_TRY(cudaMalloc(&h->profile, sizeof(double) * P));
+        RT_CREATE_TRY(dev_alloc(&h->profile, sizeof(double) * P));
         RT_CREATE_TRY(cudaMemcpyAsync(h->profile, p.profile, sizeof(double) * P, cudaMemcpyDefault, h->stream));
     }
     // Complex aperture beyond the hard edge: a full table when the mirror is
     // rough (lens and taper folded in), else per-axis factors when it is
-    // curved or the edge tapered, else nothing.
+    // curved or the edge tapered or the general local map is needed anyway
+    // (exact inversion update), else nothing.
     const double c = lens_curvature(h->alpha, o.z_over_F);
     const double g0s = g0 / h->slices;   // pump of one slice: N0/m
     double *psi = nullptr;
     if (o.roughness) {
-        RT_CREATE_TRY(cudaMalloc(&h->phase, P * h->esz()));
-        RT_CREATE_TRY(cudaMalloc(&psi, sizeof(double) * P));
+        RT_CREATE_TRY(dev_alloc(&h->phase, P * h->esz()));
+        RT_CREATE_TRY(dev_alloc(&psi, sizeof(double) * P));
         cudaError_t e = cudaMemcpyAsync(psi, o.roughness, sizeof(double) * P, cudaMemcpyDefault, h->stream);
         if (e == cudaSuccess)
             e = h->precision == RT_FP32
@@ -391,8 +397,8 @@ rt_status rt_create(int n, double fresnel, const rt_pump *pump, double g0, doubl
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         cudaFree(psi);
         RT_CREATE_TRY(e);
-    } else if (o.z_over_F != 0.0 || o.taper_px > 0) {
-        RT_CREATE_TRY(cudaMalloc(&h->lens, (size_t)n * h->esz()));
+    } else if (o.z_over_F != 0.0 || o.taper_px > 0 || o.relax == RT_RELAX_EXACT) {
+        RT_CREATE_TRY(dev_alloc(&h->lens, (size_t)n * h->esz()));
         RT_CREATE_TRY(h->precision == RT_FP32
                           ? launch_lens32(n, c, o.edge_px, o.taper_px, static_cast<float2 *>(h->lens), h->stream)
                           : launch_lens64(n, c, o.edge_px, o.taper_px, static_cast<double2 *>(h->lens), h->stream));
@@ -405,7 +411,7 @@ rt_status rt_create(int n, double fresnel, const rt_pump *pump, double g0, doubl
         RT_CREATE_TRY(launch_noise32(n, o.seed, o.noise_amp, static_cast<float2 *>(h->E), h->stream));
         RT_CREATE_TRY(launch_pump32(n, p.kind, g0s, p.order, p.radius, h->profile, static_cast<float *>(h->N), h->stream));
         if (h->pe == 2) {
-            RT_CREATE_TRY(cudaMalloc(&h->pump_tab, sizeof(float) * P));
+            RT_CREATE_TRY(dev_alloc(&h->pump_tab, sizeof(float) * P));
             RT_CREATE_TRY(cudaMemcpyAsync(h->pump_tab, h->N, sizeof(float) * P, cudaMemcpyDeviceToDevice, h->stream));
         }
     } else {
@@ -414,9 +420,14 @@ rt_status rt_create(int n, double fresnel, const rt_pump *pump, double g0, doubl
         RT_CREATE_TRY(launch_noise64(n, o.seed, o.noise_amp, static_cast<double2 *>(h->E), h->stream));
         RT_CREATE_TRY(launch_pump64(n, p.kind, g0s, p.order, p.radius, h->profile, static_cast<double *>(h->N), h->stream));
         if (h->pe == 2) {
-            RT_CREATE_TRY(cudaMalloc(&h->pump_tab, sizeof(double) * P));
+            RT_CREATE_TRY(dev_alloc(&h->pump_tab, sizeof(double) * P));
             RT_CREATE_TRY(cudaMemcpyAsync(h->pump_tab, h->N, sizeof(double) * P, cudaMemcpyDeviceToDevice, h->stream));
         }
+    }
+    if (h->slices > 1 && o.relax == RT_RELAX_EXACT) {
+        RT_CREATE_TRY(dev_alloc(&h->ones, (size_t)n * h->esz()));
+        RT_CREATE_TRY(h->precision == RT_FP32 ? launch_lens32(n, 0.0, 0, 0, static_cast<float2 *>(h->ones), h->stream)
+                                              : launch_lens64(n, 0.0, 0, 0, static_cast<double2 *>(h->ones), h->stream));
     }
     // every slice starts fully pumped: N0/m
     for (int k = 1; k < h->slices; ++k)
@@ -432,6 +443,7 @@ rt_status rt_step(rt_handle *h, long long nb)
 {
     if (!h || nb < 0) return RT_EINVAL;
     if (nb == 0) return RT_OK;
+    TraceRange tr("rt_step");
     DeviceGuard dg(h->device);
     const long long K = h->opts.chunk;
     long long left = nb;
@@ -449,6 +461,7 @@ rt_status rt_sweep(rt_handle *h, int which)
 {
     if (!h || h->precision != RT_FP32 || h->slices > 1 || (which != RT_SWEEP_COLUMNS && which != RT_SWEEP_ROWS))
         return RT_EINVAL;
+    TraceRange tr(which == RT_SWEEP_COLUMNS ? "rt_sweep columns" : "rt_sweep rows");
     DeviceGuard dg(h->device);
     float2 *E = static_cast<float2 *>(h->E);
     const float2 *tw = static_cast<const float2 *>(h->tw), *hh = static_cast<const float2 *>(h->h);
@@ -603,7 +616,7 @@ rt_status rt_read_field_at(rt_handle *h, double zeta, void *dst, size_t bytes)
     DeviceGuard dg(h->device);
     rt_status st = ensure_spectrum_scratch(h);
     if (st != RT_OK) return st;
-    if (!h->hz) RT_TRY(cudaMalloc(&h->hz, (size_t)h->n * h->esz()));
+    if (!h->hz) RT_TRY(dev_alloc(&h->hz, (size_t)h->n * h->esz()));
     const double a = h->alpha * zeta;
     if (h->precision == RT_FP32) {
         const float2 *tw = static_cast<const float2 *>(h->tw);

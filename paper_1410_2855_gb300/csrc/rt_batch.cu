@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "engine.h"
+#include "trace.h"
 
 using namespace rtk;
 
@@ -201,14 +202,14 @@ rt_status rt_batch_create(const rt_job *jobs, int count, const rt_opts *opts, rt
         b->classes[s.cls].slots.push_back(i);
     }
     if (cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess) return fail(RT_ECUDA);
-    if (cudaMalloc(&b->ctl, sizeof(SlotCtl) * count) != cudaSuccess) return fail(RT_ENOMEM);
-    if (cudaMalloc(&b->err, sizeof(int)) != cudaSuccess) return fail(RT_ENOMEM);
+    if (dev_alloc(&b->ctl, sizeof(SlotCtl) * count) != cudaSuccess) return fail(RT_ENOMEM);
+    if (dev_alloc(&b->err, sizeof(int)) != cudaSuccess) return fail(RT_ENOMEM);
     if (cudaMemsetAsync(b->err, 0, sizeof(int), b->stream) != cudaSuccess) return fail(RT_ECUDA);
     b->shared_bytes = sizeof(SlotCtl) * count + sizeof(int);
     for (SizeClass &c : b->classes) {
         const size_t twb = sizeof(float2) * (twiddle_entries(c.logn) + 1);
-        if (cudaMalloc(&c.d_res, sizeof(BatchRes) * c.slots.size()) != cudaSuccess) return fail(RT_ENOMEM);
-        if (cudaMalloc(&c.tw, twb) != cudaSuccess) return fail(RT_ENOMEM);
+        if (dev_alloc(&c.d_res, sizeof(BatchRes) * c.slots.size()) != cudaSuccess) return fail(RT_ENOMEM);
+        if (dev_alloc(&c.tw, twb) != cudaSuccess) return fail(RT_ENOMEM);
         b->shared_bytes += sizeof(BatchRes) * c.slots.size() + twb;
     }
     for (int i = 0; i < count; ++i) {
@@ -226,6 +227,7 @@ rt_status rt_batch_step(rt_batch *b, long long nb)
 {
     if (!b || nb < 0) return RT_EINVAL;
     if (nb == 0) return RT_OK;
+    TraceRange tr("rt_batch_step");
     DeviceGuard g(b->device);
     const long long K = b->opts.chunk;
     long long left = nb;

@@ -8,6 +8,14 @@
 
 namespace rtk {
 
+// Device allocation used by the whole library (cudaMalloc), with the
+// fault-injection hook behind rt_debug_fail_alloc.
+cudaError_t dev_alloc(void **p, size_t bytes);
+template <typename T> inline cudaError_t dev_alloc(T **p, size_t bytes)
+{
+    return dev_alloc(reinterpret_cast<void **>(p), bytes);
+}
+
 enum PumpKind { PUMP_SUPERGAUSS = 0, PUMP_UNIFORM = 1, PUMP_ARRAY = 2 };
 
 // Pump evaluation inside the FP32 row sweep: super-Gaussian of order 10
@@ -94,15 +102,15 @@ cudaError_t make_col_tensor_map(void *map, float2 *E, int n, int colC);
 // (gain, mirror phase, edge, inversion update) and the mean-intensity
 // reduction.  pe selects how N0 is evaluated: 0 super-Gaussian of order 10
 // on the fly, 1 uniform, 2 from GainParams::pump_tab.  The general form of
-// the kernel (aperture table, exact relaxation) runs when needs_general(g).
+// the kernel (aperture table, exact relaxation) runs as feature_form(g) says.
 cudaError_t launch_row_diffract_gain32(int logn, int pe, float2 *E, float *N, const float2 *tw, const float2 *h,
                                        const GainParams<float> &g, const StatParams &st, cudaStream_t s);
 int row_blocks32(int logn);            // most blocks of a row sweep (size of StatParams::part)
 // Set kernel attributes (shared-memory opt-in) of a bounce's kernels on the
 // current device; done before capturing a bounce into a CUDA graph.
-// ap: the row sweep applies an aperture phase.
-cudaError_t prepare_bounce32(int logn, int colC, int pe, bool ap);
-cudaError_t prepare_row32(int logn, int pe, bool ap);
+// feat: the FeatureForm of the row sweep's local map.
+cudaError_t prepare_bounce32(int logn, int colC, int pe, int feat);
+cudaError_t prepare_row32(int logn, int pe, int feat);
 cudaError_t prepare_col32(int logn, int colC);
 cudaError_t prepare_bounce64(int logn);
 int col_tile_ok32(int logn, int colC); // 1 if that column tile width is instantiated and fits
@@ -157,11 +165,14 @@ cudaError_t launch_phase32(int n, double c, int edge, int taper, const double *p
 cudaError_t launch_phase64(int n, double c, int edge, int taper, const double *psi, double2 *phase,
                            cudaStream_t s);
 
-// The row sweep needs its general form: an aperture table or the exact
-// inversion update.
-template <typename R> __host__ __device__ inline bool needs_general(const GainParams<R> &g)
+// Forms of the row sweep's local map: the plain form (flat, hard-edged
+// mirror, Euler inversion step) and the general forms, which multiply by an
+// aperture table (g.phase, else g.lens, which must then be set; a table of
+// ones serves a flat mirror) with the Euler or the exact inversion update.
+enum FeatureForm { FEAT_PLAIN = 0, FEAT_TABLE = 1, FEAT_TABLE_EXACT = 2 };
+template <typename R> __host__ __device__ inline int feature_form(const GainParams<R> &g)
 {
-    return g.lens || g.phase || g.relax_exact;
+    return g.relax_exact ? FEAT_TABLE_EXACT : ((g.lens || g.phase) ? FEAT_TABLE : FEAT_PLAIN);
 }
 // Structured starting field (rt_set_field_pattern), FP64 arithmetic.
 cudaError_t launch_pattern32(int n, int kind, int q, int alt, double w, double env, double curv, double amp,

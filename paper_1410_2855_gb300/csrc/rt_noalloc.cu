@@ -119,7 +119,8 @@ extern "C" rt_status rt_step_noalloc(int n, double fresnel, const rt_pump *pump,
     // The array keeps whatever the previous call left: the counters must start at zero.
     if (cudaMemsetAsync(ctl, 0, sizeof(NoAllocCtl), s) != cudaSuccess) return RT_ECUDA;
     if (rtk::launch_tables32(n, alpha, tw, h, s) != cudaSuccess) return RT_ECUDA;
-    const bool curved = o.z_over_F != 0.0 || o.taper_px > 0;
+    // per-axis aperture factors: curved mirror, taper, or the general local map (exact update)
+    const bool curved = o.z_over_F != 0.0 || o.taper_px > 0 || o.relax == RT_RELAX_EXACT;
     if (curved &&
         rtk::launch_lens32(n, rtk::lens_curvature(alpha, o.z_over_F), o.edge_px, o.taper_px, lens, s) != cudaSuccess)
         return RT_ECUDA;

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "engine.h"
+#include "trace.h"
 
 using namespace rtk;
 
@@ -91,11 +92,19 @@ cudaError_t class_init(rt_server *s, SClass &c, int logn)
     c.logn = logn;
     c.colC = default_col_tile32(logn);
     const int cap = s->opts.max_per_size;
-    cudaError_t e;
-    if ((e = cudaMalloc(&c.d_res, sizeof(BatchRes) * cap)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&c.ctl, sizeof(SlotCtl) * cap)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&c.tw, sizeof(float2) * (twiddle_entries(logn) + 1))) != cudaSuccess) return e;
-    return prepare_batch32(logn, c.colC);
+    cudaError_t e = dev_alloc(&c.d_res, sizeof(BatchRes) * cap);
+    if (e == cudaSuccess) e = dev_alloc(&c.ctl, sizeof(SlotCtl) * cap);
+    if (e == cudaSuccess) e = dev_alloc(&c.tw, sizeof(float2) * (twiddle_entries(logn) + 1));
+    if (e == cudaSuccess) e = prepare_batch32(logn, c.colC);
+    if (e != cudaSuccess) {  // the class is dropped: release what it holds
+        if (c.d_res) cudaFree(c.d_res);
+        if (c.ctl) cudaFree(c.ctl);
+        if (c.tw) cudaFree(c.tw);
+        c.d_res = nullptr;
+        c.ctl = nullptr;
+        c.tw = nullptr;
+    }
+    return e;
 }
 
 // Release idle slots of other sizes (largest first) until `need` more bytes fit.
@@ -207,6 +216,7 @@ void post(rt_server *s, const SSlot &sl, int status, long long bounces, double m
 // One scheduling round: launch, wait, retire.  Returns false on a CUDA failure.
 bool run_round(rt_server *s)
 {
+    TraceRange tr("serve round");
     const double t_start = s->now();
     cudaGraphExec_t ge;
     cudaError_t e = round_graph(s, &ge);
@@ -349,7 +359,7 @@ rt_status rt_serve_create(const rt_serve_opts *opts, rt_server **out)
         s->own_stream = true;
     }
     if (cudaStreamCreateWithFlags(&s->capture, cudaStreamNonBlocking) != cudaSuccess) return fail(RT_ECUDA);
-    if (cudaMalloc(&s->d_err, sizeof(int)) != cudaSuccess) return fail(RT_ENOMEM);
+    if (dev_alloc(&s->d_err, sizeof(int)) != cudaSuccess) return fail(RT_ENOMEM);
     if (cudaMemset(s->d_err, 0, sizeof(int)) != cudaSuccess) return fail(RT_ECUDA);
     s->worker = std::thread(worker_main, s);
     *out = s;

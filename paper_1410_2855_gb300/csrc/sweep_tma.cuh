@@ -124,14 +124,33 @@ __device__ __forceinline__ void init_stage_barriers(uint64_t *bar)
     __syncthreads();
 }
 
+// Complex product with every rounding spelled out, so that the general local
+// map gives the same bits wherever it is inlined (handle and batched sweeps).
+__device__ __forceinline__ float2 cmul_rn(float2 a, float2 b)
+{
+    return make_float2(__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)), __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
+}
+
+// Order-10 super-Gaussian pump g0 exp(-q^5), q = (x^2 + y^2) / r_p^2, with
+// yq = y^2 / r_p^2 precomputed per row; roundings spelled out as above (the
+// general forms; the plain form leaves contraction to the compiler, which
+// is the faster code and is only ever compared with itself).
+__device__ __forceinline__ float sg10_pump(float g0, float xc, float yq, float inv_rp2)
+{
+    const float q = __fmaf_rn(__fmul_rn(xc, xc), inv_rp2, yq);
+    const float q2 = __fmul_rn(q, q);
+    return __fmul_rn(g0, fexp(-__fmul_rn(__fmul_rn(q2, q2), q)));
+}
+
 // Local map of one row held in registers (slot s = column t + T s):
 // gain against the frozen inversion, mirror, absorbing edge, inversion
-// relaxation.  The general form (AP) also applies the complex aperture D
-// (smooth taper, curved mirror, roughness) from g.phase when set, else from
-// the separable g.lens when set, and takes the exact inversion update when
-// g.relax_exact is set.  PE_RUNTIME takes the pump evaluation from pe_rt.
-// Returns sum |E_new|^2 over the thread's 16 elements.
-template <int LOGN, int PE, bool STAGED_N0 = false, bool AP = false>
+// relaxation.  The general forms also apply the complex aperture D (smooth
+// taper, curved mirror, roughness) from g.phase when set, else from the
+// separable g.lens (one of them must be set): FEAT_TABLE with the Euler
+// inversion step, FEAT_TABLE_EXACT with the exact one.  PE_RUNTIME takes the
+// pump evaluation from pe_rt.  Returns sum |E_new|^2 over the thread's 16
+// elements.
+template <int LOGN, int PE, bool STAGED_N0 = false, int FEAT = FEAT_PLAIN>
 __device__ __forceinline__ float row_local_map(float2 (&v)[16], int t, int row, const float *nrow, float2 *erow,
                                                float *ngl, const GainParams<float> &g, const float *n0row = nullptr,
                                                int pe_rt = PE_SG10)
@@ -140,15 +159,15 @@ __device__ __forceinline__ float row_local_map(float2 (&v)[16], int t, int row, 
     const float step = 2.0f / (float)N;
     const float xc0 = (float)(t - N / 2) * step;
     const float yc = (float)(row - N / 2) * step;
-    const float yq = yc * yc * g.inv_rp2;
+    const float yq = FEAT != FEAT_PLAIN ? __fmul_rn(__fmul_rn(yc, yc), g.inv_rp2) : yc * yc * g.inv_rp2;
     const bool row_in = row >= g.edge && row < N - g.edge;
     // Aperture factor of element x: drow * dtab[x] (sqrtR folded into drow).
     const float2 *dtab = nullptr;
     float2 drow = make_float2(g.sqrtR, 0.0f);
-    if constexpr (AP) {
+    if constexpr (FEAT != FEAT_PLAIN) {
         if (g.phase) {
             dtab = g.phase + (size_t)row * N + t;
-        } else if (g.lens) {
+        } else {
             dtab = g.lens + t;
             drow = cscale(__ldg(g.lens + row), g.sqrtR);
         }
@@ -159,11 +178,12 @@ __device__ __forceinline__ float row_local_map(float2 (&v)[16], int t, int row, 
         const int x = t + si * T;
         const float nn = nrow[si * T];
         float2 e = v[si];
-        const float inten = e.x * e.x + e.y * e.y;
+        const float inten = FEAT != FEAT_PLAIN ? __fmaf_rn(e.x, e.x, __fmul_rn(e.y, e.y)) : e.x * e.x + e.y * e.y;
         const bool inside = row_in && x >= g.edge && x < N - g.edge;
-        if constexpr (AP) {
-            const float2 d = dtab ? cmul(drow, __ldg(dtab + si * T)) : drow;
-            e = cscale(cmul(e, d), inside ? fexp(0.5f * nn) : 0.0f);
+        if constexpr (FEAT != FEAT_PLAIN) {
+            const float gain = inside ? fexp(__fmul_rn(0.5f, nn)) : 0.0f;
+            e = cmul_rn(e, cmul_rn(drow, __ldg(dtab + si * T)));
+            e = make_float2(__fmul_rn(e.x, gain), __fmul_rn(e.y, gain));
         } else {
             e = cscale(e, inside ? g.sqrtR * fexp(0.5f * nn) : 0.0f);
         }
@@ -174,10 +194,7 @@ __device__ __forceinline__ float row_local_map(float2 (&v)[16], int t, int row, 
             } else if (pe_rt == PE_TABLE) {
                 n0 = __ldg(g.pump_tab + (size_t)row * N + x);
             } else {
-                const float xc = xc0 + (float)(si * T) * step;
-                const float q = xc * xc * g.inv_rp2 + yq;
-                const float q2 = q * q;
-                n0 = g.g0 * fexp(-(q2 * q2 * q));
+                n0 = sg10_pump(g.g0, __fmaf_rn((float)(si * T), step, xc0), yq, g.inv_rp2);
             }
         } else if constexpr (PE == PE_UNIFORM) {
             n0 = g.g0;
@@ -185,25 +202,27 @@ __device__ __forceinline__ float row_local_map(float2 (&v)[16], int t, int row, 
             n0 = n0row[si * T];
         } else if constexpr (PE == PE_TABLE) {
             n0 = __ldg(g.pump_tab + (size_t)row * N + x);
+        } else if constexpr (FEAT != FEAT_PLAIN) {
+            n0 = sg10_pump(g.g0, __fmaf_rn((float)(si * T), step, xc0), yq, g.inv_rp2);
         } else {
             const float xc = xc0 + (float)(si * T) * step;
             const float q = xc * xc * g.inv_rp2 + yq;
             const float q2 = q * q;
             n0 = g.g0 * fexp(-(q2 * q2 * q));
         }
-        if constexpr (AP) {
-            const float a = 1.0f + inten * g.invIsat;
-            if (g.relax_exact) {
-                const float nss = n0 / a;
-                ngl[si * T] = nss + (nn - nss) * fexp(-a * g.invT1);
-            } else {
-                ngl[si * T] = nn + (n0 - nn * a) * g.invT1;
-            }
+        if constexpr (FEAT == FEAT_TABLE_EXACT) {
+            const float a = __fmaf_rn(inten, g.invIsat, 1.0f);
+            const float nss = __fdiv_rn(n0, a);
+            ngl[si * T] = __fmaf_rn(__fsub_rn(nn, nss), fexp(-__fmul_rn(a, g.invT1)), nss);
+        } else if constexpr (FEAT == FEAT_TABLE) {
+            const float a = __fmaf_rn(inten, g.invIsat, 1.0f);
+            ngl[si * T] = __fmaf_rn(__fmaf_rn(-nn, a, n0), g.invT1, nn);
         } else {
             ngl[si * T] = nn + (n0 - nn * (1.0f + inten * g.invIsat)) * g.invT1;
         }
         erow[si * T] = e;
-        acc += e.x * e.x + e.y * e.y;
+        if constexpr (FEAT != FEAT_PLAIN) acc = __fmaf_rn(e.x, e.x, __fmaf_rn(e.y, e.y, acc));
+        else acc += e.x * e.x + e.y * e.y;
     }
     return acc;
 }
@@ -273,7 +292,7 @@ __device__ __forceinline__ void res_finish(double v, const StatParams &st, int k
 
 // Row sweep: LPC rows per group, T = n/16 threads per row.  With a pump
 // table (PE_TABLE) the rows' N0 values are staged by the copy engine too.
-template <int LOGN, int LPC, int PE, bool AP = false, bool PP = RTK_ROW_PP>
+template <int LOGN, int LPC, int PE, int FEAT = FEAT_PLAIN, bool PP = RTK_ROW_PP>
 __global__ void __launch_bounds__(LPC * Plan<LOGN>::T, smem_blocks(RowStage<LOGN, LPC, PP, PE == PE_TABLE>::total))
 k_row_tma(float2 *E, float *Nv, const float2 *__restrict__ tw, const float2 *__restrict__ h, GainParams<float> g,
           StatParams st, int ngroups)
@@ -321,9 +340,9 @@ k_row_tma(float2 *E, float *Nv, const float2 *__restrict__ tw, const float2 *__r
         // With ping-pong the first exchange goes to the extra buffer, so the
         // dense stage is only overwritten after every thread has read it.
         float2 *extra = reinterpret_cast<float2 *>(sm + 128 + 2 * L::stage) + lig * LS;
-        LineBufs<float2, PP> lb{{PP ? extra : line, line}, 0};
+        LineBufs<float2, PP> lb{{PP ? extra : line, line}, 0, st.err};
         diffract_line<LOGN, 1>(v, t, lb, tw, h, sync);
-        dacc += (double)row_local_map<LOGN, PE, TAB, AP>(v, t, row, stage_n(s) + lig * N + t, E + (size_t)row * N + t,
+        dacc += (double)row_local_map<LOGN, PE, TAB, FEAT>(v, t, row, stage_n(s) + lig * N + t, E + (size_t)row * N + t,
                                                      Nv + (size_t)row * N + t, g, stage_t(s) + lig * N + t);
         __syncthreads();  // stage s fully consumed before it is refilled
     }
@@ -367,7 +386,7 @@ k_col_tma(float2 *E, const float2 *__restrict__ tw, const float2 *__restrict__ h
         float2 v[16];
 #pragma unroll
         for (int si = 0; si < 16; ++si) v[si] = base[(t + si * T) * C + c];
-        LineBufs<float2, PP> lb{{PP ? stage(2) + c : base + c, base + c}, 0};
+        LineBufs<float2, PP> lb{{PP ? stage(2) + c : base + c, base + c}, 0, err};
         diffract_line<LOGN, C>(v, t, lb, tw, h, sync);
         float2 *col = E + (size_t)t * N + tile * C + c;
 #pragma unroll
@@ -436,15 +455,18 @@ k_row_tma_batch(const BatchRes *__restrict__ res, int nres, const float2 *__rest
 #pragma unroll
         for (int si = 0; si < 16; ++si) v[si] = line[t + si * T];
         float2 *extra = reinterpret_cast<float2 *>(sm + 128 + 2 * L::stage) + lig * LS;
-        LineBufs<float2, PP> lb{{PP ? extra : line, line}, 0};
+        LineBufs<float2, PP> lb{{PP ? extra : line, line}, 0, err};
         diffract_line<LOGN, 1>(v, t, lb, tw, R.h, sync);
         const GainParams<float> g = R.g;
         const float *nrow = stage_n(s) + lig * N + t;
         float2 *erow = R.E + (size_t)row * N + t;
         float *ngl = R.N + (size_t)row * N + t;
         float acc;
-        if (needs_general(g)) {
-            acc = row_local_map<LOGN, PE_RUNTIME, false, true>(v, t, row, nrow, erow, ngl, g, nullptr, R.pe);
+        const int feat = feature_form(g);
+        if (feat == FEAT_TABLE_EXACT) {
+            acc = row_local_map<LOGN, PE_RUNTIME, false, FEAT_TABLE_EXACT>(v, t, row, nrow, erow, ngl, g, nullptr, R.pe);
+        } else if (feat == FEAT_TABLE) {
+            acc = row_local_map<LOGN, PE_RUNTIME, false, FEAT_TABLE>(v, t, row, nrow, erow, ngl, g, nullptr, R.pe);
         } else {
             if (R.pe == PE_UNIFORM) acc = row_local_map<LOGN, PE_UNIFORM>(v, t, row, nrow, erow, ngl, g);
             else if (R.pe == PE_TABLE) acc = row_local_map<LOGN, PE_TABLE>(v, t, row, nrow, erow, ngl, g);
@@ -504,7 +526,7 @@ k_col_tma_batch(const BatchRes *__restrict__ res, int nres, const float2 *__rest
         float2 v[16];
 #pragma unroll
         for (int si = 0; si < 16; ++si) v[si] = base[(t + si * T) * C + c];
-        LineBufs<float2, PP> lb{{PP ? stage(2) + c : base + c, base + c}, 0};
+        LineBufs<float2, PP> lb{{PP ? stage(2) + c : base + c, base + c}, 0, err};
         diffract_line<LOGN, C>(v, t, lb, tw, R.h, sync);
         float2 *col = R.E + (size_t)t * N + tile * C + c;
 #pragma unroll

@@ -15,7 +15,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("RT_LIBRARY") or os.path.join(HERE, "_lib", f"libbouncemap_{platform.machine()}.so")
 
-RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENUMERIC, RT_ETIMEOUT, RT_EBUSY = 0, -1, -2, -3, -4, -5, -6
+RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENUMERIC, RT_ETIMEOUT, RT_EBUSY, RT_EBOUNDS = 0, -1, -2, -3, -4, -5, -6, -7
 RT_PUMP_SUPERGAUSS, RT_PUMP_UNIFORM, RT_PUMP_ARRAY = 0, 1, 2
 RT_FP32, RT_FP64 = 0, 1
 RT_RELAX_EULER, RT_RELAX_EXACT = 0, 1
@@ -133,6 +133,7 @@ def lib() -> ctypes.CDLL:
             "rt_serve_drain": [vp, d],
             "rt_serve_stats": [vp, ctypes.POINTER(rt_serve_stats_t)],
             "rt_serve_destroy": [vp],
+            "rt_debug_fail_alloc": [i],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -248,6 +249,11 @@ def rt_read_history(h, max_values: int) -> np.ndarray:
 def rt_read_spectrum(h, dst):
     _check(lib().rt_read_spectrum(h, _ptr(dst), _nbytes(dst)), "rt_read_spectrum")
     return dst
+
+
+def rt_debug_fail_alloc(after: int):
+    """Test hook: the after-th device allocation from now on fails once (-1 cancels)."""
+    _check(lib().rt_debug_fail_alloc(int(after)), "rt_debug_fail_alloc")
 
 
 def rt_set_field_pattern(h, pattern: rt_pattern):
