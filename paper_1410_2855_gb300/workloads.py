@@ -57,6 +57,9 @@ C1_BOUNCES = 500
 # Single 512^2 complex64 resonator, N_F = 100, 1e4 round trips.
 C2 = Resonator(n=512, fresnel=100.0, g0=0.15, T1=5000.0, R=0.95)
 C2_BOUNCES = 10_000
+# The same resonator with the paper's curved mirror (z/F = 0.16) and a rough
+# surface (0.05 rad rms).
+C2_CURVED = Resonator(n=512, fresnel=100.0, g0=0.15, T1=5000.0, R=0.95, z_over_F=0.16, roughness_rms=0.05)
 # Single 2048^2 complex64 resonator, N_F = 1000, g0 in {0.1, 0.3}, 1e4 round trips.
 C3 = tuple(Resonator(n=2048, fresnel=1000.0, g0=g, T1=1e4, R=0.9, seed=BASE_SEED + i)
            for i, g in enumerate((0.1, 0.3)))

@@ -1,7 +1,9 @@
-"""Write tests/golden/longrun_512.json: the FP64 oracle's long run of the
-512^2 resonator (N_F = 100, g0 = 0.15, T1 = 5000, R = 0.95, super-Gaussian
-pump of order 10 and radius 0.8, 8-pixel edge, splitmix64 noise start of
-amplitude 1e-6, 1e4 bounces).
+"""Write tests/golden/longrun_512.json (flat mirror) or
+tests/golden/longrun_512_curved.json (curved, rough mirror): the FP64
+oracle's long run of the 512^2 resonator (N_F = 100, g0 = 0.15, T1 = 5000,
+R = 0.95, super-Gaussian pump of order 10 and radius 0.8, 8-pixel edge,
+splitmix64 noise start of amplitude 1e-6, 1e4 bounces; the curved case adds
+z/F = 0.16 and the seeded 0.05 rad rms roughness of workloads.C2_CURVED).
 
 Beyond a few tens of bounces the map is chaotic, so the stored values are
 statistics that a faithful FP32 run must reproduce rather than the field
@@ -9,7 +11,7 @@ itself: the mean intensity averaged over the last 1000 bounces, the mean
 intensity every 100 bounces, and the dominant spatial frequency of the final
 field (all bins, and bins with max(|mx|, |my|) >= 2), with m and -m folded.
 
-Calls only the oracle:  python tests/golden/make_longrun.py [threads]
+Calls only the oracle:  python tests/golden/make_longrun.py [flat|curved] [threads]
 """
 import json
 import os
@@ -26,10 +28,12 @@ from paper_1410_2855_gb300 import workloads as wl  # noqa: E402
 
 
 def main():
-    threads = int(sys.argv[1]) if len(sys.argv) > 1 else (os.cpu_count() or 1)
-    c, nb = wl.C2, wl.C2_BOUNCES
+    case = sys.argv[1] if len(sys.argv) > 1 else "flat"
+    threads = int(sys.argv[2]) if len(sys.argv) > 2 else (os.cpu_count() or 1)
+    c, nb = (wl.C2 if case == "flat" else wl.C2_CURVED), wl.C2_BOUNCES
     p = orc.make_params(c.n, orc.alpha_from_fresnel(c.fresnel, c.d_over_w), c.g0, c.T1, c.R, Isat=c.Isat,
-                        edge=c.edge, pump_order=c.pump_order, pump_radius=c.pump_radius)
+                        edge=c.edge, pump_order=c.pump_order, pump_radius=c.pump_radius, z_over_F=c.z_over_F,
+                        roughness=c.roughness())
     E, N = orc.init_state(p, c.seed, c.noise_amp)
     t0 = time.time()
     E, N, hist = orc.run(p, E, N, nb, nthreads=threads)
@@ -42,7 +46,8 @@ def main():
         "_source": "FP64 oracle (oracle/bouncemap_oracle.c), written by tests/golden/make_longrun.py",
         "resonator": {"n": c.n, "fresnel": c.fresnel, "g0": c.g0, "T1": c.T1, "R": c.R, "Isat": c.Isat,
                       "edge": c.edge, "pump_order": c.pump_order, "pump_radius": c.pump_radius,
-                      "d_over_w": c.d_over_w, "seed": c.seed, "noise_amp": c.noise_amp},
+                      "d_over_w": c.d_over_w, "seed": c.seed, "noise_amp": c.noise_amp, "z_over_F": c.z_over_F,
+                      "roughness_rms": c.roughness_rms, "roughness_corr": c.roughness_corr},
         "bounces": nb,
         "mean_intensity_last_1000": float(np.mean(hist[-1000:])),
         "mean_intensity_every_100": [float(v) for v in hist[99::100]],
@@ -52,7 +57,8 @@ def main():
         "oracle_seconds": round(time.time() - t0, 1),
         "threads": threads,
     }
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "longrun_512.json")
+    name = "longrun_512.json" if case == "flat" else "longrun_512_curved.json"
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), name)
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
     print(path, out["mean_intensity_last_1000"], out["peaks"])

@@ -1,10 +1,13 @@
 """Long horizon: the 512^2 resonator (N_F = 100, g0 = 0.15, T1 = 5000,
-R = 0.95) run for 1e4 bounces from the seeded noise start.  The map is
-chaotic well before that, so the FP32 and FP64 GPU paths are held to the
-statistics the FP64 oracle fixed in tests/golden/longrun_512.json (written
-by tests/golden/make_longrun.py): the mean intensity over the last 1000
-bounces within 1%, and the dominant spatial frequency (m and -m folded)
-exactly, unless the oracle's runner-up is within 1e-3 of its peak."""
+R = 0.95), with a flat mirror and with the paper's curved, rough mirror, run
+for 1e4 bounces from the seeded noise start.  The map is chaotic well before
+that, so the FP32 and FP64 GPU paths are held to the statistics the FP64
+oracle fixed in tests/golden/longrun_512*.json (written by
+tests/golden/make_longrun.py): the mean intensity over the last 1000 bounces
+within 1%, and the dominant spatial frequency (m and -m folded) exactly,
+unless the oracle's runner-up is within 1e-3 of its peak.  Where the final
+spectrum has no dominant peak (runner-up above half the peak, as with the
+curved mirror) only the mean intensity is compared."""
 import json
 import os
 
@@ -14,14 +17,15 @@ import pytest
 from paper_1410_2855_gb300 import build, rt, workloads as wl
 
 pytestmark = pytest.mark.gpu
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "longrun_512.json")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
+@pytest.mark.parametrize("case", ["flat", "curved"])
 @pytest.mark.parametrize("precision", [rt.RT_FP32, rt.RT_FP64])
-def test_long_run_statistics_match_oracle(precision):
+def test_long_run_statistics_match_oracle(precision, case):
     build.build()
-    g = json.load(open(GOLDEN))
-    c = wl.C2
+    g = json.load(open(os.path.join(GOLDEN, "longrun_512.json" if case == "flat" else "longrun_512_curved.json")))
+    c = wl.C2 if case == "flat" else wl.C2_CURVED
     with rt.Resonator.from_params(c, precision=precision, history_cap=20000, chunk=500) as r:
         r.step(g["bounces"])
         hist = r.history(g["bounces"])
@@ -31,5 +35,7 @@ def test_long_run_statistics_match_oracle(precision):
     assert abs(mean / g["mean_intensity_last_1000"] - 1.0) <= 0.01
     for ring, (mx, my, pw) in peaks.items():
         ref = g["peaks"][str(ring)]
+        if ref["runner_up"] > 0.5 * ref["power"]:
+            continue                                     # no dominant peak to compare
         tie = ref["runner_up"] >= (1.0 - 1e-3) * ref["power"]
         assert tie or (mx, my) == (ref["mx"], ref["my"]), (ring, mx, my, ref)
