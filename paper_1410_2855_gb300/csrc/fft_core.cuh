@@ -159,6 +159,12 @@ template <int LOGN> struct Plan {
     }
 };
 
+// 1: a pass's twiddles are loaded before its exchange, so their latency
+// overlaps the barrier and the shared-memory traffic.
+#ifndef RTK_TW_PREFETCH
+#define RTK_TW_PREFETCH 1
+#endif
+
 // Twiddle from the forward table (exp(-...)), conjugated for the inverse.
 // TWS: the table is in shared memory (plain load) rather than global memory
 // (read-only cache load).
@@ -227,6 +233,12 @@ __device__ __forceinline__ void fft_line(V (&v)[16], const int t, LineBufs<V, PP
         const int Ns = NsPrev * 16;
         V *line = lb.take();
         V *rd_base = line + padi(t) * CS;
+        const V *twp = tw + off + (t & (Ns - 1));
+        V wpre[RTK_TW_PREFETCH ? 15 : 1];
+        if constexpr (RTK_TW_PREFETCH) {
+#pragma unroll
+            for (int r = 1; r < 16; ++r) wpre[r - 1] = TWS ? twp[(r - 1) * Ns] : __ldg(twp + (r - 1) * Ns);
+        }
         if (!PP) sync();
         if (NsPrev == 1) {
             V *w = line + 17 * t * CS;
@@ -252,9 +264,11 @@ __device__ __forceinline__ void fft_line(V (&v)[16], const int t, LineBufs<V, PP
             for (int r = 0; r < 16; ++r)
                 if (sm_in<LOGN, CS>(line, &sm_at<CS>(line, t + r * T), lb.chk)) v[r] = sm_at<CS>(line, t + r * T);
         }
-        const V *twp = tw + off + (t & (Ns - 1));
 #pragma unroll
-        for (int r = 1; r < 16; ++r) v[r] = twmul<DIR, TWS>(v[r], twp, (r - 1) * Ns);
+        for (int r = 1; r < 16; ++r) {
+            if constexpr (RTK_TW_PREFETCH) v[r] = DIR > 0 ? cmulc(v[r], wpre[r - 1]) : cmul(v[r], wpre[r - 1]);
+            else v[r] = twmul<DIR, TWS>(v[r], twp, (r - 1) * Ns);
+        }
         off += 15 * Ns;
         dft<16, DIR>(v);
     }
@@ -263,6 +277,16 @@ __device__ __forceinline__ void fft_line(V (&v)[16], const int t, LineBufs<V, PP
         constexpr int NsPrev = NsL / 16;
         V *line = lb.take();
         V *rd_base = line + padi(t) * CS;
+        V wl[RTK_TW_PREFETCH ? NB * (RL - 1) : 1];
+        if constexpr (RTK_TW_PREFETCH) {
+#pragma unroll
+            for (int i = 0; i < NB; ++i)
+#pragma unroll
+                for (int r = 1; r < RL; ++r) {
+                    const V *q = tw + off + t + i * T + (r - 1) * NsL;
+                    wl[i * (RL - 1) + r - 1] = TWS ? *q : __ldg(q);
+                }
+        }
         if (!PP) sync();
         if constexpr (NsPrev == 1) {
             V *w = line + 17 * t * CS;
@@ -289,7 +313,14 @@ __device__ __forceinline__ void fft_line(V (&v)[16], const int t, LineBufs<V, PP
                                                                                    : v[i];
             const V *twp = tw + off + j;
 #pragma unroll
-            for (int r = 1; r < RL; ++r) u[r] = twmul<DIR, TWS>(u[r], twp, (r - 1) * NsL);
+            for (int r = 1; r < RL; ++r) {
+                if constexpr (RTK_TW_PREFETCH) {
+                    const V w = wl[i * (RL - 1) + r - 1];
+                    u[r] = DIR > 0 ? cmulc(u[r], w) : cmul(u[r], w);
+                } else {
+                    u[r] = twmul<DIR, TWS>(u[r], twp, (r - 1) * NsL);
+                }
+            }
             dft<RL, DIR>(u);
 #pragma unroll
             for (int r = 0; r < RL; ++r) v[i + r * NB] = u[r];
