@@ -218,9 +218,11 @@ __device__ __forceinline__ bool sm_in(const V *base, const V *p, int *chk)
 // is a barrier over every thread that shares them.  Shared addresses are a
 // per-thread base plus compile-time offsets: spans and T are multiples of 16
 // wherever the pad arithmetic allows it.
-template <int LOGN, int DIR, int CS, bool PP, bool TWS = false, typename V, typename SyncF>
+// POST: multiply the result by post[k] (element k of the output line); the
+// factors are loaded ahead of the last exchange when there is a trailing pass.
+template <int LOGN, int DIR, int CS, bool PP, bool TWS = false, bool POST = false, typename V, typename SyncF>
 __device__ __forceinline__ void fft_line(V (&v)[16], const int t, LineBufs<V, PP> &lb, const V *__restrict__ tw,
-                                         SyncF sync)
+                                         SyncF sync, const V *__restrict__ post = nullptr)
 {
     using P = Plan<LOGN>;
     constexpr int N = P::N, T = P::T;
@@ -277,6 +279,11 @@ __device__ __forceinline__ void fft_line(V (&v)[16], const int t, LineBufs<V, PP
         constexpr int NsPrev = NsL / 16;
         V *line = lb.take();
         V *rd_base = line + padi(t) * CS;
+        V pl[POST ? 16 : 1];
+        if constexpr (POST) {
+#pragma unroll
+            for (int s = 0; s < 16; ++s) pl[s] = __ldg(post + t + s * T);
+        }
         V wl[RTK_TW_PREFETCH ? NB * (RL - 1) : 1];
         if constexpr (RTK_TW_PREFETCH) {
 #pragma unroll
@@ -323,8 +330,14 @@ __device__ __forceinline__ void fft_line(V (&v)[16], const int t, LineBufs<V, PP
             }
             dft<RL, DIR>(u);
 #pragma unroll
-            for (int r = 0; r < RL; ++r) v[i + r * NB] = u[r];
+            for (int r = 0; r < RL; ++r) {
+                if constexpr (POST) v[i + r * NB] = cmul(u[r], pl[i + r * NB]);
+                else v[i + r * NB] = u[r];
+            }
         }
+    } else if constexpr (POST) {
+#pragma unroll
+        for (int s = 0; s < 16; ++s) v[s] = cmul(v[s], __ldg(post + t + s * T));
     }
 }
 

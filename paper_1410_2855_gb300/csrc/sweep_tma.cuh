@@ -33,6 +33,12 @@ constexpr int ERR_TIMEOUT = -5;
 #define RTK_COL_PP 1
 #endif
 
+// 1: the propagator factors are loaded ahead of the forward transform's last
+// exchange and applied as its outputs come out.
+#ifndef RTK_H_PREFETCH
+#define RTK_H_PREFETCH 1
+#endif
+
 // TAB: the stage also carries the rows' N0 (pump table) values.
 template <int LOGN, int LPC, bool PP, bool TAB = false> struct RowStage {
     static constexpr int N = 1 << LOGN;
@@ -233,11 +239,15 @@ __device__ __forceinline__ void diffract_line(float2 (&v)[16], int t, LineBufs<f
                                               const float2 *__restrict__ tw, const float2 *__restrict__ h,
                                               SyncF sync)
 {
+#if RTK_H_PREFETCH
+    fft_line<LOGN, -1, CS, PP, false, true>(v, t, lb, tw, sync, h);
+#else
     constexpr int T = Plan<LOGN>::T;
     fft_line<LOGN, -1, CS>(v, t, lb, tw, sync);
     const float2 *hp = h + t;
 #pragma unroll
     for (int si = 0; si < 16; ++si) v[si] = cmul(v[si], __ldg(hp + si * T));
+#endif
     fft_line<LOGN, +1, CS>(v, t, lb, tw, sync);
 }
 
