@@ -79,6 +79,16 @@ template <typename V> __device__ __forceinline__ V cmul(V a, V b)
 {
     return cmk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
+// a * b with every rounding spelled out: the same bits wherever it is
+// inlined (no context-dependent contraction into fused multiply-adds).
+__device__ __forceinline__ float2 cmul_rn(float2 a, float2 b)
+{
+    return make_float2(__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)), __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
+}
+__device__ __forceinline__ double2 cmul_rn(double2 a, double2 b)
+{
+    return make_double2(__fma_rn(a.x, b.x, -__dmul_rn(a.y, b.y)), __fma_rn(a.x, b.y, __dmul_rn(a.y, b.x)));
+}
 // a * conj(b)
 template <typename V> __device__ __forceinline__ V cmulc(V a, V b)
 {
@@ -331,13 +341,13 @@ __device__ __forceinline__ void fft_line(V (&v)[16], const int t, LineBufs<V, PP
             dft<RL, DIR>(u);
 #pragma unroll
             for (int r = 0; r < RL; ++r) {
-                if constexpr (POST) v[i + r * NB] = cmul(u[r], pl[i + r * NB]);
+                if constexpr (POST) v[i + r * NB] = cmul_rn(u[r], pl[i + r * NB]);
                 else v[i + r * NB] = u[r];
             }
         }
     } else if constexpr (POST) {
 #pragma unroll
-        for (int s = 0; s < 16; ++s) v[s] = cmul(v[s], __ldg(post + t + s * T));
+        for (int s = 0; s < 16; ++s) v[s] = cmul_rn(v[s], __ldg(post + t + s * T));
     }
 }
 

@@ -121,13 +121,10 @@ k_row(const cv<R> *in, cv<R> *out, const cv<R> *__restrict__ tw, const cv<R> *__
 
     if constexpr (MODE == MODE_INV) {
         fft_line<LOGN, +1, 1>(v, t, lb, tw, sync);
-    } else {
+    } else if constexpr (MODE == MODE_FWD) {
         fft_line<LOGN, -1, 1>(v, t, lb, tw, sync);
-    }
-    if constexpr (MODE >= MODE_DIFF) {
-        const V *hp = h + t;
-#pragma unroll
-        for (int s = 0; s < 16; ++s) v[s] = cmul(v[s], __ldg(hp + s * T));
+    } else {  // diffraction: the propagator is applied as the forward transform ends
+        fft_line<LOGN, -1, 1, false, false, true>(v, t, lb, tw, sync, h);
         fft_line<LOGN, +1, 1>(v, t, lb, tw, sync);
     }
     V *dst = out + (size_t)row * N + t;
@@ -157,13 +154,10 @@ k_col(cv<R> *X, const cv<R> *__restrict__ tw, const cv<R> *__restrict__ h)
     for (int s = 0; s < 16; ++s) v[s] = col[(size_t)s * T * N];
     if constexpr (MODE == MODE_INV) {
         fft_line<LOGN, +1, C>(v, t, lb, tw, sync);
-    } else {
+    } else if constexpr (MODE == MODE_FWD) {
         fft_line<LOGN, -1, C>(v, t, lb, tw, sync);
-    }
-    if constexpr (MODE >= MODE_DIFF) {
-        const V *hp = h + t;
-#pragma unroll
-        for (int s = 0; s < 16; ++s) v[s] = cmul(v[s], __ldg(hp + s * T));
+    } else {  // diffraction, as in the persistent sweeps
+        fft_line<LOGN, -1, C, false, false, true>(v, t, lb, tw, sync, h);
         fft_line<LOGN, +1, C>(v, t, lb, tw, sync);
     }
 #pragma unroll

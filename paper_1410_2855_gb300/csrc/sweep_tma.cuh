@@ -130,13 +130,6 @@ __device__ __forceinline__ void init_stage_barriers(uint64_t *bar)
     __syncthreads();
 }
 
-// Complex product with every rounding spelled out, so that the general local
-// map gives the same bits wherever it is inlined (handle and batched sweeps).
-__device__ __forceinline__ float2 cmul_rn(float2 a, float2 b)
-{
-    return make_float2(__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)), __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
-}
-
 // Order-10 super-Gaussian pump g0 exp(-q^5), q = (x^2 + y^2) / r_p^2, with
 // yq = y^2 / r_p^2 precomputed per row; roundings spelled out as above (the
 // general forms; the plain form leaves contraction to the compiler, which
@@ -246,7 +239,7 @@ __device__ __forceinline__ void diffract_line(float2 (&v)[16], int t, LineBufs<f
     fft_line<LOGN, -1, CS>(v, t, lb, tw, sync);
     const float2 *hp = h + t;
 #pragma unroll
-    for (int si = 0; si < 16; ++si) v[si] = cmul(v[si], __ldg(hp + si * T));
+    for (int si = 0; si < 16; ++si) v[si] = cmul_rn(v[si], __ldg(hp + si * T));
 #endif
     fft_line<LOGN, +1, CS>(v, t, lb, tw, sync);
 }
