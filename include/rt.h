@@ -88,7 +88,8 @@ typedef enum {
     RT_ENUMERIC = -4,  /* the field's mean intensity became NaN or Inf */
     RT_ETIMEOUT = -5,  /* a bounded wait ran out */
     RT_EBUSY = -6,     /* the handle or server cannot take the request now */
-    RT_EBOUNDS = -7    /* an index left its buffer (bounds-checked builds only; the access was skipped) */
+    RT_EBOUNDS = -7,   /* an index left its buffer (bounds-checked builds only; the access was skipped) */
+    RT_ECANCELED = -8  /* a served request was cancelled (rt_serve_cancel) */
 } rt_status;
 
 enum { RT_PUMP_SUPERGAUSS = 0, RT_PUMP_UNIFORM = 1, RT_PUMP_ARRAY = 2 };
@@ -391,6 +392,13 @@ rt_status rt_serve_create(const rt_serve_opts *opts, rt_server **out);
  * until then.  *id receives the request id.
  * RT_EINVAL for bad jobs or a request that could never fit the budget. */
 rt_status rt_serve_submit(rt_server *s, const rt_job *job, long long n_bounces, void *field_out, long long *id);
+
+/* Cancel request `id`: a queued request is dropped at once, a running one
+ * stops after the current scheduling round; either way its result is posted
+ * with status RT_ECANCELED, the bounces it ran, and field_out left
+ * unwritten.  RT_EINVAL if the id is unknown or its result was already
+ * posted. */
+rt_status rt_serve_cancel(rt_server *s, long long id);
 
 /* Move up to `max` finished results into out (oldest first); *got = count. */
 rt_status rt_serve_poll(rt_server *s, rt_result *out, int max, int *got);

@@ -279,6 +279,7 @@ const char *rt_status_string(rt_status s)
     case RT_ETIMEOUT: return "bounded wait timed out";
     case RT_EBUSY: return "busy";
     case RT_EBOUNDS: return "index out of bounds (checked build)";
+    case RT_ECANCELED: return "request cancelled";
     default: return "unknown status";
     }
 }

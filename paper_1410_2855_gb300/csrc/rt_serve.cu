@@ -19,6 +19,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <set>
 #include <string>
 #include <thread>
 #include <vector>
@@ -71,6 +72,8 @@ struct rt_server {
     bool stop = false;
     std::deque<Request> queue;
     std::deque<rt_result> results;
+    std::set<long long> live;         // ids queued or running
+    std::set<long long> cancel;       // ids to cancel once the worker holds them
     long long next_id = 1, submitted = 0, finished = 0, running = 0, rounds = 0;
     double point_bounces = 0.0, busy_s = 0.0;
     long long resident = 0;
@@ -196,6 +199,22 @@ cudaError_t round_graph(rt_server *s, cudaGraphExec_t *out)
     return cudaSuccess;
 }
 
+// Result of a request that never ran (cancelled while queued); s->mu held.
+void post_unrun_locked(rt_server *s, const Request &q, int status)
+{
+    rt_result r{};
+    r.id = q.id;
+    r.status = status;
+    r.n = q.job.n;
+    r.submit_s = q.submit_s;
+    r.admit_s = -1.0;
+    r.finish_s = s->now();
+    s->results.push_back(r);
+    ++s->finished;
+    s->live.erase(q.id);
+    s->cancel.erase(q.id);
+}
+
 void post(rt_server *s, const SSlot &sl, int status, long long bounces, double mean)
 {
     rt_result r{};
@@ -211,6 +230,8 @@ void post(rt_server *s, const SSlot &sl, int status, long long bounces, double m
     s->results.push_back(r);
     ++s->finished;
     --s->running;
+    s->live.erase(r.id);
+    s->cancel.erase(r.id);
 }
 
 // One scheduling round: launch, wait, retire.  Returns false on a CUDA failure.
@@ -219,6 +240,11 @@ bool run_round(rt_server *s)
     TraceRange tr("serve round");
     const double t_start = s->now();
     cudaGraphExec_t ge;
+    std::set<long long> cancel;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        cancel = s->cancel;
+    }
     cudaError_t e = round_graph(s, &ge);
     if (e == cudaSuccess) e = cudaGraphLaunch(ge, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -251,6 +277,11 @@ bool run_round(rt_server *s)
                 }
                 post(s, sl, status, b, ctl[k].last_mean);
                 sl.busy = false;
+            } else if (cancel.count(sl.req.id)) {
+                // stop the slot (later rounds skip it) and report what it ran
+                if (e == cudaSuccess) e = slot_set_target(c.d_res + k, 0, s->stream);
+                post(s, sl, RT_ECANCELED, b, ctl[k].last_mean);
+                sl.busy = false;
             }
         }
     }
@@ -274,7 +305,10 @@ void worker_main(rt_server *s)
         {
             std::unique_lock<std::mutex> lk(s->mu);
             if (s->stop) break;
-            fresh.assign(s->queue.begin(), s->queue.end());
+            for (const Request &q : s->queue) {
+                if (s->cancel.count(q.id)) post_unrun_locked(s, q, RT_ECANCELED);
+                else fresh.push_back(q);
+            }
             s->queue.clear();
             any_running = s->running > 0;
             if (fresh.empty() && !any_running) {
@@ -292,7 +326,10 @@ void worker_main(rt_server *s)
         {
             std::lock_guard<std::mutex> lk(s->mu);
             s->running += admitted;
-            for (auto it = waiting.rbegin(); it != waiting.rend(); ++it) s->queue.push_front(*it);
+            for (auto it = waiting.rbegin(); it != waiting.rend(); ++it) {
+                if (s->cancel.count(it->id)) post_unrun_locked(s, *it, RT_ECANCELED);
+                else s->queue.push_front(*it);
+            }
             any_running = s->running > 0;
         }
         if (!any_running) {
@@ -381,10 +418,33 @@ rt_status rt_serve_submit(rt_server *s, const rt_job *job, long long n_bounces, 
         r.id = s->next_id++;
         r.submit_s = s->now();
         s->queue.push_back(r);
+        s->live.insert(r.id);
         ++s->submitted;
     }
     s->cv.notify_one();
     *id = r.id;
+    return RT_OK;
+}
+
+rt_status rt_serve_cancel(rt_server *s, long long id)
+{
+    if (!s) return RT_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (!s->live.count(id)) return RT_EINVAL;
+        bool dropped = false;
+        for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+            if (it->id == id) {
+                post_unrun_locked(s, *it, RT_ECANCELED);
+                s->queue.erase(it);
+                dropped = true;
+                break;
+            }
+        }
+        if (!dropped) s->cancel.insert(id);  // being admitted or running: the worker stops it
+    }
+    s->done_cv.notify_all();
+    s->cv.notify_one();
     return RT_OK;
 }
 

@@ -15,7 +15,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("RT_LIBRARY") or os.path.join(HERE, "_lib", f"libbouncemap_{platform.machine()}.so")
 
-RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENUMERIC, RT_ETIMEOUT, RT_EBUSY, RT_EBOUNDS = 0, -1, -2, -3, -4, -5, -6, -7
+RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENUMERIC, RT_ETIMEOUT, RT_EBUSY, RT_EBOUNDS, RT_ECANCELED = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
 RT_PUMP_SUPERGAUSS, RT_PUMP_UNIFORM, RT_PUMP_ARRAY = 0, 1, 2
 RT_FP32, RT_FP64 = 0, 1
 RT_RELAX_EULER, RT_RELAX_EXACT = 0, 1
@@ -130,6 +131,7 @@ def lib() -> ctypes.CDLL:
             "rt_serve_create": [ctypes.POINTER(rt_serve_opts), ctypes.POINTER(vp)],
             "rt_serve_submit": [vp, ctypes.POINTER(rt_job), ll, vp, ctypes.POINTER(ll)],
             "rt_serve_poll": [vp, ctypes.POINTER(rt_result), i, ctypes.POINTER(i)],
+            "rt_serve_cancel": [vp, ll],
             "rt_serve_drain": [vp, d],
             "rt_serve_stats": [vp, ctypes.POINTER(rt_serve_stats_t)],
             "rt_serve_destroy": [vp],
@@ -549,6 +551,10 @@ class Server:
         if field_out is not None:
             self._keep[rid.value] = field_out
         return rid.value
+
+    def cancel(self, request_id: int):
+        """Cancel a queued or running request (its result is posted with RT_ECANCELED)."""
+        _check(lib().rt_serve_cancel(self.h, int(request_id)), "rt_serve_cancel")
 
     def poll(self, max_results: int = 1024):
         buf = (rt_result * max_results)()

@@ -85,3 +85,32 @@ def test_invalid_requests_are_rejected():
         j.pump.order = 8.0                    # needs an N0 table: not served
         with pytest.raises(rt.RtError):
             srv.submit(j, 5)
+
+
+def test_cancellation_of_queued_and_running_requests():
+    # A long request is stopped after a round; a request still waiting for
+    # room is dropped without running; the other request is unaffected.
+    long = wl.Resonator(n=256, fresnel=150.0, g0=0.25, T1=900.0, R=0.93, seed=31)
+    short = wl.Resonator(n=256, fresnel=150.0, g0=0.25, T1=900.0, R=0.93, seed=32)
+    slot = 256 * 256 * 12
+    out = np.zeros((256, 256), np.complex64)
+    with rt.Server(chunk=20, budget_bytes=int(1.5 * slot)) as srv:   # one request resident at a time
+        a = srv.submit(long, 10_000_000)
+        b = srv.submit(short, 40, out)
+        c = srv.submit(short, 40)
+        t0 = time.time()
+        while srv.stats().running == 0 and time.time() - t0 < 60:
+            time.sleep(0.002)
+        srv.cancel(c)                       # still queued behind a
+        srv.cancel(a)                       # running
+        with pytest.raises(rt.RtError):
+            srv.cancel(987654)
+        srv.drain(120)
+        res = {r.id: r for r in srv.poll()}
+        with pytest.raises(rt.RtError):
+            srv.cancel(a)                   # already posted
+    assert res[a].status == rt.RT_ECANCELED and 0 < res[a].bounces < 10_000_000
+    assert res[c].status == rt.RT_ECANCELED and res[c].bounces == 0 and res[c].admit_s < 0
+    assert res[b].status == 0 and res[b].bounces == 40
+    ref, _ = alone(short, 40)
+    assert np.array_equal(out, ref)
