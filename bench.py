@@ -562,6 +562,24 @@ def comparisons(args, rt, torch, main, streams, params, res, E0, N0, rank, world
     extra["extensions"]["workload"] = ("2048^2, N_F 1000, g0 0.3, R 0.9, one stream; field_at and the pattern "
                                        "include the host copy / synchronisation (wall clock)")
 
+    # ---- a resonator larger than L2: 4096^2 (192 MiB of state), one stream
+    big = dataclasses.replace(base, n=4096, fresnel=4000.0)
+    with torch.cuda.stream(main):
+        with rt.Resonator.from_params(big, cuda_stream=main.cuda_stream, chunk=100) as r:
+            r.step(100)
+            torch.cuda.synchronize()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(main)
+            r.step(300)
+            e.record(main)
+            torch.cuda.synchronize()
+            r.sync()
+            rate = 300 / (s.elapsed_time(e) / 1e3)
+    peak, _ = measured_peak()
+    extra["larger_than_l2"] = {"workload": "one 4096^2 resonator (N_F 4000, g0 0.3, R 0.9): 192 MiB of state "
+                                           "against a 126 MB L2; one stream, graphs of 100 bounces",
+                               "round_trips_per_s": rate, "bounce_hbm_frac": 40 * 4096 ** 2 * rate / 1e9 / peak}
+
     # ---- batched parameter sweep: 256 resonators of side 256/512/1024 in one graph per 100 bounces
     jobs = wl.batch_sweep(count=256, sides=(256, 512, 1024))
     with torch.cuda.stream(main):
