@@ -307,13 +307,15 @@ def weak_scaling_rate(local_ms, local_units, world, device=None):
     return world * local_units / (total_ms / 1e3), total_ms
 
 
-def serve_replay(rt, stream, count=40, rate_hz=50.0):
+def serve_replay(rt, stream, count=40, rate_hz=50.0, policy=0, round_points=0):
     """Replay the first `count` requests of the seeded Poisson stream (mean
     rate_hz; sides 128..2048, bounces log-uniform in [1e3, 1e5]) against a
     server with 500-bounce rounds and an 8 GiB budget; latency is completion
-    minus submission on the server clock."""
+    minus submission on the server clock.  policy: the server's scheduling
+    policy (0 first come first served, 1 shortest remaining work first)."""
     trace = wl.serve_trace(count=count, rate_hz=rate_hz)
-    with rt.Server(chunk=500, budget_bytes=8 << 30, cuda_stream=stream.cuda_stream) as srv:
+    with rt.Server(chunk=500, budget_bytes=8 << 30, cuda_stream=stream.cuda_stream, policy=policy,
+                   round_points=round_points) as srv:
         t0 = time.perf_counter()
         for req in trace:
             delay = t0 + req.arrival_s - time.perf_counter()
@@ -329,6 +331,7 @@ def serve_replay(rt, stream, count=40, rate_hz=50.0):
     offered = sum(float(q.job.n) ** 2 * q.bounces for q in trace) / max(trace[-1].arrival_s, 1e-9)
     return {"workload": f"first {count} requests of a Poisson stream at {rate_hz:g} req/s, sides uniform over "
                         "{128,...,2048}, bounces log-uniform in [1e3,1e5]; 500-bounce rounds, 8 GiB budget",
+            "policy": "shortest remaining work first" if policy else "every resident request every round",
             "requests": len(res), "failed": sum(1 for r in res if r.status != 0),
             "p50_latency_s": lat[len(lat) // 2], "p99_latency_s": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
             "round_trips_per_s": sum(r.bounces for r in res) / span,
@@ -603,6 +606,7 @@ def comparisons(args, rt, torch, main, streams, params, res, E0, N0, rank, world
 
     # ---- serving: a bounded replay of the Poisson request stream
     extra["serve"] = serve_replay(rt, main)
+    extra["serve_shortest_first"] = serve_replay(rt, main, policy=rt.RT_SERVE_SHORTEST_FIRST)
 
     # ---- plain FP64 GPU path on the same GPU (unfused, six sweeps per bounce)
     p = params[1]

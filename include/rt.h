@@ -356,11 +356,18 @@ rt_status rt_batch_destroy(rt_batch *b);
  * request's result is the same as running it alone on a handle. */
 typedef struct rt_server rt_server;
 
+enum { RT_SERVE_FIFO = 0, RT_SERVE_SHORTEST_FIRST = 1 };
+
 typedef struct {
     long long budget_bytes;   /* device memory for resident requests (8 GiB) */
     int chunk;                /* bounces per scheduling round (500) */
     int max_per_size;         /* resident requests of one grid size at most (128) */
     void *cuda_stream;        /* stream to run on; NULL = the server creates its own */
+    int policy;               /* RT_SERVE_FIFO: every resident request advances chunk bounces per round;
+                                 RT_SERVE_SHORTEST_FIRST: each round advances only the resident requests
+                                 with the least remaining work (n^2 x bounces left, ties by submission)
+                                 until their points reach round_points; the others wait (FIFO) */
+    long long round_points;   /* shortest-first: grid points advanced per round (0 = 2^23, two 2048^2 grids) */
 } rt_serve_opts;
 
 typedef struct {

@@ -11,6 +11,7 @@
 // per-slot counters, and retires finished requests: their final field is
 // copied to the caller's buffer and a result is posted.  Device state stays
 // resident between rounds.
+#include <algorithm>
 #include <chrono>
 #include <climits>
 #include <condition_variable>
@@ -46,6 +47,7 @@ struct SSlot {
     bool busy = false;
     Request req;
     long long last_bounce = 0;
+    long long target = 0;       // bounce target last written to the slot's descriptor
 };
 
 struct SClass {
@@ -54,6 +56,7 @@ struct SClass {
     SlotCtl *ctl = nullptr;     // capacity entries
     float2 *tw = nullptr;
     std::vector<SSlot> slots;   // allocated slots (<= capacity)
+    std::vector<long long> targets;  // host staging of the slots' bounce targets
 };
 
 }  // namespace
@@ -157,6 +160,7 @@ bool admit(rt_server *s, Request &r)
     if (slot_start(r.job, sl.buf, c.colC, c.tw, &c.ctl[idx], c.d_res + idx, kHistCap, r.bounces, s->stream) !=
         cudaSuccess)
         return false;
+    sl.target = r.bounces;
     sl.busy = true;
     sl.req = r;
     sl.req.admit_s = s->now();
@@ -234,6 +238,47 @@ void post(rt_server *s, const SSlot &sl, int status, long long bounces, double m
     s->cancel.erase(r.id);
 }
 
+// Shortest-first: advance only the resident requests with the least work
+// left this round (their grid points up to round_points), by writing every
+// slot's bounce target; the batched kernels skip slots at their target.
+cudaError_t select_round(rt_server *s)
+{
+    struct Cand {
+        SClass *c;
+        int k;
+        double left;
+        long long id;
+    };
+    std::vector<Cand> cand;
+    for (auto &kv : s->classes)
+        for (size_t k = 0; k < kv.second.slots.size(); ++k) {
+            const SSlot &sl = kv.second.slots[k];
+            if (!sl.busy) continue;
+            const double n2 = (double)sl.req.job.n * sl.req.job.n;
+            cand.push_back({&kv.second, (int)k, n2 * (double)(sl.req.bounces - sl.last_bounce), sl.req.id});
+        }
+    std::sort(cand.begin(), cand.end(),
+              [](const Cand &a, const Cand &b) { return a.left < b.left || (a.left == b.left && a.id < b.id); });
+    const double budget = s->opts.round_points > 0 ? (double)s->opts.round_points : (double)(1ll << 23);
+    double pts = 0.0;
+    for (const Cand &cd : cand) {
+        SSlot &sl = cd.c->slots[cd.k];
+        const bool active = pts < budget;
+        if (active) pts += (double)sl.req.job.n * sl.req.job.n;
+        sl.target = active ? std::min(sl.req.bounces, sl.last_bounce + (long long)s->opts.chunk) : sl.last_bounce;
+    }
+    for (auto &kv : s->classes) {
+        SClass &c = kv.second;
+        if (c.slots.empty()) continue;
+        c.targets.resize(c.slots.size());
+        for (size_t k = 0; k < c.slots.size(); ++k) c.targets[k] = c.slots[k].target;
+        cudaError_t e = cudaMemcpy2DAsync(&c.d_res[0].target, sizeof(BatchRes), c.targets.data(), sizeof(long long),
+                                          sizeof(long long), c.slots.size(), cudaMemcpyHostToDevice, s->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 // One scheduling round: launch, wait, retire.  Returns false on a CUDA failure.
 bool run_round(rt_server *s)
 {
@@ -245,7 +290,8 @@ bool run_round(rt_server *s)
         std::lock_guard<std::mutex> lk(s->mu);
         cancel = s->cancel;
     }
-    cudaError_t e = round_graph(s, &ge);
+    cudaError_t e = s->opts.policy == RT_SERVE_SHORTEST_FIRST ? select_round(s) : cudaSuccess;
+    if (e == cudaSuccess) e = round_graph(s, &ge);
     if (e == cudaSuccess) e = cudaGraphLaunch(ge, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     int err = 0;
@@ -280,6 +326,7 @@ bool run_round(rt_server *s)
             } else if (cancel.count(sl.req.id)) {
                 // stop the slot (later rounds skip it) and report what it ran
                 if (e == cudaSuccess) e = slot_set_target(c.d_res + k, 0, s->stream);
+                sl.target = 0;
                 post(s, sl, RT_ECANCELED, b, ctl[k].last_mean);
                 sl.busy = false;
             }
@@ -378,7 +425,8 @@ rt_status rt_serve_create(const rt_serve_opts *opts, rt_server **out)
     rt_serve_opts o;
     if (opts) o = *opts;
     else rt_serve_opts_default(&o);
-    if (o.budget_bytes <= 0 || o.chunk <= 0 || o.max_per_size <= 0) return RT_EINVAL;
+    if (o.budget_bytes <= 0 || o.chunk <= 0 || o.max_per_size <= 0 || o.round_points < 0) return RT_EINVAL;
+    if (o.policy != RT_SERVE_FIFO && o.policy != RT_SERVE_SHORTEST_FIRST) return RT_EINVAL;
     rt_server *s = new (std::nothrow) rt_server();
     if (!s) return RT_ENOMEM;
     s->opts = o;

@@ -21,6 +21,7 @@ RT_PUMP_SUPERGAUSS, RT_PUMP_UNIFORM, RT_PUMP_ARRAY = 0, 1, 2
 RT_FP32, RT_FP64 = 0, 1
 RT_RELAX_EULER, RT_RELAX_EXACT = 0, 1
 RT_PATTERN_GAUSSIAN, RT_PATTERN_BEAM_ARRAY, RT_PATTERN_VORTEX_ARRAY = 0, 1, 2
+RT_SERVE_FIFO, RT_SERVE_SHORTEST_FIRST = 0, 1
 
 
 class RtError(RuntimeError):
@@ -59,7 +60,7 @@ class rt_job(ctypes.Structure):
 
 class rt_serve_opts(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_longlong), ("chunk", ctypes.c_int), ("max_per_size", ctypes.c_int),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("cuda_stream", ctypes.c_void_p), ("policy", ctypes.c_int), ("round_points", ctypes.c_longlong)]
 
 
 class rt_result(ctypes.Structure):
@@ -528,7 +529,8 @@ def rt_serve_opts_default() -> rt_serve_opts:
 
 class Server:
     """Continuous-batching server (C ABI rt_serve_*).  ``Server(**opts)`` with
-    rt_serve_opts fields (budget_bytes, chunk, max_per_size, cuda_stream)."""
+    rt_serve_opts fields (budget_bytes, chunk, max_per_size, cuda_stream,
+    policy, round_points)."""
 
     def __init__(self, **opts):
         o = rt_serve_opts_default()

@@ -135,3 +135,11 @@ def test_sliced_gain_medium_is_refused_where_unsupported(lib):
     jobs = (rt.rt_job * 1)(rt.rt_job_default(64))
     h = ctypes.c_void_p()
     assert lib.rt_batch_create(jobs, 1, ctypes.byref(o), ctypes.byref(h)) == rt.RT_EINVAL and not h.value
+
+
+def test_server_rejects_bad_options_before_touching_the_device(lib):
+    h = ctypes.c_void_p()
+    for field, value in [("policy", 7), ("round_points", -1), ("chunk", 0)]:
+        o = rt.rt_serve_opts_default()
+        setattr(o, field, value)
+        assert lib.rt_serve_create(ctypes.byref(o), ctypes.byref(h)) == rt.RT_EINVAL and not h.value

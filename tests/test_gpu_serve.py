@@ -114,3 +114,26 @@ def test_cancellation_of_queued_and_running_requests():
     assert res[b].status == 0 and res[b].bounces == 40
     ref, _ = alone(short, 40)
     assert np.array_equal(out, ref)
+
+
+def test_shortest_first_policy_runs_short_requests_first_with_identical_results():
+    # With a round budget of one 256^2 grid, only the request with the least
+    # work left advances each round: the short request submitted after the
+    # long one finishes first, and both results equal their runs alone.
+    long = wl.Resonator(n=512, fresnel=150.0, g0=0.25, T1=900.0, R=0.93, seed=41)
+    short = wl.Resonator(n=128, fresnel=60.0, g0=0.2, T1=500.0, R=0.95, seed=42)
+    outs = [np.zeros((512, 512), np.complex64), np.zeros((128, 128), np.complex64)]
+    with rt.Server(chunk=100, budget_bytes=1 << 28, policy=rt.RT_SERVE_SHORTEST_FIRST,
+                   round_points=256 * 256) as srv:
+        a = srv.submit(long, 60_000, outs[0])          # about a second of rounds
+        t0 = time.time()
+        while srv.stats().running == 0 and time.time() - t0 < 60:
+            time.sleep(0.002)
+        b = srv.submit(short, 300, outs[1])
+        srv.drain(300)
+        res = {r.id: r for r in srv.poll()}
+    assert res[a].status == 0 and res[b].status == 0
+    assert res[b].finish_s < res[a].finish_s
+    for p, nb, o in ((long, 60_000, outs[0]), (short, 300, outs[1])):
+        ref, _ = alone(p, nb)
+        assert np.array_equal(o, ref)
