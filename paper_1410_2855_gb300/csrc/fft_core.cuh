@@ -99,30 +99,137 @@ template <typename V> __device__ __forceinline__ V cscale(V a, typename real_of<
     return cmk<V>(a.x * s, a.y * s);
 }
 
-// exp(DIR * 2 pi i k / 16), k a constant after unrolling; multiples of 4
-// are done with swaps and negations only.
+// a * (DIR i)^q: quarter turns are swaps and negations only.
+template <int DIR, typename V> __device__ __forceinline__ V quarter(V a, int q)
+{
+    q &= 3;
+    if (q == 0) return a;
+    if (q == 2) return cmk<V>(-a.x, -a.y);
+    return (q == 1) == (DIR > 0) ? cmk<V>(-a.y, a.x) : cmk<V>(a.y, -a.x);
+}
+
+#ifndef RTK_ROT_SMALL
+#define RTK_ROT_SMALL 1
+#endif
+
+// Rotation by a small angle theta in the form a + a * ((cos theta - 1) + i sin theta).
+// cos theta - 1 is far smaller than cos theta, so its rounded value carries
+// about three more bits of cos theta; with it the rounded pair lies within
+// about 1e-8 of the unit circle, where the rounded (cos, sin) pair of pi/8
+// or pi/4 falls 3-6e-8 inside it.  Every pass of every transform applied
+// that shortfall to the same paths, so an FP32 round trip lost about 2.5e-7
+// of its power to it; in this form the loss drops to rounding noise.
+// RTK_ROT_SMALL=0 builds the rounded (cos, sin) form for comparison.
+template <typename R> struct Rot16Const;
+template <> struct Rot16Const<float> {
+    // cos - 1 and sin of pi/8 rounded to nearest; of pi/4, cos - 1 is the
+    // float one ulp above the nearest, which puts the pair 8e-9 outside the
+    // circle instead of 3.4e-8 inside it (found by exact search over
+    // neighbouring floats).
+    static constexpr float cm8 = -0.0761204659938812255859375f, s8 = 0.3826834261417388916015625f;
+    static constexpr float cm4 = -0.2928932011127471923828125f, s4 = 0.707106769084930419921875f;
+};
+template <> struct Rot16Const<double> {
+    static constexpr double cm8 = -0.07612046748871324387, s8 = 0.38268343236508977173;
+    static constexpr double cm4 = -0.29289321881345247560, s4 = 0.70710678118654752440;
+};
+
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// g * Re(a w) and g * Im(a w) for w = (1 + cm) + i s and a sign g = +-1
+// known at compile time, each rounding explicit.  The sign rides on the FMA
+// operands (rounding to nearest is symmetric under negation), so a quarter
+// turn after the rotation costs no instruction.
+template <typename V, typename R> __device__ __forceinline__ R rot_re(V a, R cm, R s, R g)
+{
+    return fma_rn(g * a.x, cm, fma_rn(-g * a.y, s, g * a.x));
+}
+template <typename V, typename R> __device__ __forceinline__ R rot_im(V a, R cm, R s, R g)
+{
+    return fma_rn(g * a.y, cm, fma_rn(g * a.x, s, g * a.y));
+}
+
+#if RTK_ROT_SMALL
+// exp(DIR * 2 pi i k / 16), k a constant after unrolling.  k = 4q + j with
+// j in {-1, 0, 1, 2}: a rotation by j pi/8, then q quarter turns.
+template <int DIR, typename V>
+__device__ __forceinline__ V rot16(V a, int k)
+{
+    using R = typename real_of<V>::type;
+    using K = Rot16Const<R>;
+    k &= 15;
+    const int j = (k & 3) == 3 ? -1 : (k & 3);
+    if (j == 0) return quarter<DIR>(a, k >> 2);
+    const int q = ((k - j) >> 2) & 3;
+    const R cm = j == 2 ? K::cm4 : K::cm8;
+    const R s = (j < 0) == (DIR > 0) ? -(j == 2 ? K::s4 : K::s8) : (j == 2 ? K::s4 : K::s8);
+    // (DIR i)^q (P + i Q): q = 0: (P, Q); 2: (-P, -Q); DIR i: (-Q, P); -DIR i: (Q, -P).
+    if (q == 0) return cmk<V>(rot_re(a, cm, s, R(1)), rot_im(a, cm, s, R(1)));
+    if (q == 2) return cmk<V>(rot_re(a, cm, s, R(-1)), rot_im(a, cm, s, R(-1)));
+    if ((q == 1) == (DIR > 0)) return cmk<V>(rot_im(a, cm, s, R(-1)), rot_re(a, cm, s, R(1)));
+    return cmk<V>(rot_im(a, cm, s, R(1)), rot_re(a, cm, s, R(-1)));
+}
+#else
+// exp(DIR * 2 pi i k / 16) from the rounded (cos, sin) pairs.
 template <int DIR, typename V>
 __device__ __forceinline__ V rot16(V a, int k)
 {
     using R = typename real_of<V>::type;
     k &= 15;
-    if (k == 0) return a;
-    if (k == 4) return DIR > 0 ? cmk<V>(-a.y, a.x) : cmk<V>(a.y, -a.x);
-    if (k == 8) return cmk<V>(-a.x, -a.y);
-    if (k == 12) return DIR > 0 ? cmk<V>(a.y, -a.x) : cmk<V>(-a.y, a.x);
+    if ((k & 3) == 0) return quarter<DIR>(a, k >> 2);
     const R c8 = R(0.92387953251128675613), s8 = R(0.38268343236508977173), r2 = R(0.70710678118654752440);
     const R C[16] = {R(1), c8, r2, s8, R(0), -s8, -r2, -c8, R(-1), -c8, -r2, -s8, R(0), s8, r2, c8};
     const R S[16] = {R(0), s8, r2, c8, R(1), c8, r2, s8, R(0), -s8, -r2, -c8, R(-1), -c8, -r2, -s8};
     const R c = C[k], s = DIR > 0 ? S[k] : -S[k];
     return cmk<V>(a.x * c - a.y * s, a.x * s + a.y * c);
 }
+#endif
+
+#ifndef RTK_DFT44
+#define RTK_DFT44 1
+#endif
+
+// In-place radix-4 DFT, outputs in natural order: y_k = sum_j a_j (DIR i)^(jk).
+template <int DIR, typename V> __device__ __forceinline__ void dft4(V &a0, V &a1, V &a2, V &a3)
+{
+    const V t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), d = csub(a1, a3);
+    const V t3 = DIR > 0 ? cmk<V>(-d.y, d.x) : cmk<V>(d.y, -d.x);  // DIR i (a1 - a3)
+    a0 = cadd(t0, t2);
+    a1 = cadd(t1, t3);
+    a2 = csub(t0, t2);
+    a3 = csub(t1, t3);
+}
 
 // In-register DFT of size RAD (2, 4, 8, 16): X[k] = sum_j x[j] exp(DIR 2 pi i jk/RAD).
-// Radix-2 decimation in frequency, then a compile-time reordering (register
-// renaming) back to natural order.
+// Size 16 is split 4 x 4 (j = 4 j1 + j2, k = k1 + 4 k2): radix-4 DFTs over
+// j1, the factors exp(DIR 2 pi i j2 k1 / 16), radix-4 DFTs over j2; eight
+// non-trivial rotations where four radix-2 stages need ten.  The other sizes
+// are radix-2 decimation in frequency.  Both end with a compile-time
+// reordering (register renaming) back to natural order.
 template <int RAD, int DIR, typename V>
 __device__ __forceinline__ void dft(V (&v)[RAD])
 {
+#if RTK_DFT44
+    if constexpr (RAD == 16) {
+#pragma unroll
+        for (int j2 = 0; j2 < 4; ++j2) dft4<DIR>(v[j2], v[4 + j2], v[8 + j2], v[12 + j2]);
+#pragma unroll
+        for (int j2 = 1; j2 < 4; ++j2)
+#pragma unroll
+            for (int k1 = 1; k1 < 4; ++k1) v[j2 + 4 * k1] = rot16<DIR>(v[j2 + 4 * k1], j2 * k1);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) dft4<DIR>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+        V t[16];
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) t[k1 + 4 * k2] = v[4 * k1 + k2];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = t[k];
+        return;
+    }
+#endif
 #pragma unroll
     for (int half = RAD / 2; half >= 1; half >>= 1) {
 #pragma unroll

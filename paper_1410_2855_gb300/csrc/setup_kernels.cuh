@@ -10,6 +10,43 @@
 
 namespace rtk {
 
+#ifndef RTK_UNIT_TABLES
+#define RTK_UNIT_TABLES 1
+#endif
+
+// Stores the FP64 factor (re, im) of squared modulus mod2 in the path's
+// precision.  For FP32, of the (at most four) pairs formed from the floats
+// just below and above re and im, the one whose squared modulus is closest
+// to mod2 (ties keep round-to-nearest); each component stays within one ulp.
+// The tables are applied to the same paths every bounce, so a modulus that
+// rounding left above or below 1 would scale those paths' power by the same
+// factor each time; this keeps that factor within about 1e-8 of exact.
+template <typename V> __device__ __forceinline__ V store_factor(double re, double im, double mod2)
+{
+    (void)mod2;
+    return cmk<V>(re, im);
+}
+#if RTK_UNIT_TABLES
+template <> __device__ __forceinline__ float2 store_factor<float2>(double re, double im, double mod2)
+{
+    const float rc[2] = {__double2float_rn(re), __double2float_rd(re) == __double2float_rn(re) ? __double2float_ru(re)
+                                                                                               : __double2float_rd(re)};
+    const float ic[2] = {__double2float_rn(im), __double2float_rd(im) == __double2float_rn(im) ? __double2float_ru(im)
+                                                                                               : __double2float_rd(im)};
+    float2 best = make_float2(rc[0], ic[0]);
+    double err = fabs((double)rc[0] * rc[0] + (double)ic[0] * ic[0] - mod2);
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            const double e = fabs((double)rc[a] * rc[a] + (double)ic[b] * ic[b] - mod2);
+            if (e < err) {
+                err = e;
+                best = make_float2(rc[a], ic[b]);
+            }
+        }
+    return best;
+}
+#endif
+
 // Per-axis propagator h[k] = exp(-i pi alpha m^2) / n, m the signed
 // frequency of bin k (the 1-D factor of the transfer function of eq.
 // limit_of_operators_renorm_final; the 1/n carries the inverse transform's
@@ -30,7 +67,7 @@ __global__ void k_prop_table(int n, double alpha, V *h)
     double sp, cp;
     sincospi(t, &sp, &cp);
     const double inv = 1.0 / (double)n;
-    h[k] = cmk<V>(cp * inv, -sp * inv);
+    h[k] = store_factor<V>(cp * inv, -sp * inv, inv * inv);
 }
 
 // Phase of the complex aperture (eq. complex_aperture2) as the library
@@ -67,7 +104,7 @@ __global__ void k_lens_table(int n, double c_over_pi, int edge, int taper, V *le
     double sp, cp;
     sincospi(lens_turns(c_over_pi, x * x), &sp, &cp);
     const double a = aperture_modulus(j, n, edge, taper);
-    lens[j] = cmk<V>(a * cp, -a * sp);
+    lens[j] = store_factor<V>(a * cp, -a * sp, a * a);
 }
 
 // Full aperture factors A(x) A(y) exp(-i (c (x^2 + y^2) + psi[y n + x])); psi may be null.
@@ -85,7 +122,7 @@ __global__ void k_phase_table(int n, double c_over_pi, int edge, int taper, cons
         if (psi) sincos(psi[i], &sr, &cr);
         const double a = aperture_modulus(x, n, edge, taper) * aperture_modulus(y, n, edge, taper);
         // exp(-i (a + b)) = (cos a cos b - sin a sin b) - i (sin a cos b + cos a sin b)
-        phase[i] = cmk<V>(a * (cl * cr - sl * sr), -a * (sl * cr + cl * sr));
+        phase[i] = store_factor<V>(a * (cl * cr - sl * sr), -a * (sl * cr + cl * sr), a * a);
     }
 }
 
@@ -165,7 +202,7 @@ __global__ void k_twiddles(int logn, int total, V *tw)
     const int r = local / Ns + 1, j = local % Ns;
     double s, c;
     sincospi(2.0 * (double)((long long)r * j) / ((double)Ns * R), &s, &c);
-    tw[e] = cmk<V>(c, -s);
+    tw[e] = store_factor<V>(c, -s, 1.0);
 }
 
 __host__ __device__ inline int twiddle_count(int logn)

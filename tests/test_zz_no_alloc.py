@@ -25,7 +25,8 @@ def rel(a, b):
 @pytest.mark.parametrize("n, fresnel, g0, T1, R, z_over_F, taper_px, relax",
                          [(256, 100.0, 0.3, 1000.0, 0.9, 0.0, 0, 0),
                           (256, 100.0, 0.3, 1000.0, 0.9, 0.3, 5, 1),
-                          (2048, 1000.0, 0.3, 1e4, 0.9, 0.0, 0, 0)])
+                          (2048, 1000.0, 0.3, 1e4, 0.9, 0.0, 0, 0),
+                          (4096, 4000.0, 0.3, 1e4, 0.9, 0.0, 0, 0)])      # RT_NOALLOC_MAX_N
 def test_noalloc_matches_handle_path_on_two_calls(n, fresnel, g0, T1, R, z_over_F, taper_px, relax):
     import torch
 
