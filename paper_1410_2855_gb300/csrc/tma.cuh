@@ -1,6 +1,6 @@
 // Inline-PTX wrappers for the asynchronous copy engine (TMA) and shared-memory
 // mbarriers used by the persistent sweeps: 1-D bulk copies of contiguous rows,
-// 2-D tensor-map tile copies of column strips, and bounded waits.
+// 2-D tensor-map tile loads of column strips, and bounded waits.
 #pragma once
 
 #include <cuda.h>
@@ -88,31 +88,6 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         "[%4];" ::"r"(smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
-}
-
-// 2-D tile store through a tensor map (shared -> global), tracked by the
-// issuing thread's bulk-async group.
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, const void *src)
-{
-    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
-                     reinterpret_cast<uint64_t>(map)),
-                 "r"(x), "r"(y), "r"(smem_u32(src))
-                 : "memory");
-}
-
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-
-// Wait until the issuing thread's committed bulk stores have finished reading
-// shared memory (the source may then be overwritten).
-__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-
-// Wait until the issuing thread's committed bulk stores are complete.
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-
-// Barrier over `count` threads (a multiple of 32) on hardware barrier `id`.
-__device__ __forceinline__ void named_barrier(int id, int count)
-{
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 __host__ __device__ constexpr size_t round128(size_t b) { return (b + 127) / 128 * 128; }
