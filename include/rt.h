@@ -353,7 +353,10 @@ rt_status rt_batch_destroy(rt_batch *b);
  * size share each launch; a request stops exactly at its own bounce count),
  * then retires finished requests, copying each final field to the buffer
  * given at submission.  State stays on the device between rounds.  A
- * request's result is the same as running it alone on a handle. */
+ * request's result is the same as running it alone on a handle.  A request
+ * whose set-up fails waits for room while others run; if it still cannot be
+ * placed with nothing else resident (every idle slot released), its result
+ * is posted at once with RT_ENOMEM (allocation failed) or RT_ECUDA. */
 typedef struct rt_server rt_server;
 
 enum { RT_SERVE_FIFO = 0, RT_SERVE_SHORTEST_FIRST = 1 };
@@ -372,7 +375,7 @@ typedef struct {
 
 typedef struct {
     long long id;             /* from rt_serve_submit */
-    int status;               /* RT_OK, or the error that ended the request */
+    int status;               /* RT_OK, or the error that ended the request (RT_ECANCELED, RT_ENOMEM, ...) */
     int n;                    /* grid side */
     long long bounces;        /* bounces run */
     double mean_intensity;    /* <|E|^2> after the last bounce */
@@ -460,6 +463,10 @@ rt_status rt_step_noalloc(int n, double fresnel, const rt_pump *pump, double g0,
  * negative value cancels a pending failure.  The failure is produced on the
  * host before any device call.  Process-wide; returns RT_OK. */
 rt_status rt_debug_fail_alloc(int after);
+/* The same for `count` consecutive allocations starting with the after-th
+ * (count < 0: every one from the after-th on, until cancelled by a negative
+ * `after`).  rt_debug_fail_alloc(a) is rt_debug_fail_alloc_n(a, 1). */
+rt_status rt_debug_fail_alloc_n(int after, int count);
 
 /* Release every device buffer and graph of the handle (NULL is accepted). */
 rt_status rt_destroy(rt_handle *h);

@@ -195,4 +195,70 @@ cudaError_t enqueue_classes_bounce(const std::vector<ClassLaunch> &cls, int *err
     return cudaSuccess;
 }
 
+
+cudaError_t branches_prepare(Branches &br, size_t nclasses)
+{
+    const size_t want = nclasses > 1 ? nclasses - 1 : 0;
+    if (want > 0 && !br.fork) {
+        cudaError_t e = cudaEventCreateWithFlags(&br.fork, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+    }
+    while (br.streams.size() < want) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            if (st) cudaStreamDestroy(st);
+            return e;
+        }
+        br.streams.push_back(st);
+        br.join.push_back(ev);
+    }
+    return cudaSuccess;
+}
+
+void branches_free(Branches &br)
+{
+    for (cudaStream_t st : br.streams) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : br.join) cudaEventDestroy(ev);
+    if (br.fork) cudaEventDestroy(br.fork);
+    br.streams.clear();
+    br.join.clear();
+    br.fork = nullptr;
+}
+
+static cudaError_t enqueue_class_chain(const ClassLaunch &c, int *err, long long k, cudaStream_t s)
+{
+    cudaError_t e = cudaSuccess;
+    for (long long i = 0; i < k && e == cudaSuccess; ++i) {
+        e = launch_col_batch32(c.logn, c.colC, c.d_res, c.nres, c.tw, err, s);
+        if (e == cudaSuccess) e = launch_row_batch32(c.logn, c.d_res, c.nres, c.tw, err, s);
+    }
+    return e;
+}
+
+cudaError_t capture_class_bounces(const std::vector<ClassLaunch> &cls, int *err, long long k, cudaStream_t cap,
+                                  Branches &br)
+{
+    if (cls.empty()) return cudaSuccess;
+    if (cls.size() == 1) return enqueue_class_chain(cls[0], err, k, cap);
+    if (br.streams.size() < cls.size() - 1 || !br.fork) return cudaErrorInvalidValue;
+    cudaError_t e = cudaEventRecord(br.fork, cap);
+    if (e != cudaSuccess) return e;
+    size_t joined = 0;  // branches forked into the capture
+    for (size_t j = 1; j < cls.size() && e == cudaSuccess; ++j)
+        if ((e = cudaStreamWaitEvent(br.streams[j - 1], br.fork, 0)) == cudaSuccess) ++joined;
+    if (e == cudaSuccess) e = enqueue_class_chain(cls[0], err, k, cap);
+    for (size_t j = 1; j < cls.size() && e == cudaSuccess; ++j)
+        e = enqueue_class_chain(cls[j], err, k, br.streams[j - 1]);
+    // join every branch that was forked, whatever happened
+    for (size_t j = 0; j < joined; ++j) {
+        cudaError_t je = cudaEventRecord(br.join[j], br.streams[j]);
+        if (je == cudaSuccess) je = cudaStreamWaitEvent(cap, br.join[j], 0);
+        if (e == cudaSuccess) e = je;
+    }
+    return e;
+}
+
 }  // namespace rtk

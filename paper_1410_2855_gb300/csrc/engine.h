@@ -70,6 +70,23 @@ struct ClassLaunch {
 // One bounce of every class: all column sweeps, then all row sweeps.
 cudaError_t enqueue_classes_bounce(const std::vector<ClassLaunch> &cls, int *err, cudaStream_t s);
 
+// Side streams and fork/join events for capturing one graph branch per size
+// class.  Created before a capture (branches_prepare), freed by branches_free.
+struct Branches {
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+};
+cudaError_t branches_prepare(Branches &br, size_t nclasses);
+void branches_free(Branches &br);
+
+// Into the capture running on `cap`: k bounces of every class, each class's
+// chain of launches on its own branch (the classes' resonators are
+// independent, so their launches may overlap and fill each other's tails),
+// joined back into `cap`.  The joins are made even when a launch fails.
+cudaError_t capture_class_bounces(const std::vector<ClassLaunch> &cls, int *err, long long k, cudaStream_t cap,
+                                  Branches &br);
+
 // Device index guard.
 struct DeviceGuard {
     int prev = -1, want;

@@ -1,6 +1,7 @@
 // Batches of resonators (include/rt.h, rt_batch_*): slots grouped by grid
 // size; each bounce is one batched column sweep and one batched row sweep per
-// size class, captured as CUDA graphs of `chunk` bounces.  Each slot carries
+// size class, captured as CUDA graphs of `chunk` bounces with one branch per
+// size class (the classes' launches overlap).  Each slot carries
 // a stop-at-bounce target that the kernels honour, so slots with different
 // remaining work share the same launches and graphs.
 #include <climits>
@@ -48,6 +49,7 @@ struct rt_batch {
     int *err = nullptr;      // batch-wide error word (copy-engine timeouts)
     size_t shared_bytes = 0;
     std::map<long long, cudaGraphExec_t> graphs;
+    Branches branches;       // one graph branch per size class
 };
 
 namespace {
@@ -80,6 +82,7 @@ void release(rt_batch *b)
     if (b->ctl) cudaFree(b->ctl);
     if (b->err) cudaFree(b->err);
     if (b->capture) cudaStreamDestroy(b->capture);
+    branches_free(b->branches);
 }
 
 cudaError_t batch_graph(rt_batch *b, long long k, cudaGraphExec_t *out)
@@ -93,9 +96,9 @@ cudaError_t batch_graph(rt_batch *b, long long k, cudaGraphExec_t *out)
     for (SizeClass &c : b->classes)
         if ((e = prepare_batch32(c.logn, c.colC)) != cudaSuccess) return e;
     const std::vector<ClassLaunch> cl = launches(b);
+    if ((e = branches_prepare(b->branches, cl.size())) != cudaSuccess) return e;
     if ((e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
-    cudaError_t le = cudaSuccess;
-    for (long long i = 0; i < k && le == cudaSuccess; ++i) le = enqueue_classes_bounce(cl, b->err, b->capture);
+    const cudaError_t le = capture_class_bounces(cl, b->err, k, b->capture, b->branches);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(b->capture, &g);
     if (le != cudaSuccess) e = le;

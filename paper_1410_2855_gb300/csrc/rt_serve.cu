@@ -10,7 +10,8 @@
 // own bounce count because its slot's target is reached), waits, reads the
 // per-slot counters, and retires finished requests: their final field is
 // copied to the caller's buffer and a result is posted.  Device state stays
-// resident between rounds.
+// resident between rounds.  A request that cannot be placed even with
+// nothing resident fails (its result is posted) instead of waiting.
 #include <algorithm>
 #include <chrono>
 #include <climits>
@@ -83,6 +84,7 @@ struct rt_server {
     // worker-only state
     std::map<int, SClass> classes;
     std::map<std::string, cudaGraphExec_t> graphs;
+    Branches branches;                // one graph branch per size class
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 };
@@ -128,14 +130,29 @@ void make_room(rt_server *s, long long need, int keep_logn)
     }
 }
 
-// Try to place a request; returns true if admitted.
-bool admit(rt_server *s, Request &r)
+// Release every idle slot that can go (trailing idle slots of each class).
+void release_idle(rt_server *s)
 {
+    for (auto &kv : s->classes) {
+        SClass &c = kv.second;
+        while (!c.slots.empty() && !c.slots.back().busy) {
+            s->resident -= (long long)c.slots.back().buf.bytes;
+            slot_free(&c.slots.back().buf);
+            c.slots.pop_back();
+        }
+    }
+}
+
+// Try to place a request; returns true if admitted.  A CUDA failure on the
+// way (set-up of its size class, slot allocation or start) is left in *why.
+bool admit(rt_server *s, Request &r, cudaError_t *why)
+{
+    *why = cudaSuccess;
     const int logn = log2_of(r.job.n);
     auto it = s->classes.find(logn);
     if (it == s->classes.end()) {
         SClass c;
-        if (class_init(s, c, logn) != cudaSuccess) return false;
+        if ((*why = class_init(s, c, logn)) != cudaSuccess) return false;
         it = s->classes.emplace(logn, c).first;
     }
     SClass &c = it->second;
@@ -151,14 +168,14 @@ bool admit(rt_server *s, Request &r)
         if (s->resident + need > s->opts.budget_bytes) make_room(s, need, logn);
         if (s->resident + need > s->opts.budget_bytes) return false;
         SSlot ns;
-        if (slot_alloc(r.job.n, kHistCap, false, false, &ns.buf) != cudaSuccess) return false;
+        if ((*why = slot_alloc(r.job.n, kHistCap, false, false, &ns.buf)) != cudaSuccess) return false;
         s->resident += (long long)ns.buf.bytes;
         c.slots.push_back(ns);
         idx = (int)c.slots.size() - 1;
     }
     SSlot &sl = c.slots[idx];
-    if (slot_start(r.job, sl.buf, c.colC, c.tw, &c.ctl[idx], c.d_res + idx, kHistCap, r.bounces, s->stream) !=
-        cudaSuccess)
+    if ((*why = slot_start(r.job, sl.buf, c.colC, c.tw, &c.ctl[idx], c.d_res + idx, kHistCap, r.bounces,
+                           s->stream)) != cudaSuccess)
         return false;
     sl.target = r.bounces;
     sl.busy = true;
@@ -183,10 +200,11 @@ cudaError_t round_graph(rt_server *s, cudaGraphExec_t *out)
         *out = it->second;
         return cudaSuccess;
     }
-    cudaError_t e = cudaStreamBeginCapture(s->capture, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e = branches_prepare(s->branches, cl.size());
     if (e != cudaSuccess) return e;
-    cudaError_t le = cudaSuccess;
-    for (int b = 0; b < s->opts.chunk && le == cudaSuccess; ++b) le = enqueue_classes_bounce(cl, s->d_err, s->capture);
+    e = cudaStreamBeginCapture(s->capture, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    const cudaError_t le = capture_class_bounces(cl, s->d_err, s->opts.chunk, s->capture, s->branches);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(s->capture, &g);
     if (le != cudaSuccess) e = le;
@@ -366,12 +384,31 @@ void worker_main(rt_server *s)
         // admission, oldest first; what does not fit goes back to the queue front
         std::vector<Request> waiting;
         long long admitted = 0;
+        cudaError_t why = cudaSuccess;
         for (Request &r : fresh) {
-            if (admit(s, r)) ++admitted;
+            if (admit(s, r, &why)) ++admitted;
             else waiting.push_back(r);
+        }
+        // Nothing resident and nothing admitted: no later round can free room,
+        // so release every idle slot and try once more.  A request that still
+        // cannot be placed before anything else is admitted has failed
+        // (RT_ENOMEM, or RT_ECUDA after another CUDA error) rather than wait
+        // for ever.
+        std::vector<std::pair<Request, int>> failed;
+        if (!waiting.empty() && admitted == 0 && !any_running) {
+            release_idle(s);
+            std::vector<Request> still;
+            for (Request &r : waiting) {
+                if (admit(s, r, &why)) ++admitted;
+                else if (admitted == 0)
+                    failed.emplace_back(r, why == cudaErrorMemoryAllocation ? RT_ENOMEM : RT_ECUDA);
+                else still.push_back(r);
+            }
+            waiting.swap(still);
         }
         {
             std::lock_guard<std::mutex> lk(s->mu);
+            for (auto &f : failed) post_unrun_locked(s, f.first, s->cancel.count(f.first.id) ? RT_ECANCELED : f.second);
             s->running += admitted;
             for (auto it = waiting.rbegin(); it != waiting.rend(); ++it) {
                 if (s->cancel.count(it->id)) post_unrun_locked(s, *it, RT_ECANCELED);
@@ -400,6 +437,7 @@ void release(rt_server *s)
     }
     if (s->d_err) cudaFree(s->d_err);
     if (s->capture) cudaStreamDestroy(s->capture);
+    branches_free(s->branches);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
 }
 

@@ -137,6 +137,7 @@ def lib() -> ctypes.CDLL:
             "rt_serve_stats": [vp, ctypes.POINTER(rt_serve_stats_t)],
             "rt_serve_destroy": [vp],
             "rt_debug_fail_alloc": [i],
+            "rt_debug_fail_alloc_n": [i, i],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -257,6 +258,12 @@ def rt_read_spectrum(h, dst):
 def rt_debug_fail_alloc(after: int):
     """Test hook: the after-th device allocation from now on fails once (-1 cancels)."""
     _check(lib().rt_debug_fail_alloc(int(after)), "rt_debug_fail_alloc")
+
+
+def rt_debug_fail_alloc_n(after: int, count: int):
+    """Fault injection (test hook): `count` consecutive device allocations
+    starting with the after-th fail as out of memory (count < 0: all of them)."""
+    _check(lib().rt_debug_fail_alloc_n(int(after), int(count)), "rt_debug_fail_alloc_n")
 
 
 def rt_set_field_pattern(h, pattern: rt_pattern):

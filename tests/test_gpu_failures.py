@@ -3,7 +3,8 @@ hangs the device): an injected allocation failure at every allocation of a
 handle's and a batch's set-up returns RT_ENOMEM and releases what was
 allocated; a resonator whose gain diverges reports RT_ENUMERIC from its
 device error word and stays usable for reads; the serving loop admits a
-request once a failed allocation is retried."""
+request once a failed allocation is retried, and posts RT_ENOMEM for a
+request that cannot be placed even with nothing else resident."""
 import numpy as np
 import pytest
 import torch
@@ -74,6 +75,32 @@ def test_served_request_is_admitted_after_a_failed_allocation():
         r = {x.id: x for x in srv.poll()}[i]
         assert r.status == 0 and r.bounces == 12
     rt.rt_debug_fail_alloc(-1)
+    with rt.Resonator.from_params(p, chunk=0) as h:
+        h.step(12)
+        assert np.array_equal(out, h.field())
+
+
+def test_served_request_that_cannot_be_placed_fails_instead_of_waiting():
+    # Every allocation fails: with nothing else resident no later round could
+    # make room, so the request's result is posted at once with RT_ENOMEM
+    # (and drain returns) instead of the request waiting for ever.  The server
+    # keeps working once allocations succeed again.
+    p = wl.Resonator(n=128, fresnel=50.0, g0=0.2, T1=800.0, R=0.9, seed=10)
+    out = np.zeros((128, 128), np.complex64)
+    with rt.Server(chunk=8, budget_bytes=1 << 26) as srv:
+        rt.rt_debug_fail_alloc_n(0, -1)
+        try:
+            i = srv.submit(p, 12, out)
+            srv.drain(60)
+            r = {x.id: x for x in srv.poll()}[i]
+        finally:
+            rt.rt_debug_fail_alloc_n(-1, 0)
+        assert r.status == rt.RT_ENOMEM and r.bounces == 0 and r.admit_s < 0
+        assert not out.any()
+        j = srv.submit(p, 12, out)
+        srv.drain(120)
+        r = {x.id: x for x in srv.poll()}[j]
+        assert r.status == 0 and r.bounces == 12
     with rt.Resonator.from_params(p, chunk=0) as h:
         h.step(12)
         assert np.array_equal(out, h.field())
