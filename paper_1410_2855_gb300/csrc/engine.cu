@@ -196,9 +196,31 @@ cudaError_t enqueue_classes_bounce(const std::vector<ClassLaunch> &cls, int *err
 }
 
 
-cudaError_t branches_prepare(Branches &br, size_t nclasses)
+// The launch sets that get a branch each: every class, split into up to
+// `split` parts of consecutive resonators.  Measured on GB300 for batches
+// (256 resonators of side 256/512/1024; 64 of side 1024): one part 183k and
+// 72k round trips/s, two 198k and 80k, three 204k and 89k, four 201k and 89k.
+// Serving rounds (a few requests per class): one part 49k round trips/s,
+// three 44k.
+static std::vector<ClassLaunch> class_parts(const std::vector<ClassLaunch> &cls, int split)
 {
-    const size_t want = nclasses > 1 ? nclasses - 1 : 0;
+    std::vector<ClassLaunch> out;
+    for (const ClassLaunch &c : cls) {
+        const int parts = c.nres < split ? (c.nres > 0 ? c.nres : 1) : (split > 0 ? split : 1);
+        int first = 0;
+        for (int q = 0; q < parts; ++q) {
+            const int cnt = c.nres / parts + (q < c.nres % parts ? 1 : 0);
+            out.push_back({c.logn, c.colC, c.d_res + first, cnt, c.tw});
+            first += cnt;
+        }
+    }
+    return out;
+}
+
+cudaError_t branches_prepare(Branches &br, const std::vector<ClassLaunch> &cls, int split)
+{
+    const size_t nb = class_parts(cls, split).size();
+    const size_t want = nb > 1 ? nb - 1 : 0;
     if (want > 0 && !br.fork) {
         cudaError_t e = cudaEventCreateWithFlags(&br.fork, cudaEventDisableTiming);
         if (e != cudaSuccess) return e;
@@ -238,9 +260,10 @@ static cudaError_t enqueue_class_chain(const ClassLaunch &c, int *err, long long
     return e;
 }
 
-cudaError_t capture_class_bounces(const std::vector<ClassLaunch> &cls, int *err, long long k, cudaStream_t cap,
-                                  Branches &br)
+cudaError_t capture_class_bounces(const std::vector<ClassLaunch> &classes, int *err, long long k, cudaStream_t cap,
+                                  Branches &br, int split)
 {
+    const std::vector<ClassLaunch> cls = class_parts(classes, split);
     if (cls.empty()) return cudaSuccess;
     if (cls.size() == 1) return enqueue_class_chain(cls[0], err, k, cap);
     if (br.streams.size() < cls.size() - 1 || !br.fork) return cudaErrorInvalidValue;

@@ -70,22 +70,29 @@ struct ClassLaunch {
 // One bounce of every class: all column sweeps, then all row sweeps.
 cudaError_t enqueue_classes_bounce(const std::vector<ClassLaunch> &cls, int *err, cudaStream_t s);
 
-// Side streams and fork/join events for capturing one graph branch per size
-// class.  Created before a capture (branches_prepare), freed by branches_free.
+// Side streams and fork/join events for capturing graph branches: one per
+// size class, or per part of one (class_parts).  Created before a capture
+// (branches_prepare), freed by branches_free.
 struct Branches {
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> join;
     cudaEvent_t fork = nullptr;
 };
-cudaError_t branches_prepare(Branches &br, size_t nclasses);
+cudaError_t branches_prepare(Branches &br, const std::vector<ClassLaunch> &cls, int split);
 void branches_free(Branches &br);
 
-// Into the capture running on `cap`: k bounces of every class, each class's
-// chain of launches on its own branch (the classes' resonators are
-// independent, so their launches may overlap and fill each other's tails),
-// joined back into `cap`.  The joins are made even when a launch fails.
+// Into the capture running on `cap`: k bounces of every class, each class
+// split into up to `split` parts of consecutive resonators, each part's chain
+// of launches on its own stream (the resonators are independent, so the
+// launches may overlap and fill each other's tails), joined back into `cap`.
+// The joins are made even when a launch fails.
 cudaError_t capture_class_bounces(const std::vector<ClassLaunch> &cls, int *err, long long k, cudaStream_t cap,
-                                  Branches &br);
+                                  Branches &br, int split);
+
+// Parts per size class: batches (many resonators per class) and serving
+// rounds (few per class, where more, smaller launches cost more than they fill).
+constexpr int kBatchSplit = 3;
+constexpr int kServeSplit = 1;
 
 // Device index guard.
 struct DeviceGuard {

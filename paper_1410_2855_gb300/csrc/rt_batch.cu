@@ -1,7 +1,7 @@
 // Batches of resonators (include/rt.h, rt_batch_*): slots grouped by grid
 // size; each bounce is one batched column sweep and one batched row sweep per
-// size class, captured as CUDA graphs of `chunk` bounces with one branch per
-// size class (the classes' launches overlap).  Each slot carries
+// size class, captured as CUDA graphs of `chunk` bounces with up to three
+// branches per size class (their launches overlap).  Each slot carries
 // a stop-at-bounce target that the kernels honour, so slots with different
 // remaining work share the same launches and graphs.
 #include <climits>
@@ -96,9 +96,9 @@ cudaError_t batch_graph(rt_batch *b, long long k, cudaGraphExec_t *out)
     for (SizeClass &c : b->classes)
         if ((e = prepare_batch32(c.logn, c.colC)) != cudaSuccess) return e;
     const std::vector<ClassLaunch> cl = launches(b);
-    if ((e = branches_prepare(b->branches, cl.size())) != cudaSuccess) return e;
+    if ((e = branches_prepare(b->branches, cl, kBatchSplit)) != cudaSuccess) return e;
     if ((e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
-    const cudaError_t le = capture_class_bounces(cl, b->err, k, b->capture, b->branches);
+    const cudaError_t le = capture_class_bounces(cl, b->err, k, b->capture, b->branches, kBatchSplit);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(b->capture, &g);
     if (le != cudaSuccess) e = le;

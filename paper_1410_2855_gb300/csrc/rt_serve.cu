@@ -200,11 +200,11 @@ cudaError_t round_graph(rt_server *s, cudaGraphExec_t *out)
         *out = it->second;
         return cudaSuccess;
     }
-    cudaError_t e = branches_prepare(s->branches, cl.size());
+    cudaError_t e = branches_prepare(s->branches, cl, kServeSplit);
     if (e != cudaSuccess) return e;
     e = cudaStreamBeginCapture(s->capture, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    const cudaError_t le = capture_class_bounces(cl, s->d_err, s->opts.chunk, s->capture, s->branches);
+    const cudaError_t le = capture_class_bounces(cl, s->d_err, s->opts.chunk, s->capture, s->branches, kServeSplit);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(s->capture, &g);
     if (le != cudaSuccess) e = le;
