@@ -41,6 +41,26 @@ def test_batch_slots_match_single_handles_bit_for_bit():
                 assert np.allclose(b.history(i, 23), r.history(23), rtol=1e-12)
 
 
+def test_class_split_across_graph_branches_keeps_every_slot_bit_identical():
+    # Five resonators of one size: a captured batch graph runs them as three
+    # branches of 2, 2 and 1 consecutive slots; with a second size class and
+    # a remainder of direct launches (10 = 2 x 4 + 2 bounces).
+    jobs = [wl.Resonator(n=128, fresnel=40.0 + 10 * k, g0=0.15 + 0.03 * k, T1=600.0 + 100 * k, R=0.9, seed=60 + k)
+            for k in range(5)] + [wl.Resonator(n=64, fresnel=25.0, g0=0.2, T1=700.0, R=0.95, seed=66)]
+    with rt.Batch(jobs, chunk=4, history_cap=16) as b:
+        for i, p in enumerate(jobs):
+            b.write_field(i, wl.smooth_field(p.n, 200 + i, 1.0, dtype=np.complex64))
+        b.step(10)
+        for i, p in enumerate(jobs):
+            with rt.Resonator.from_params(p, chunk=0) as r:
+                r.set_field(wl.smooth_field(p.n, 200 + i, 1.0, dtype=np.complex64))
+                r.step(10)
+                assert np.array_equal(b.field(i), r.field()), i
+                assert np.array_equal(b.inversion(i), r.inversion()), i
+                assert b.stats(i).bounces == 10
+                assert np.allclose(b.history(i, 10), r.history(10), rtol=1e-12)
+
+
 def test_bounce_budget_stops_a_slot_while_others_continue():
     with rt.Batch(MIX[:3], chunk=5) as b:
         b.step(4)
