@@ -75,6 +75,39 @@ def test_one_bounce_matches_oracle(precision, case, kind):
     assert float(np.linalg.norm(N1 - oN) / np.linalg.norm(oN)) <= TOL1[precision]
 
 
+EXTREMES = [  # (label, n, fresnel, g0, T1, R, edge, Isat, bounces)
+    ("T1=1", 64, 20.0, 0.3, 1.0, 0.9, 8, 1.0, 2),                 # the inversion follows the intensity at once
+    ("edge=n/2", 64, 20.0, 0.3, 500.0, 0.9, 32, 1.0, 2),          # every pixel absorbed
+    ("edge=0", 64, 20.0, 0.3, 500.0, 0.9, 0, 1.0, 3),
+    ("Isat=1e-6", 64, 20.0, 0.3, 1000.0, 0.9, 8, 1e-6, 1),        # deep saturation: N is driven far negative
+    ("Isat=1e30", 64, 20.0, 0.5, 1000.0, 0.95, 8, 1e30, 3),       # no saturation
+    ("NF=0.5", 128, 0.5, 0.2, 1000.0, 0.95, 8, 1.0, 3),           # alpha m^2 up to 5e3: phase wraps thousands of times
+    ("NF=1e5", 128, 1e5, 0.2, 1000.0, 0.95, 8, 1.0, 3),           # almost no diffraction
+    ("R=1e-6", 64, 20.0, 0.2, 1000.0, 1e-6, 8, 1.0, 2),           # the mirror takes 1e-3 of the amplitude
+]
+
+
+@pytest.mark.parametrize("precision", [FP32, FP64])
+@pytest.mark.parametrize("case", EXTREMES, ids=[c[0] for c in EXTREMES])
+def test_parameter_extremes_match_oracle(precision, case):
+    # The ends of the ranges the library accepts (T1 >= 1, 0 < R <= 1,
+    # 0 <= edge <= n/2, any Isat and Fresnel number > 0), a lasing-scale
+    # start, a few bounces: same bars as one bounce, scaled by the bounces.
+    _, n, fres, g0, T1, R, edge, Isat, nb = case
+    E0 = start_field("lasing", n, precision, 31 + n)
+    with gpu(n, fres, g0, T1, R, precision, edge=edge, Isat=Isat) as r:
+        r.set_field(E0)
+        r.step(nb)
+        E1, N1 = r.field(), r.inversion()
+    p = oparams(n, fres, g0, T1, R, edge=edge, Isat=Isat)
+    oE, oN, _ = orc.run(p, E0.astype(np.complex128), orc.pump(p), nb)
+    if edge == n // 2:
+        assert not np.any(E1) and not np.any(oE)        # exactly zero, as the oracle
+    else:
+        assert rel_l2(E1, oE) <= TOL1[precision] * nb
+    assert float(np.linalg.norm(N1 - oN) / np.linalg.norm(oN)) <= TOL1[precision] * nb
+
+
 @pytest.mark.parametrize("precision", [FP32, FP64])
 @pytest.mark.parametrize("case", CASES[1:5])
 def test_twenty_bounces_match_oracle(precision, case):
