@@ -56,6 +56,9 @@ def test_default_options(lib):
 @pytest.mark.parametrize("args", [
     dict(n=100), dict(n=16), dict(n=8192), dict(fresnel=0.0), dict(fresnel=float("nan")),
     dict(g0=-0.1), dict(T1=0.5), dict(R=0.0), dict(R=1.5),
+    # just past each end of the accepted ranges, and non-finite values
+    dict(n=2 ** 13), dict(fresnel=-1.0), dict(fresnel=float("inf")), dict(g0=float("nan")), dict(g0=float("inf")),
+    dict(T1=0.999999), dict(T1=float("inf")), dict(R=1.0 + 1e-12), dict(R=-0.5), dict(R=float("nan")),
 ])
 def test_create_rejects_bad_arguments_before_touching_the_device(lib, args):
     p = dict(n=64, fresnel=100.0, g0=0.2, T1=1000.0, R=0.95)
@@ -67,7 +70,9 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib, args):
 
 def test_create_rejects_bad_options(lib):
     h = ctypes.c_void_p()
-    for field, value in [("precision", 3), ("edge_px", -1), ("Isat", 0.0), ("history_cap", -5), ("chunk", -1),
+    for field, value in [("precision", 3), ("edge_px", -1), ("edge_px", 33), ("Isat", 0.0), ("Isat", float("nan")),
+                         ("Isat", float("inf")), ("noise_amp", -1e-6), ("noise_amp", float("nan")),
+                         ("pump_diam_over_window", 0.0), ("history_cap", -5), ("chunk", -1),
                          ("z_over_F", float("inf")), ("z_over_F", float("nan")), ("slices", -1), ("slices", 65),
                          ("taper_px", -1), ("taper_px", 33), ("relax", 2)]:
         o = rt.rt_opts_default()
