@@ -272,6 +272,25 @@ def test_super_gaussian_pump_profile():
     assert np.all(np.diff(N0[c, c:]) < 0)
 
 
+def test_super_gaussian_of_order_two_is_the_gaussian():
+    # order and radius are the caller's: order 2, radius 0.3 is g0 exp(-(r/0.3)^2)
+    n, g0 = 32, 0.2
+    N0 = orc.pump(orc.make_params(n, 0.01, g0, 10.0, 0.9, pump_order=2.0, pump_radius=0.3))
+    x = (np.arange(n) - n // 2) / (n // 2)
+    r2 = x[None, :] ** 2 + x[:, None] ** 2
+    assert np.max(np.abs(N0 - g0 * np.exp(-r2 / 0.09))) <= 1e-15
+
+
+def test_uniform_and_array_pumps():
+    n, g0 = 16, 0.3
+    assert np.all(orc.pump(orc.make_params(n, 0.01, g0, 10.0, 0.9, pump_kind=orc.PUMP_UNIFORM)) == g0)
+    prof = np.zeros((n, n))
+    prof[2, 11] = 1.0                                        # row 2, column 11: y = 2, x = 11
+    prof[5, :] = 0.5
+    N0 = orc.pump(orc.make_params(n, 0.01, g0, 10.0, 0.9, pump_kind=orc.PUMP_ARRAY, pump_profile=prof))
+    assert np.array_equal(N0, g0 * prof) and N0[2, 11] == g0 and N0[11, 2] == 0.0
+
+
 # --------------------------------------------------------------------- noise
 
 def test_splitmix64_published_vectors():
