@@ -329,6 +329,21 @@ def test_spectrum_peak_folding_and_ring():
     assert orc.spectrum_peak(S2, ring=4)[:2] == (-3, 5)
 
 
+def test_spectrum_parseval_and_history_is_the_mean_intensity():
+    # sum_m S(m) = n^2 sum_j |E_j|^2 for the unnormalised transform; the
+    # reported mean intensity of a bounce is <|E|^2> of the field it returns.
+    n = 32
+    rng = np.random.default_rng(5)
+    E = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    S = orc.spectrum(E)
+    assert np.all(S >= 0.0)
+    assert abs(S.sum() - n * n * np.sum(np.abs(E) ** 2)) <= 1e-12 * S.sum()
+    p = orc.make_params(n, 0.05, 0.3, 200.0, 0.9)
+    for nb in (1, 4):
+        E1, _, hist = orc.run(p, E, orc.pump(p), nb)
+        assert len(hist) == nb and abs(hist[-1] - np.mean(np.abs(E1) ** 2)) <= 1e-14 * hist[-1]
+
+
 # ----------------------------------------------------- the paper's own numbers
 
 def test_paper_parameters_give_the_quoted_fresnel_range_and_period():
