@@ -109,6 +109,37 @@ def test_parameter_extremes_match_oracle(precision, case):
 
 
 @pytest.mark.parametrize("precision", [FP32, FP64])
+@pytest.mark.parametrize("pump", ["array", "order4", "uniform"])
+def test_pump_forms_match_oracle(precision, pump):
+    # The N0-table path (an array pump, a super-Gaussian of order other than
+    # 10) and the uniform pump, after 1 and 20 bounces.
+    n, fres, g0, T1, R = 128, 50.0, 0.3, 500.0, 0.9
+    prof = np.random.default_rng(17).uniform(0.0, 1.0, size=(n, n))
+    kw = {"array": dict(pump_kind=rt.RT_PUMP_ARRAY, pump_profile=prof),
+          "order4": dict(pump_order=4.0, pump_radius=0.6),
+          "uniform": dict(pump_kind=rt.RT_PUMP_UNIFORM)}[pump]
+    okw = {"array": dict(pump_kind=orc.PUMP_ARRAY, pump_profile=prof),
+           "order4": dict(pump_order=4.0, pump_radius=0.6),
+           "uniform": dict(pump_kind=orc.PUMP_UNIFORM)}[pump]
+    op = orc.make_params(n, orc.alpha_from_fresnel(fres, 0.8), g0, T1, R, **okw)
+    E0 = start_field("lasing", n, precision, 41)
+    with gpu(n, fres, g0, T1, R, precision, **kw) as r:
+        assert np.allclose(r.inversion(), orc.pump(op), rtol=1e-6, atol=1e-12)   # N starts at N0
+        r.set_field(E0)
+        r.step(20)
+        E20, N20 = r.field(), r.inversion()
+    E1o, N1o, _ = orc.run(op, E0.astype(np.complex128), orc.pump(op), 1)
+    E20o, N20o, _ = orc.run(op, E1o, N1o, 19)
+    assert rel_l2(E20, E20o) <= TOL20[precision]
+    assert float(np.linalg.norm(N20 - N20o) / np.linalg.norm(N20o)) <= TOL20[precision]
+    with gpu(n, fres, g0, T1, R, precision, **kw) as r:
+        r.set_field(E0)
+        r.step(1)
+        assert rel_l2(r.field(), E1o) <= TOL1[precision]
+        assert float(np.linalg.norm(r.inversion() - N1o) / np.linalg.norm(N1o)) <= TOL1[precision]
+
+
+@pytest.mark.parametrize("precision", [FP32, FP64])
 @pytest.mark.parametrize("case", CASES[1:5])
 def test_twenty_bounces_match_oracle(precision, case):
     n, fres, g0, T1, R = case
