@@ -344,6 +344,21 @@ def test_spectrum_parseval_and_history_is_the_mean_intensity():
         assert len(hist) == nb and abs(hist[-1] - np.mean(np.abs(E1) ** 2)) <= 1e-14 * hist[-1]
 
 
+def test_threaded_oracle_is_bit_identical_to_one_thread():
+    # The host baseline runs the oracle on all cores; threads split rows and
+    # columns of the transforms and rows of the local map, so every value is
+    # computed by the same operations whatever the thread count.
+    n = 64
+    p = orc.make_params(n, 0.05, 0.3, 300.0, 0.9, z_over_F=0.2, taper=3, relax=1)
+    E0 = orc.noise(n, 9, 1.0)
+    N0 = orc.initial_inversion(p)
+    one = orc.run(p, E0, N0, 3, nthreads=1)
+    for t in (2, 5):
+        many = orc.run(p, E0, N0, 3, nthreads=t)
+        assert all(np.array_equal(a, b) for a, b in zip(one, many)), t
+    assert np.array_equal(orc.fft2(E0, nthreads=1), orc.fft2(E0, nthreads=3))
+
+
 # ----------------------------------------------------- the paper's own numbers
 
 def test_paper_parameters_give_the_quoted_fresnel_range_and_period():
