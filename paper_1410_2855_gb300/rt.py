@@ -553,6 +553,9 @@ class Server:
         """Queue a request; field_out (numpy complex64 n x n or a device
         tensor) receives the final field."""
         j = job if isinstance(job, rt_job) else job_from_params(job)
+        if field_out is not None and _nbytes(field_out) != j.n * j.n * 8:
+            # the library writes n*n complex64 values there, later, from its worker
+            raise ValueError(f"field_out must hold {j.n}x{j.n} complex64 values")
         rid = ctypes.c_longlong()
         _check(lib().rt_serve_submit(self.h, ctypes.byref(j), int(n_bounces),
                                      _ptr(field_out) if field_out is not None else None, ctypes.byref(rid)),

@@ -148,3 +148,18 @@ def test_server_rejects_bad_options_before_touching_the_device(lib):
         o = rt.rt_serve_opts_default()
         setattr(o, field, value)
         assert lib.rt_serve_create(ctypes.byref(o), ctypes.byref(h)) == rt.RT_EINVAL and not h.value
+
+
+def test_server_refuses_a_wrong_sized_output_buffer_before_calling_the_library():
+    # The server writes n*n complex64 values into field_out from its worker
+    # thread; the binding checks the size first (no device is touched).
+    import numpy as np
+
+    from paper_1410_2855_gb300 import workloads as wl
+    srv = rt.Server.__new__(rt.Server)
+    srv.h, srv._keep = None, {}
+    n = wl.C2.n
+    for bad in (np.zeros((n // 2, n), np.complex64), np.zeros((n, n), np.complex128), np.zeros((n, n), np.float32)):
+        with pytest.raises(ValueError):
+            srv.submit(wl.C2, 10, bad)
+    assert srv._keep == {}
