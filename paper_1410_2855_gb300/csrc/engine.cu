@@ -1,4 +1,6 @@
-// Slot set-up shared by batches and the server (engine.h).
+// Shared by batches and the server (engine.h): slot set-up, the batched
+// bounce launches, and their capture into graphs with one branch per part
+// of a size class.
 #include <climits>
 #include <cmath>
 #include <cstring>
