@@ -4,13 +4,15 @@ Rot16Const<float>): each literal is an exact float, the rotation it encodes,
 rad of its angle, and for pi/8 and pi/4 it is the best such float pair among
 the neighbours of the nearest roundings.  The rounded (cos, sin) pairs lie
 5.7e-8 and 3.4e-8 inside the circle, which is checked too, since that gap is
-what the (cos - 1, sin) form exists to close.  Exact rational arithmetic."""
+what the (cos - 1, sin) form exists to close.  Exact rational arithmetic.
+The FP64 constants (Rot16Const<double>) are the correctly rounded doubles."""
 import math
 import os
 import re
 from fractions import Fraction
 
 import numpy as np
+import pytest
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1410_2855_gb300", "csrc",
                    "fft_core.cuh")
@@ -70,3 +72,19 @@ def test_rounded_cos_sin_pairs_fall_inside_the_circle():
         cf, sf = Fraction(float(np.float32(math.cos(theta)))), Fraction(float(np.float32(math.sin(theta))))
         e = float(cf ** 2 + sf ** 2 - 1)
         assert e < 0 and abs(abs(e) - gap) < 0.1e-8
+
+
+def test_double_constants_are_correctly_rounded():
+    # Rot16Const<double>: cos(theta) - 1 and sin(theta) for pi/8 and pi/4,
+    # each the double nearest the exact value (50-digit reference).
+    mpmath = pytest.importorskip("mpmath")
+    text = open(SRC).read()
+    body = text[text.index("template <> struct Rot16Const<double>"):]
+    body = body[:body.index("};")]
+    vals = dict(re.findall(r"(cm8|s8|cm4|s4)\s*=\s*(-?[0-9.]+)", body))
+    mpmath.mp.dps = 50
+    exact = {"cm8": mpmath.cos(mpmath.pi / 8) - 1, "s8": mpmath.sin(mpmath.pi / 8),
+             "cm4": mpmath.cos(mpmath.pi / 4) - 1, "s4": mpmath.sin(mpmath.pi / 4)}
+    for k, v in exact.items():
+        d = float(vals[k])                                  # the literal as the compiler rounds it
+        assert d == float(v), (k, d, float(v))              # float(mpf) rounds to nearest
