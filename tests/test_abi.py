@@ -163,3 +163,22 @@ def test_server_refuses_a_wrong_sized_output_buffer_before_calling_the_library()
         with pytest.raises(ValueError):
             srv.submit(wl.C2, 10, bad)
     assert srv._keep == {}
+
+
+def test_job_from_params_carries_every_field(lib):
+    # A workloads record with a distinct value in every field reaches the
+    # C struct field for field; a rough mirror's phase array is referenced.
+    import numpy as np
+
+    from paper_1410_2855_gb300 import workloads as wl
+    p = wl.Resonator(n=256, fresnel=123.0, g0=0.21, T1=4321.0, R=0.87, Isat=2.5, edge=5, pump_order=6.0,
+                     pump_radius=0.55, d_over_w=0.7, seed=99, noise_amp=3e-6, z_over_F=0.12, roughness_rms=0.07,
+                     roughness_corr=0.1, taper_px=4, relax=1)
+    j = rt.job_from_params(p)
+    assert (j.n, j.fresnel, j.g0, j.T1, j.R) == (256, 123.0, 0.21, 4321.0, 0.87)
+    assert (j.pump.kind, j.pump.order, j.pump.radius) == (rt.RT_PUMP_SUPERGAUSS, 6.0, 0.55) and not j.pump.profile
+    assert (j.Isat, j.edge_px, j.seed, j.noise_amp, j.pump_diam_over_window) == (2.5, 5, 99, 3e-6, 0.7)
+    assert (j.z_over_F, j.taper_px, j.relax) == (0.12, 4, 1)
+    assert j.roughness == j._psi.ctypes.data and np.array_equal(j._psi, p.roughness())
+    smooth = rt.job_from_params(wl.Resonator(n=64, fresnel=10.0, g0=0.2, T1=100.0, R=0.9))
+    assert not smooth.roughness
