@@ -182,3 +182,25 @@ def test_job_from_params_carries_every_field(lib):
     assert j.roughness == j._psi.ctypes.data and np.array_equal(j._psi, p.roughness())
     smooth = rt.job_from_params(wl.Resonator(n=64, fresnel=10.0, g0=0.2, T1=100.0, R=0.9))
     assert not smooth.roughness
+
+
+def test_resonator_from_params_passes_every_field():
+    # The same record through Resonator.from_params: the constructor's
+    # arguments are recorded (no device is touched) and must carry every field.
+    import numpy as np
+
+    from paper_1410_2855_gb300 import workloads as wl
+
+    class Probe(rt.Resonator):
+        def __init__(self, *args, **kw):
+            self.args, self.kw, self.h = args, kw, None
+
+    p = wl.Resonator(n=256, fresnel=123.0, g0=0.21, T1=4321.0, R=0.87, Isat=2.5, edge=5, pump_order=6.0,
+                     pump_radius=0.55, d_over_w=0.7, seed=99, noise_amp=3e-6, z_over_F=0.12, roughness_rms=0.07,
+                     roughness_corr=0.1, taper_px=4, relax=1)
+    r = Probe.from_params(p, precision=rt.RT_FP64, chunk=7)
+    assert r.args == (256, 123.0, 0.21, 4321.0, 0.87)
+    kw = dict(r.kw)
+    assert np.array_equal(kw.pop("roughness"), p.roughness())
+    assert kw == dict(precision=rt.RT_FP64, pump_order=6.0, pump_radius=0.55, Isat=2.5, edge_px=5, seed=99,
+                      noise_amp=3e-6, pump_diam_over_window=0.7, z_over_F=0.12, taper_px=4, relax=1, chunk=7)
