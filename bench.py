@@ -185,7 +185,7 @@ def oracle_rate(params_list, E0s, N0s, budget_s=12.0, horizons=(1, 20)):
     its fields after each of `horizons` bounces from the starting state
     (those runs are part of the timed sample)."""
     import oracle as orc
-    threads = os.cpu_count() or 1
+    threads = orc.threads_available(os.cpu_count() or 1)
     done, t_total = 0, 0.0
     fields = {}
 
@@ -217,7 +217,7 @@ def run_reference(args):
     res = workload(0)
     params = [oracle_params(p) for p in res]
     init = [orc.init_state(p, r.seed, r.noise_amp) for p, r in zip(params, res)]
-    threads = os.cpu_count() or 1
+    threads = orc.threads_available(os.cpu_count() or 1)
     # each step: one bounce of each resonator (bounded sample of the workload)
     for _ in range(args.warmup):
         for p, (E, N) in zip(params, init):

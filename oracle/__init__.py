@@ -85,6 +85,12 @@ class Pattern(ctypes.Structure):
 _dp = ctypes.POINTER(ctypes.c_double)
 
 
+def threads_available(requested: int) -> int:
+    """Threads a call with nthreads=requested really uses: `requested` when
+    the library was compiled with OpenMP, else 1."""
+    return max(1, int(requested)) if lib().orc_openmp() else 1
+
+
 def lib() -> ctypes.CDLL:
     global _lib
     with _lock:
@@ -93,6 +99,7 @@ def lib() -> ctypes.CDLL:
             L = ctypes.CDLL(_LIB_PATH)
             vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
             L.orc_version.restype = i
+            L.orc_openmp.restype = i
             L.orc_dft.argtypes = [vp, vp, i, i]
             L.orc_fft.argtypes = [vp, i, i]
             L.orc_fft.restype = i

@@ -95,6 +95,17 @@ typedef struct {
 
 int orc_version(void) { return 1; }
 
+/* 1 when the library was compiled with OpenMP, so that the nthreads
+ * arguments take effect; 0 when every call runs on one thread. */
+int orc_openmp(void)
+{
+#ifdef _OPENMP
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 static int is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 /* Signed frequency of DFT bin k. */

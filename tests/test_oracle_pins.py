@@ -344,6 +344,14 @@ def test_spectrum_parseval_and_history_is_the_mean_intensity():
         assert len(hist) == nb and abs(hist[-1] - np.mean(np.abs(E1) ** 2)) <= 1e-14 * hist[-1]
 
 
+def test_thread_count_reported_for_the_host_baseline():
+    # The host baseline states how many threads the oracle used: all that
+    # were asked for with OpenMP, one without it.
+    assert orc.lib().orc_openmp() in (0, 1)
+    assert orc.threads_available(6) == (6 if orc.lib().orc_openmp() else 1)
+    assert orc.threads_available(0) == 1
+
+
 def test_threaded_oracle_is_bit_identical_to_one_thread():
     # The host baseline runs the oracle on all cores; threads split rows and
     # columns of the transforms and rows of the local map, so every value is
