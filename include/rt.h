@@ -390,6 +390,7 @@ typedef struct {
     double point_bounces;              /* sum over finished rounds of n^2 x bounces run */
     double busy_s;                     /* wall time spent in scheduling rounds */
     long long rounds;
+    long long peak_resident_bytes;     /* most device bytes ever held for requests at once (<= budget) */
 } rt_serve_stats_t;
 
 rt_status rt_serve_opts_default(rt_serve_opts *opts);
@@ -443,14 +444,17 @@ rt_status rt_serve_destroy(rt_server *s);
  * RT_EINVAL).  Options used: Isat, edge_px, pump_diam_over_window,
  * cuda_stream, col_tile, z_over_F, taper_px, relax (NULL opts = defaults).
  *
- * The first call on each device looks up the array's device address, with
- * that device current; make that first call before any stream capture.
+ * The first call in each CUDA context (per device, and again after
+ * cudaDeviceReset) looks up the array's device address with that device
+ * current; make that first call before any stream capture.
  * All calls share the one array: each call rebuilds the tables and clears
  * the counters it needs, and calls whose work overlaps on the GPU race with
  * one another, so order them on one stream or with events.
  * With mean_intensity == NULL the call is asynchronous on the stream.  With
- * a host pointer it waits for the work, returns a device error (RT_ENUMERIC,
- * RT_ETIMEOUT) if one occurred, and stores <|E|^2> after the last bounce. */
+ * a host pointer it waits for the work, stores <|E|^2> after the last
+ * bounce, and returns a device error (RT_ENUMERIC, RT_ETIMEOUT) if one
+ * occurred in this call or in an asynchronous call before it: such an error
+ * stays in the array until a synchronous call reports it, once. */
 #define RT_NOALLOC_MAX_N 4096
 rt_status rt_step_noalloc(int n, double fresnel, const rt_pump *pump, double g0, double T1, double R,
                           const rt_opts *opts, void *field, void *inversion, long long n_bounces,

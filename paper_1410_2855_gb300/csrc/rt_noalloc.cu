@@ -10,8 +10,11 @@
 //   [.., +kPartMax*8)         block partial sums of the mean intensity
 //   [.., +kMaxN*8)            per-axis curved-mirror factors (n complex64)
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <mutex>
+
+#include <cuda.h>
 
 #include "rt.h"
 #include "rt_internal.h"
@@ -28,12 +31,17 @@ constexpr size_t kPartBytes = kPartMax * sizeof(double);
 constexpr size_t kLensBytes = (size_t)kMaxN * sizeof(float2);
 constexpr size_t kScratchBytes = kCtlBytes + kHBytes + kTwBytes + kPartBytes + kLensBytes;
 
+// The counters come first and are cleared by every call; the sticky error
+// word comes last and is cleared only once a synchronous call has reported it.
 struct NoAllocCtl {
     unsigned int count;
-    int err;
+    unsigned int pad;
     long long bounce;
     double last_mean;
+    int err;
 };
+constexpr size_t kCountersBytes = offsetof(NoAllocCtl, err);
+static_assert(sizeof(NoAllocCtl) <= kCtlBytes, "control block");
 
 }  // namespace
 
@@ -42,22 +50,59 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 namespace {
 
-// Device address of the scratch array, looked up once per device with that
-// device current.  In host code the array's name only denotes a host-side
-// stand-in, so kernels must be given this address instead.
+// Device address of the scratch array.  In host code the array's name only
+// denotes a host-side stand-in, so kernels must be given the address that
+// cudaGetSymbolAddress reports with the device current.  It is looked up once
+// per CUDA context: a context created after cudaDeviceReset gets a new id
+// (cuCtxGetId), and with it a fresh lookup instead of a stale address.
 std::mutex g_addr_mutex;
-void *g_addr[64] = {};
+struct ScratchAddr {
+    unsigned long long ctx_id;
+    void *ptr;
+};
+ScratchAddr g_addr[64] = {};
+
+using PFN_ctx_current = CUresult (*)(CUcontext *);
+using PFN_ctx_id = CUresult (*)(CUcontext, unsigned long long *);
+
+// Id of the calling thread's current context (made current by the runtime).
+rt_status current_context_id(int dev, unsigned long long *id)
+{
+    static PFN_ctx_current get_current = nullptr;
+    static PFN_ctx_id get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 4000, cudaEnableDefault, &q1) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || !f1)
+            return RT_ECUDA;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q2 != cudaDriverEntryPointSuccess || !f2)
+            return RT_ECUDA;
+        get_current = reinterpret_cast<PFN_ctx_current>(f1);
+        get_id = reinterpret_cast<PFN_ctx_id>(f2);
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS) return RT_ECUDA;
+    if (!ctx) {  // nothing current yet: the runtime makes the device's primary context current
+        if (cudaSetDevice(dev) != cudaSuccess || get_current(&ctx) != CUDA_SUCCESS || !ctx) return RT_ECUDA;
+    }
+    return get_id(ctx, id) == CUDA_SUCCESS ? RT_OK : RT_ECUDA;
+}
 
 rt_status scratch_address(int dev, unsigned char **out)
 {
     if (dev < 0 || dev >= 64) return RT_ECUDA;
+    unsigned long long ctx = 0;
+    rt_status st = current_context_id(dev, &ctx);
+    if (st != RT_OK) return st;
     std::lock_guard<std::mutex> lock(g_addr_mutex);
-    if (!g_addr[dev]) {
+    if (!g_addr[dev].ptr || g_addr[dev].ctx_id != ctx) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return RT_ECUDA;
-        g_addr[dev] = p;
+        g_addr[dev] = {ctx, p};
     }
-    *out = static_cast<unsigned char *>(g_addr[dev]);
+    *out = static_cast<unsigned char *>(g_addr[dev].ptr);
     return RT_OK;
 }
 
@@ -96,7 +141,8 @@ extern "C" rt_status rt_step_noalloc(int n, double fresnel, const rt_pump *pump,
     const int logn = log2i(n);
     const int colC = o.col_tile ? o.col_tile : rtk::default_col_tile32(logn);
     if (!rtk::col_tile_ok32(logn, colC)) return RT_EINVAL;
-    if ((size_t)rtk::twiddle_entries(logn) > kTwMax || (size_t)rtk::row_blocks32(logn) > kPartMax) return RT_EINVAL;
+    // the same twiddle_entries + 1 slots as the handle, batch and serve paths
+    if ((size_t)rtk::twiddle_entries(logn) + 1 > kTwMax || (size_t)rtk::row_blocks32(logn) > kPartMax) return RT_EINVAL;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RT_ECUDA;
@@ -116,8 +162,10 @@ extern "C" rt_status rt_step_noalloc(int n, double fresnel, const rt_pump *pump,
     alignas(64) unsigned char tmap[128];
     if (rtk::make_col_tensor_map(tmap, E, n, colC) != cudaSuccess) return RT_ECUDA;
 
-    // The array keeps whatever the previous call left: the counters must start at zero.
-    if (cudaMemsetAsync(ctl, 0, sizeof(NoAllocCtl), s) != cudaSuccess) return RT_ECUDA;
+    // The array keeps whatever the previous call left: the counters must
+    // start at zero.  The error word is kept, so that an error of an
+    // asynchronous call is still there for the next synchronous one.
+    if (cudaMemsetAsync(ctl, 0, kCountersBytes, s) != cudaSuccess) return RT_ECUDA;
     if (rtk::launch_tables32(n, alpha, tw, h, s) != cudaSuccess) return RT_ECUDA;
     // per-axis aperture factors: curved mirror, taper, or the general local map (exact update)
     const bool curved = o.z_over_F != 0.0 || o.taper_px > 0 || o.relax == RT_RELAX_EXACT;
@@ -156,7 +204,10 @@ extern "C" rt_status rt_step_noalloc(int n, double fresnel, const rt_pump *pump,
     NoAllocCtl c;
     if (cudaMemcpyAsync(&c, ctl, sizeof(c), cudaMemcpyDeviceToHost, s) != cudaSuccess) return RT_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return RT_ECUDA;
-    if (c.err) return (rt_status)c.err;
+    if (c.err) {  // reported once: clear it for the calls that follow
+        if (cudaMemsetAsync(&ctl->err, 0, sizeof(int), s) != cudaSuccess) return RT_ECUDA;
+        return (rt_status)c.err;
+    }
     *mean_intensity = n_bounces > 0 ? c.last_mean : 0.0;
     return RT_OK;
 }

@@ -13,6 +13,7 @@
 // resident between rounds.  A request that cannot be placed even with
 // nothing resident fails (its result is posted) instead of waiting.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <climits>
 #include <condition_variable>
@@ -80,7 +81,9 @@ struct rt_server {
     std::set<long long> cancel;       // ids to cancel once the worker holds them
     long long next_id = 1, submitted = 0, finished = 0, running = 0, rounds = 0;
     double point_bounces = 0.0, busy_s = 0.0;
-    long long resident = 0;
+    // Device bytes held for requests, and the most ever held.  Only the
+    // worker changes them; rt_serve_stats reads them from other threads.
+    std::atomic<long long> resident{0}, peak_resident{0};
     // worker-only state
     std::map<int, SClass> classes;
     std::map<std::string, cudaGraphExec_t> graphs;
@@ -169,7 +172,8 @@ bool admit(rt_server *s, Request &r, cudaError_t *why)
         if (s->resident + need > s->opts.budget_bytes) return false;
         SSlot ns;
         if ((*why = slot_alloc(r.job.n, kHistCap, false, false, &ns.buf)) != cudaSuccess) return false;
-        s->resident += (long long)ns.buf.bytes;
+        const long long now_resident = s->resident += (long long)ns.buf.bytes;
+        if (now_resident > s->peak_resident.load()) s->peak_resident.store(now_resident);
         c.slots.push_back(ns);
         idx = (int)c.slots.size() - 1;
     }
@@ -564,7 +568,8 @@ rt_status rt_serve_stats(rt_server *s, rt_serve_stats_t *out)
     out->queued = (long long)s->queue.size();
     out->running = s->running;
     out->done = s->finished;
-    out->resident_bytes = s->resident;
+    out->resident_bytes = s->resident.load();
+    out->peak_resident_bytes = s->peak_resident.load();
     out->point_bounces = s->point_bounces;
     out->busy_s = s->busy_s;
     out->rounds = s->rounds;

@@ -72,7 +72,8 @@ class rt_result(ctypes.Structure):
 class rt_serve_stats_t(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_longlong), ("queued", ctypes.c_longlong), ("running", ctypes.c_longlong),
                 ("done", ctypes.c_longlong), ("resident_bytes", ctypes.c_longlong),
-                ("point_bounces", ctypes.c_double), ("busy_s", ctypes.c_double), ("rounds", ctypes.c_longlong)]
+                ("point_bounces", ctypes.c_double), ("busy_s", ctypes.c_double), ("rounds", ctypes.c_longlong),
+                ("peak_resident_bytes", ctypes.c_longlong)]
 
 
 class rt_stats_t(ctypes.Structure):

@@ -117,6 +117,7 @@ def test_struct_layouts_match_the_header(tmp_path, lib):
             printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", offsetof(rt_opts, z_over_F), offsetof(rt_opts, roughness),
                    sizeof(rt_job), offsetof(rt_job, pump), offsetof(rt_job, z_over_F), offsetof(rt_job, roughness),
                    sizeof(rt_serve_opts), sizeof(rt_result));
+            printf("%zu %zu\\n", sizeof(rt_serve_stats_t), offsetof(rt_serve_stats_t, peak_resident_bytes));
             return 0;
         }
     """))
@@ -127,7 +128,8 @@ def test_struct_layouts_match_the_header(tmp_path, lib):
             rt.rt_opts.chunk.offset, rt.rt_stats_t.history_len.offset, rt.rt_opts.cuda_stream.offset,
             rt.rt_opts.z_over_F.offset, rt.rt_opts.roughness.offset, ctypes.sizeof(rt.rt_job), rt.rt_job.pump.offset,
             rt.rt_job.z_over_F.offset, rt.rt_job.roughness.offset, ctypes.sizeof(rt.rt_serve_opts),
-            ctypes.sizeof(rt.rt_result)]
+            ctypes.sizeof(rt.rt_result), ctypes.sizeof(rt.rt_serve_stats_t),
+            rt.rt_serve_stats_t.peak_resident_bytes.offset]
     assert got == want
 
 

@@ -52,3 +52,27 @@ def test_noalloc_matches_handle_path_on_two_calls(n, fresnel, g0, T1, R, z_over_
             assert float(np.linalg.norm(N - N_ref) / np.linalg.norm(N_ref)) <= TOL
             ref_mean = ref.stats().mean_intensity
             assert abs(mean - ref_mean) <= TOL * ref_mean
+
+
+def test_error_of_an_asynchronous_call_reaches_the_next_synchronous_call():
+    # An Inf in the caller's field makes the mean intensity non-finite.  The
+    # asynchronous call (no host pointer for the mean) cannot report it; the
+    # next synchronous call does, once, and the call after that is clean.
+    import torch
+
+    build.build()
+    n = 64
+    E = np.ones((n, n), np.complex64)
+    E[n // 2, n // 2] = np.inf
+    E_dev = torch.from_numpy(E.view(np.float32).copy()).cuda()
+    N_dev = torch.zeros((n, n), dtype=torch.float32, device="cuda")
+    opts = rt.rt_opts_default()
+    opts.cuda_stream = torch.cuda.current_stream().cuda_stream
+    rt.rt_step_noalloc(n, 50.0, None, 0.2, 100.0, 0.95, opts, E_dev, N_dev, 1, wait=False)
+    with pytest.raises(rt.RtError) as ei:
+        rt.rt_step_noalloc(n, 50.0, None, 0.2, 100.0, 0.95, opts, E_dev, N_dev, 0)
+    assert ei.value.status == rt.RT_ENUMERIC
+    E_dev.copy_(torch.from_numpy(np.ones((n, n), np.complex64).view(np.float32)))
+    N_dev.zero_()
+    mean = rt.rt_step_noalloc(n, 50.0, None, 0.2, 100.0, 0.95, opts, E_dev, N_dev, 1)
+    assert np.isfinite(mean) and mean > 0
