@@ -61,6 +61,11 @@ def parse_args():
     ap.add_argument("--bounces-per-step", type=int, default=500)
     ap.add_argument("--no-comparisons", action="store_true", help="skip the comparison legs")
     ap.add_argument("--col-tile", type=int, default=0, help="fixed column-sweep tile width (0: autotune)")
+    ap.add_argument("--serve-requests", type=int, default=1000,
+                    help="requests of the 50 req/s serving replay (the first arrivals of the seeded trace)")
+    ap.add_argument("--serve-capacity-requests", type=int, default=100,
+                    help="requests of the serving replay at a sustainable rate")
+    ap.add_argument("--serve-capacity-rate", type=float, default=2.0, help="its arrival rate, requests/s")
     return ap.parse_args()
 
 
@@ -73,15 +78,16 @@ def workload(rank: int):
             for c in wl.C3]
 
 
-def config_block(B, extra=None):
+def config_block():
+    """The workload, the same in both arms (the bounce count per step of each
+    arm is reported beside it)."""
     c = wl.C3[0]
-    cfg = {"workload": "two 2048x2048 complex64 resonators, N_F=1000, g0 in {0.1,0.3}, T1=1e4, R=0.9, "
-                       "super-Gaussian pump (order 10, r=0.8), 8 px edge, 1e4 round trips per resonator",
-           "grid": c.n, "resonators": len(wl.C3), "fresnel": c.fresnel, "g0": [r.g0 for r in wl.C3],
-           "T1": c.T1, "R": c.R, "bounces_per_step": B}
-    if extra:
-        cfg.update(extra)
-    return cfg
+    return {"workload": "two 2048x2048 complex64 resonators, N_F=1000, g0 in {0.1,0.3}, T1=1e4, R=0.9, "
+                        "super-Gaussian pump (order 10, r=0.8), 8 px edge, 1e4 round trips per resonator",
+            "grid": c.n, "resonators": len(wl.C3), "fresnel": c.fresnel, "g0": [r.g0 for r in wl.C3],
+            "T1": c.T1, "R": c.R,
+            "l2": "GPU arm: L2 flushed between steps (256 MiB write), each resonator's 48 MiB state L2-resident "
+                  "within a step; host arm: not applicable"}
 
 
 # ------------------------------------------------------------------ clocks
@@ -180,12 +186,31 @@ def oracle_params(p):
                            edge=p.edge, pump_order=p.pump_order, pump_radius=p.pump_radius)
 
 
+def oracle_setup_s(params_list, E0s, N0s, threads):
+    """Seconds the oracle spends per call before its first bounce (pump,
+    phase table in long double, buffers): the median of three calls of zero
+    bounces, per resonator."""
+    import oracle as orc
+    out = []
+    for p, E, N in zip(params_list, E0s, N0s):
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            orc.run(p, E, N, 0, nthreads=threads, history=False)
+            ts.append(time.perf_counter() - t0)
+        out.append(statistics.median(ts))
+    return out
+
+
 def oracle_rate(params_list, E0s, N0s, budget_s=12.0, horizons=(1, 20)):
     """Bounces/s of the FP64 oracle on the host cores (bounded sample), and
     its fields after each of `horizons` bounces from the starting state
-    (those runs are part of the timed sample)."""
+    (those runs are part of the timed sample).  Every call pays the oracle's
+    set-up, which is timed separately and taken out, so the rate is bounces
+    over bounce time."""
     import oracle as orc
     threads = orc.threads_available(os.cpu_count() or 1)
+    setup = oracle_setup_s(params_list, E0s, N0s, threads)
     done, t_total = 0, 0.0
     fields = {}
 
@@ -193,7 +218,7 @@ def oracle_rate(params_list, E0s, N0s, budget_s=12.0, horizons=(1, 20)):
         nonlocal done, t_total
         t0 = time.perf_counter()
         E, _, _ = orc.run(params_list[i], E0s[i], N0s[i], nb, nthreads=threads, history=False)
-        t_total += time.perf_counter() - t0
+        t_total += max(time.perf_counter() - t0 - setup[i], 1e-9)
         done += nb
         return E
 
@@ -203,10 +228,77 @@ def oracle_rate(params_list, E0s, N0s, budget_s=12.0, horizons=(1, 20)):
     while t_total < budget_s and done < 64:
         for i in range(len(params_list)):
             timed_run(i, 4)
-    return done / t_total, threads, done, fields
+    return done / t_total, threads, done, fields, statistics.mean(setup)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.complex128) - b) / np.linalg.norm(b))
+
+
+def batch_slot_errors(rt, orc, threads, stream):
+    """Relative L2 against the FP64 oracle after 1 and 20 bounces of one
+    sampled resonator per grid size of the batched sweep (the first of each
+    size among the 256), run in a batch through the batched kernels, the
+    oracle started from the slot's own initial field and its own pump."""
+    jobs = wl.batch_sweep(count=256, sides=(256, 512, 1024))
+    first = {}
+    for i, j in enumerate(jobs):
+        first.setdefault(j.n, i)
+    picks = [jobs[i] for i in sorted(first.values())]
+    out = []
+    with rt.Batch(picks, chunk=0, cuda_stream=stream.cuda_stream) as bt:
+        E0 = [bt.field(i) for i in range(len(picks))]
+        bt.step(1)
+        E1 = [bt.field(i) for i in range(len(picks))]
+        bt.step(19)
+        E20 = [bt.field(i) for i in range(len(picks))]
+    for k, j in enumerate(picks):
+        q = oracle_params(j)
+        N0 = orc.pump(q)
+        o1, _, _ = orc.run(q, E0[k], N0, 1, nthreads=threads, history=False)
+        o20, _, _ = orc.run(q, E0[k], N0, 20, nthreads=threads, history=False)
+        out.append({"slot": jobs.index(j), "n": j.n, "fresnel": j.fresnel, "bounce1_rel_l2": rel_l2(E1[k], o1),
+                    "bounce20_rel_l2": rel_l2(E20[k], o20)})
+    return out
+
+
+def served_request_errors(rt, orc, threads, stream):
+    """Relative L2 against the FP64 oracle of served results: the first
+    request of each grid size of the serving trace, submitted for 1 and for
+    20 bounces together (they share rounds), each compared with the oracle
+    run from the same seeded noise start (the oracle's own generator,
+    rounded to complex64 as the library rounds it) and its own pump."""
+    trace = wl.serve_trace(count=200, rate_hz=50.0)
+    first = {}
+    for q in trace:
+        first.setdefault(q.job.n, q.job)
+    picks = [first[n] for n in sorted(first)]
+    outs = {}
+    with rt.Server(chunk=500, budget_bytes=8 << 30, cuda_stream=stream.cuda_stream) as srv:
+        for j in picks:
+            for nb in (1, 20):
+                buf = np.zeros((j.n, j.n), np.complex64)
+                srv.submit(j, nb, buf)
+                outs[(j.n, nb)] = buf
+        srv.drain(600.0)
+        res = srv.poll(64)
+    assert all(r.status == 0 for r in res)
+    out = []
+    for j in picks:
+        q = oracle_params(j)
+        E0, N0 = orc.init_state(q, j.seed, j.noise_amp)
+        E0 = E0.astype(np.complex64).astype(np.complex128)
+        o1, _, _ = orc.run(q, E0, N0, 1, nthreads=threads, history=False)
+        o20, _, _ = orc.run(q, E0, N0, 20, nthreads=threads, history=False)
+        out.append({"n": j.n, "fresnel": j.fresnel, "bounce1_rel_l2": rel_l2(outs[(j.n, 1)], o1),
+                    "bounce20_rel_l2": rel_l2(outs[(j.n, 20)], o20)})
+    return out
 
 
 # ---------------------------------------------------------------- reference
+
+REF_BOUNCES_PER_STEP = 4
+
 
 def run_reference(args):
     rank, local_rank, world = dist_env()
@@ -218,23 +310,34 @@ def run_reference(args):
     params = [oracle_params(p) for p in res]
     init = [orc.init_state(p, r.seed, r.noise_amp) for p, r in zip(params, res)]
     threads = orc.threads_available(os.cpu_count() or 1)
-    # each step: one bounce of each resonator (bounded sample of the workload)
+    setup = oracle_setup_s(params, [E for E, _ in init], [N for _, N in init], threads)
+    k = REF_BOUNCES_PER_STEP
+    # each step: k bounces of each resonator from its start (a bounded sample
+    # of the workload); the oracle's per-call set-up is taken out of each call
     for _ in range(args.warmup):
         for p, (E, N) in zip(params, init):
-            orc.run(p, E, N, 1, nthreads=threads, history=False)
-    t0 = time.perf_counter()
+            orc.run(p, E, N, k, nthreads=threads, history=False)
+    step_s = []
+    t_wall = time.perf_counter()
     for _ in range(args.steps):
-        for p, (E, N) in zip(params, init):
-            orc.run(p, E, N, 1, nthreads=threads, history=False)
-    dt = time.perf_counter() - t0
-    value = args.steps * len(params) / dt
-    sample = (f"{args.steps} steps x 1 bounce of each of the {len(params)} 2048^2 resonators "
-              "(FP64 oracle, table set-up included)")
+        t = 0.0
+        for i, (p, (E, N)) in enumerate(zip(params, init)):
+            t0 = time.perf_counter()
+            orc.run(p, E, N, k, nthreads=threads, history=False)
+            t += max(time.perf_counter() - t0 - setup[i], 1e-9)
+        step_s.append(t)
+    wall = time.perf_counter() - t_wall
+    dt = sum(step_s)
+    value = args.steps * k * len(params) / dt
+    sample = (f"{args.steps} steps x {k} bounces of each of the {len(params)} 2048^2 resonators (FP64 oracle, "
+              f"{threads} threads); the oracle's set-up before the first bounce of each call "
+              f"({statistics.mean(setup):.3f} s: pump, phase table, buffers) is timed separately and not counted")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_block(1, {"l2": "n/a (host)"}),
+        "config": config_block(),
+        "bounces_per_step": k, "oracle_setup_s_per_call": statistics.mean(setup), "wall_s_with_setup": wall,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -314,13 +417,21 @@ def weak_scaling_rate(local_ms, local_units, world, device=None):
     return world * local_units / (total_ms / 1e3), total_ms
 
 
-def serve_replay(rt, stream, count=40, rate_hz=50.0, policy=0, round_points=0):
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(q * len(xs)))] if xs else None
+
+
+def serve_replay(rt, stream, count=1000, rate_hz=50.0, policy=0, round_points=0):
     """Replay the first `count` requests of the seeded Poisson stream (mean
     rate_hz; sides 128..2048, bounces log-uniform in [1e3, 1e5]) against a
     server with 500-bounce rounds and an 8 GiB budget; latency is completion
-    minus submission on the server clock.  policy: the server's scheduling
-    policy (0 first come first served, 1 shortest remaining work first)."""
+    minus submission on the server clock, split into queueing (admission
+    minus submission) and service (completion minus admission).  policy: the
+    server's scheduling policy (0 first come first served, 1 shortest
+    remaining work first)."""
     trace = wl.serve_trace(count=count, rate_hz=rate_hz)
+    t_wall = time.perf_counter()
     with rt.Server(chunk=500, budget_bytes=8 << 30, cuda_stream=stream.cuda_stream, policy=policy,
                    round_points=round_points) as srv:
         t0 = time.perf_counter()
@@ -329,21 +440,28 @@ def serve_replay(rt, stream, count=40, rate_hz=50.0, policy=0, round_points=0):
             if delay > 0:
                 time.sleep(delay)
             srv.submit(req.job, req.bounces)
-        srv.drain(1800.0)
+        srv.drain(3600.0)
         res = srv.poll(4 * count)
         st = srv.stats()
-    lat = sorted(r.finish_s - r.submit_s for r in res)
+    lat = [r.finish_s - r.submit_s for r in res]
     work = sum(float(r.n) ** 2 * r.bounces for r in res)
     span = max(r.finish_s for r in res) - min(r.submit_s for r in res)
-    offered = sum(float(q.job.n) ** 2 * q.bounces for q in trace) / max(trace[-1].arrival_s, 1e-9)
+    arrivals_s = max(trace[-1].arrival_s, 1e-9)
+    offered = sum(float(q.job.n) ** 2 * q.bounces for q in trace) / arrivals_s
     return {"workload": f"first {count} requests of a Poisson stream at {rate_hz:g} req/s, sides uniform over "
                         "{128,...,2048}, bounces log-uniform in [1e3,1e5]; 500-bounce rounds, 8 GiB budget",
             "policy": "shortest remaining work first" if policy else "every resident request every round",
             "requests": len(res), "failed": sum(1 for r in res if r.status != 0),
-            "p50_latency_s": lat[len(lat) // 2], "p99_latency_s": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "p50_latency_s": _pct(lat, 0.5), "p99_latency_s": _pct(lat, 0.99),
+            "p50_queue_s": _pct([r.admit_s - r.submit_s for r in res], 0.5),
+            "p99_queue_s": _pct([r.admit_s - r.submit_s for r in res], 0.99),
+            "p50_service_s": _pct([r.finish_s - r.admit_s for r in res], 0.5),
+            "p99_service_s": _pct([r.finish_s - r.admit_s for r in res], 0.99),
             "round_trips_per_s": sum(r.bounces for r in res) / span,
+            "offered_req_per_s": len(trace) / arrivals_s, "served_req_per_s": len(res) / span,
             "served_point_bounces_per_s": work / span, "offered_point_bounces_per_s": offered,
-            "rounds": st.rounds}
+            "offered_over_served": offered / (work / span), "rounds": st.rounds,
+            "peak_resident_bytes": st.peak_resident_bytes, "wall_s": time.perf_counter() - t_wall}
 
 
 def run_ours(args):
@@ -468,11 +586,10 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": config_block(B, {"l2": "flushed between steps (256 MiB write); each resonator's 48 MiB state "
-                                         "stays L2-resident within a step",
-                                   "graph": f"one CUDA graph per {B} bounces per resonator",
-                                   "streams": "one per resonator, concurrent",
-                                   "col_tile": col_tile, "col_tile_source": tile_source}),
+        "config": config_block(),
+        "bounces_per_step": B,
+        "launch": {"graph": f"one CUDA graph per {B} bounces per resonator",
+                   "streams": "one per resonator, concurrent", "col_tile": col_tile, "col_tile_source": tile_source},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": dom_gbs, "peak": peak, "unit": "GB/s",
                      "frac": dom_gbs / peak, "peak_kind": f"of {peak_kind}",
                      "traffic": profiled_traffic(dom, params[0].n),
@@ -649,9 +766,18 @@ def comparisons(args, rt, torch, main, streams, params, res, E0, N0, rank, world
                 "round_trips_per_s": len(jobs) * 200 / secs, "point_bounces_per_s": Pb * 200 / secs,
                 "hbm_frac": 40 * Pb * 200 / secs / 1e9 / peak, "footprint_bytes": bt.footprint()}
 
-    # ---- serving: a bounded replay of the Poisson request stream
-    extra["serve"] = serve_replay(rt, main)
-    extra["serve_shortest_first"] = serve_replay(rt, main, policy=rt.RT_SERVE_SHORTEST_FIRST)
+    # ---- serving: the first requests of the seeded 50 req/s Poisson stream
+    # (several times what the GPU can serve: latency there is the backlog),
+    # then a replay at a rate the GPU sustains (latency is service plus
+    # modest queueing), each under both scheduling policies
+    extra["serve_overload"] = {
+        "fifo": serve_replay(rt, main, count=args.serve_requests, rate_hz=50.0),
+        "shortest_first": serve_replay(rt, main, count=args.serve_requests, rate_hz=50.0,
+                                       policy=rt.RT_SERVE_SHORTEST_FIRST)}
+    extra["serve_capacity_rate"] = {
+        "fifo": serve_replay(rt, main, count=args.serve_capacity_requests, rate_hz=args.serve_capacity_rate),
+        "shortest_first": serve_replay(rt, main, count=args.serve_capacity_requests,
+                                       rate_hz=args.serve_capacity_rate, policy=rt.RT_SERVE_SHORTEST_FIRST)}
 
     # ---- plain FP64 GPU path on the same GPU (unfused, six sweeps per bounce)
     p = params[1]
@@ -676,25 +802,25 @@ def comparisons(args, rt, torch, main, streams, params, res, E0, N0, rank, world
         oparams = [oracle_params(q) for q in params]
         E0w = [x.astype(np.complex128) for x in E0]
         N0o = [orc.pump(q) for q in oparams]
-        rate, threads, done, fields = oracle_rate(oparams, E0w, N0o)
-
-        def rel(a, b):
-            return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        rate, threads, done, fields, setup_s = oracle_rate(oparams, E0w, N0o)
 
         err1, err20 = [], []
         for i, (q, e0) in enumerate(zip(params, E0)):
             with rt.Resonator.from_params(q, precision=rt.RT_FP32, chunk=0) as r1:
                 r1.set_field(e0)
                 r1.step(1)
-                err1.append(rel(r1.field(), fields[(i, 1)]))
+                err1.append(rel_l2(r1.field(), fields[(i, 1)]))
                 r1.step(19)
-                err20.append(rel(r1.field(), fields[(i, 20)]))
+                err20.append(rel_l2(r1.field(), fields[(i, 20)]))
         extra["error_vs_oracle"] = {"bounce1_rel_l2": err1, "bounce20_rel_l2": err20,
                                     "bar": {"bounce1": 1e-5, "bounce20": 1e-3},
-                                    "resonators": "the two 2048^2 resonators, same start as the oracle"}
+                                    "resonators": "the two 2048^2 resonators, same start as the oracle",
+                                    "batch_slots": batch_slot_errors(rt, orc, threads, main),
+                                    "served_requests": served_request_errors(rt, orc, threads, main)}
         extra["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                  "sample": f"{done} oracle bounces over the two 2048^2 resonators, runs of 1, 20 and 4 bounces "
-                                           f"(FP64, {threads} threads, table set-up included)"}
+                                           f"(FP64, {threads} threads); the set-up before the first bounce of each "
+                                           f"call ({setup_s:.3f} s) is timed separately and not counted"}
     return extra
 
 

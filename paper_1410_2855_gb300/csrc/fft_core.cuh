@@ -276,21 +276,127 @@ template <int LOGN> struct Plan {
     }
 };
 
-// 1: a pass's twiddles are loaded before its exchange, so their latency
-// overlaps the barrier and the shared-memory traffic.
-#ifndef RTK_TW_PREFETCH
-#define RTK_TW_PREFETCH 1
-#endif
-
-// Twiddle from the forward table (exp(-...)), conjugated for the inverse.
-// TWS: the table is in shared memory (plain load) rather than global memory
-// (read-only cache load).
-template <int DIR, bool TWS = false, typename V>
-__device__ __forceinline__ V twmul(V a, const V *__restrict__ tw, int k)
+// Twiddle multiply of a pass, every rounding spelled out (the same bits in
+// every kernel that runs the line FFT): a * w for the forward transform
+// (DIR < 0; the table holds exp(-...)), a * conj(w) for the inverse.
+template <int DIR> __device__ __forceinline__ float2 twm(float2 a, float2 w)
 {
-    const V w = TWS ? tw[k] : __ldg(tw + k);
-    return DIR > 0 ? cmulc(a, w) : cmul(a, w);
+    return DIR > 0 ? make_float2(__fmaf_rn(a.x, w.x, __fmul_rn(a.y, w.y)), __fmaf_rn(a.y, w.x, -__fmul_rn(a.x, w.y)))
+                   : cmul_rn(a, w);
 }
+template <int DIR> __device__ __forceinline__ double2 twm(double2 a, double2 w)
+{
+    return DIR > 0 ? make_double2(__fma_rn(a.x, w.x, __dmul_rn(a.y, w.y)), __fma_rn(a.y, w.x, -__dmul_rn(a.x, w.y)))
+                   : cmul_rn(a, w);
+}
+
+// ---- two lines at once ----------------------------------------------------
+// A thread of the column-pair sweep carries the same element of two adjacent
+// columns.  They share every twiddle and propagator factor, and the pair
+// moves through shared and global memory as one 16-byte access.  Each half
+// goes through exactly the operations of a single line, so the results are
+// bit-identical to transforming the columns one at a time.
+struct __align__(16) cpair {
+    float2 a, b;
+};
+__device__ __forceinline__ cpair cadd(cpair x, cpair y) { return {cadd(x.a, y.a), cadd(x.b, y.b)}; }
+__device__ __forceinline__ cpair csub(cpair x, cpair y) { return {csub(x.a, y.a), csub(x.b, y.b)}; }
+template <int DIR> __device__ __forceinline__ cpair rot16(cpair x, int k)
+{
+    return {rot16<DIR>(x.a, k), rot16<DIR>(x.b, k)};
+}
+template <int DIR> __device__ __forceinline__ void dft4(cpair &a0, cpair &a1, cpair &a2, cpair &a3)
+{
+    dft4<DIR>(a0.a, a1.a, a2.a, a3.a);
+    dft4<DIR>(a0.b, a1.b, a2.b, a3.b);
+}
+template <int DIR> __device__ __forceinline__ cpair twm(cpair x, float2 w) { return {twm<DIR>(x.a, w), twm<DIR>(x.b, w)}; }
+__device__ __forceinline__ cpair cmul_rn(cpair x, float2 w) { return {cmul_rn(x.a, w), cmul_rn(x.b, w)}; }
+
+template <typename V> struct table_of { using type = V; };
+template <> struct table_of<cpair> { using type = float2; };
+
+// Offset of pass p's block in the pass-major twiddle table (passes p >= 1;
+// p = P16 is the trailing pass).
+template <int LOGN> __host__ __device__ constexpr int tw_pass_off(int p)
+{
+    int s = 0, Ns = 16;
+    for (int q = 1; q < p; ++q, Ns *= 16) s += 15 * Ns;
+    return s;
+}
+
+// ---- table sources of the line FFT -------------------------------------------
+// A line FFT needs, per thread, 15 twiddles for each radix-16 pass after the
+// first, NB (RL - 1) for the trailing radix-RL pass, and (POST) the 16
+// factors of its output elements.  TabGlobal loads them from global memory
+// (read-only cache) where they are used; TabRegs holds them in registers for
+// the life of a kernel, loaded once.
+template <int LOGN, typename W> struct TabShape {
+    using P = Plan<LOGN>;
+    static constexpr int NP = P::P16 - 1;                                          // radix-16 passes with twiddles
+    static constexpr int NL = P::LASTLOG ? (16 / P::LASTR) * (P::LASTR - 1) : 0;  // trailing-pass twiddles
+};
+
+template <int LOGN, typename W> struct TabGlobal {
+    const W *__restrict__ tw;
+    const W *__restrict__ post;
+    __device__ __forceinline__ void pass(int p, int t, W (&w)[15]) const
+    {
+        const int Ns = 1 << (4 * p);
+        const W *q = tw + tw_pass_off<LOGN>(p) + (t & (Ns - 1));
+#pragma unroll
+        for (int r = 1; r < 16; ++r) w[r - 1] = __ldg(q + (r - 1) * Ns);
+    }
+    template <int NL> __device__ __forceinline__ void last(int t, W (&w)[NL]) const
+    {
+        using P = Plan<LOGN>;
+        constexpr int RL = P::LASTR, NB = 16 / RL, NsL = P::N / RL, T = P::T;
+        const W *q = tw + tw_pass_off<LOGN>(P::P16) + t;
+#pragma unroll
+        for (int i = 0; i < NB; ++i)
+#pragma unroll
+            for (int r = 1; r < RL; ++r) w[i * (RL - 1) + r - 1] = __ldg(q + i * T + (r - 1) * NsL);
+    }
+    __device__ __forceinline__ void postv(int t, W (&w)[16]) const
+    {
+#pragma unroll
+        for (int s = 0; s < 16; ++s) w[s] = __ldg(post + t + s * Plan<LOGN>::T);
+    }
+};
+
+template <int LOGN, typename W> struct TabRegs {
+    using S = TabShape<LOGN, W>;
+    W pw[S::NP > 0 ? S::NP : 1][15];
+    W lw[S::NL > 0 ? S::NL : 1];
+    W h[16];
+    __device__ __forceinline__ void load_tw(const W *__restrict__ tw, int t)
+    {
+        const TabGlobal<LOGN, W> g{tw, nullptr};
+#pragma unroll
+        for (int p = 1; p <= S::NP; ++p) g.pass(p, t, pw[p - 1]);
+        if constexpr (S::NL > 0) g.last(t, lw);
+    }
+    __device__ __forceinline__ void load_post(const W *__restrict__ post, int t)
+    {
+        const TabGlobal<LOGN, W> g{nullptr, post};
+        g.postv(t, h);
+    }
+    __device__ __forceinline__ void pass(int p, int t, W (&w)[15]) const
+    {
+#pragma unroll
+        for (int r = 0; r < 15; ++r) w[r] = pw[p - 1][r];
+    }
+    template <int NL> __device__ __forceinline__ void last(int t, W (&w)[NL]) const
+    {
+#pragma unroll
+        for (int i = 0; i < NL; ++i) w[i] = lw[i];
+    }
+    __device__ __forceinline__ void postv(int t, W (&w)[16]) const
+    {
+#pragma unroll
+        for (int s = 0; s < 16; ++s) w[s] = h[s];
+    }
+};
 
 // Element i of a padded line with element stride CS (1 for a row buffer; C
 // for the [row][column] tile of the column sweep).
@@ -334,30 +440,32 @@ __device__ __forceinline__ bool sm_in(const V *base, const V *p, int *chk)
 // `lb` holds this line's padded shared buffer(s) (element stride CS); sync()
 // is a barrier over every thread that shares them.  Shared addresses are a
 // per-thread base plus compile-time offsets: spans and T are multiples of 16
-// wherever the pad arithmetic allows it.
-// POST: multiply the result by post[k] (element k of the output line); the
-// factors are loaded ahead of the last exchange when there is a trailing pass.
-template <int LOGN, int DIR, int CS, bool PP, bool TWS = false, bool POST = false, typename V, typename SyncF>
-__device__ __forceinline__ void fft_line(V (&v)[16], const int t, LineBufs<V, PP> &lb, const V *__restrict__ tw,
-                                         SyncF sync, const V *__restrict__ post = nullptr)
+// wherever the pad arithmetic allows it.  A pass's twiddles are fetched
+// before its exchange, so their latency overlaps the barrier.
+// POST: multiply the result by factor k of `tab` (element k of the output
+// line); the factors are fetched ahead of the last exchange when there is a
+// trailing pass.  read_done() runs once every read of the last exchange is
+// issued (by this thread): a caller can release the buffer there.
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+template <int LOGN, int DIR, int CS, bool PP, bool POST, typename V, typename Tab, typename SyncF,
+          typename Hook = NoHook>
+__device__ __forceinline__ void fft_line_t(V (&v)[16], const int t, LineBufs<V, PP> &lb, const Tab &tab, SyncF sync,
+                                           Hook read_done = Hook{})
 {
     using P = Plan<LOGN>;
+    using W = typename table_of<V>::type;
     constexpr int N = P::N, T = P::T;
     constexpr bool T16 = (T % 16) == 0;
     dft<16, DIR>(v);
-    int off = 0;
 #pragma unroll
     for (int p = 1; p < P::P16; ++p) {
         const int NsPrev = 1 << (4 * (p - 1));
-        const int Ns = NsPrev * 16;
         V *line = lb.take();
         V *rd_base = line + padi(t) * CS;
-        const V *twp = tw + off + (t & (Ns - 1));
-        V wpre[RTK_TW_PREFETCH ? 15 : 1];
-        if constexpr (RTK_TW_PREFETCH) {
-#pragma unroll
-            for (int r = 1; r < 16; ++r) wpre[r - 1] = TWS ? twp[(r - 1) * Ns] : __ldg(twp + (r - 1) * Ns);
-        }
+        W wpre[15];
+        tab.pass(p, t, wpre);
         if (!PP) sync();
         if (NsPrev == 1) {
             V *w = line + 17 * t * CS;
@@ -383,12 +491,9 @@ __device__ __forceinline__ void fft_line(V (&v)[16], const int t, LineBufs<V, PP
             for (int r = 0; r < 16; ++r)
                 if (sm_in<LOGN, CS>(line, &sm_at<CS>(line, t + r * T), lb.chk)) v[r] = sm_at<CS>(line, t + r * T);
         }
+        if (P::LASTLOG == 0 && p == P::P16 - 1) read_done();
 #pragma unroll
-        for (int r = 1; r < 16; ++r) {
-            if constexpr (RTK_TW_PREFETCH) v[r] = DIR > 0 ? cmulc(v[r], wpre[r - 1]) : cmul(v[r], wpre[r - 1]);
-            else v[r] = twmul<DIR, TWS>(v[r], twp, (r - 1) * Ns);
-        }
-        off += 15 * Ns;
+        for (int r = 1; r < 16; ++r) v[r] = twm<DIR>(v[r], wpre[r - 1]);
         dft<16, DIR>(v);
     }
     if constexpr (P::LASTLOG > 0) {
@@ -396,21 +501,10 @@ __device__ __forceinline__ void fft_line(V (&v)[16], const int t, LineBufs<V, PP
         constexpr int NsPrev = NsL / 16;
         V *line = lb.take();
         V *rd_base = line + padi(t) * CS;
-        V pl[POST ? 16 : 1];
-        if constexpr (POST) {
-#pragma unroll
-            for (int s = 0; s < 16; ++s) pl[s] = __ldg(post + t + s * T);
-        }
-        V wl[RTK_TW_PREFETCH ? NB * (RL - 1) : 1];
-        if constexpr (RTK_TW_PREFETCH) {
-#pragma unroll
-            for (int i = 0; i < NB; ++i)
-#pragma unroll
-                for (int r = 1; r < RL; ++r) {
-                    const V *q = tw + off + t + i * T + (r - 1) * NsL;
-                    wl[i * (RL - 1) + r - 1] = TWS ? *q : __ldg(q);
-                }
-        }
+        W pl[POST ? 16 : 1];
+        if constexpr (POST) tab.postv(t, pl);
+        W wl[NB * (RL - 1)];
+        tab.last(t, wl);
         if (!PP) sync();
         if constexpr (NsPrev == 1) {
             V *w = line + 17 * t * CS;
@@ -426,25 +520,27 @@ __device__ __forceinline__ void fft_line(V (&v)[16], const int t, LineBufs<V, PP
                     w[r * (17 * NsPrev / 16) * CS] = v[r];
         }
         sync();
+        // every read of the exchange first (the values' old copies in v are
+        // dead once written), then the passes
+        V ua[16];
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
             const int j = t + i * T;
             V *rb = T16 ? rd_base + i * (17 * T / 16) * CS : line + padi(j) * CS;
-            V u[RL];
 #pragma unroll
             for (int r = 0; r < RL; ++r)
-                u[r] = sm_in<LOGN, CS>(line, &rb[r * (17 * NsL / 16) * CS], lb.chk) ? rb[r * (17 * NsL / 16) * CS]
-                                                                                   : v[i];
-            const V *twp = tw + off + j;
+                ua[i * RL + r] = sm_in<LOGN, CS>(line, &rb[r * (17 * NsL / 16) * CS], lb.chk)
+                                     ? rb[r * (17 * NsL / 16) * CS]
+                                     : v[i];
+        }
+        read_done();
 #pragma unroll
-            for (int r = 1; r < RL; ++r) {
-                if constexpr (RTK_TW_PREFETCH) {
-                    const V w = wl[i * (RL - 1) + r - 1];
-                    u[r] = DIR > 0 ? cmulc(u[r], w) : cmul(u[r], w);
-                } else {
-                    u[r] = twmul<DIR, TWS>(u[r], twp, (r - 1) * NsL);
-                }
-            }
+        for (int i = 0; i < NB; ++i) {
+            V u[RL];
+#pragma unroll
+            for (int r = 0; r < RL; ++r) u[r] = ua[i * RL + r];
+#pragma unroll
+            for (int r = 1; r < RL; ++r) u[r] = twm<DIR>(u[r], wl[i * (RL - 1) + r - 1]);
             dft<RL, DIR>(u);
 #pragma unroll
             for (int r = 0; r < RL; ++r) {
@@ -453,9 +549,20 @@ __device__ __forceinline__ void fft_line(V (&v)[16], const int t, LineBufs<V, PP
             }
         }
     } else if constexpr (POST) {
+        W pl[16];
+        tab.postv(t, pl);
 #pragma unroll
-        for (int s = 0; s < 16; ++s) v[s] = cmul_rn(v[s], __ldg(post + t + s * T));
+        for (int s = 0; s < 16; ++s) v[s] = cmul_rn(v[s], pl[s]);
     }
+}
+
+// The line FFT with its tables read from global memory where they are used.
+template <int LOGN, int DIR, int CS, bool PP = false, bool POST = false, typename V, typename SyncF>
+__device__ __forceinline__ void fft_line(V (&v)[16], const int t, LineBufs<V, PP> &lb, const V *__restrict__ tw,
+                                         SyncF sync, const V *__restrict__ post = nullptr)
+{
+    const TabGlobal<LOGN, V> tab{tw, post};
+    fft_line_t<LOGN, DIR, CS, PP, POST>(v, t, lb, tab, sync);
 }
 
 }  // namespace rtk

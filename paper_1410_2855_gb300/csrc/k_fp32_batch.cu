@@ -10,15 +10,16 @@ static cudaError_t col_batch32_c(const BatchRes *res, int nres, const float2 *tw
     if constexpr (!col_tma_fits<LOGN, C>()) {
         return cudaErrorInvalidValue;
     } else {
-        using L = ColPlan<LOGN, C>;
-        auto k = k_col_tma_batch<LOGN, C>;
+        using F = ColForm<LOGN, C>;
+        auto k = F::batch_kernel();
+        constexpr int threads = F::threads;
         static std::atomic<unsigned long long> mask{0};
         static std::atomic<int> per_sm{0};
-        cudaError_t e = ensure_smem(k, L::total, mask);
+        cudaError_t e = ensure_smem(k, F::smem, mask);
         if (e != cudaSuccess) return e;
         const int items = nres * ((1 << LOGN) / C);
-        const int grid = persistent_grid(k, C * Plan<LOGN>::T, L::total, items, per_sm);
-        k<<<grid, C * Plan<LOGN>::T, L::total, s>>>(res, nres, tw, err);
+        const int grid = persistent_grid(k, threads, F::smem, items, per_sm);
+        k<<<grid, threads, F::smem, s>>>(res, nres, tw, err);
         return cudaGetLastError();
     }
 }
@@ -73,7 +74,7 @@ template <int LOGN, int C> static cudaError_t col_batch_prep_c()
         return cudaErrorInvalidValue;
     } else {
         static std::atomic<unsigned long long> mask{0};
-        return ensure_smem(k_col_tma_batch<LOGN, C>, ColPlan<LOGN, C>::total, mask);
+        return ensure_smem(ColForm<LOGN, C>::batch_kernel(), ColForm<LOGN, C>::smem, mask);
     }
 }
 

@@ -37,15 +37,16 @@ static cudaError_t col_diff32_c(float2 *E, const float2 *tw, const float2 *h, co
     if constexpr (!col_fits32<LOGN, C>()) {
         return cudaErrorInvalidValue;
     } else if constexpr (col_tma_fits<LOGN, C>()) {
-        using L = ColPlan<LOGN, C>;
-        auto k = k_col_tma<LOGN, C>;
+        using F = ColForm<LOGN, C>;
+        auto k = F::kernel();
+        constexpr int threads = F::threads;
         static std::atomic<unsigned long long> mask{0};
         static std::atomic<int> per_sm{0};
-        cudaError_t e = ensure_smem(k, L::total, mask);
+        cudaError_t e = ensure_smem(k, F::smem, mask);
         if (e != cudaSuccess) return e;
         const int ntiles = (1 << LOGN) / C;
-        const int grid = persistent_grid(k, C * Plan<LOGN>::T, L::total, ntiles, per_sm);
-        k<<<grid, C * Plan<LOGN>::T, L::total, s>>>(E, tw, h, *static_cast<const CUtensorMap *>(tmap), ntiles, err);
+        const int grid = persistent_grid(k, threads, F::smem, ntiles, per_sm);
+        k<<<grid, threads, F::smem, s>>>(E, tw, h, *static_cast<const CUtensorMap *>(tmap), ntiles, err);
         return cudaGetLastError();
     } else {
         cudaError_t e = col_attr<float, LOGN, C, MODE_DIFF>();
@@ -81,7 +82,7 @@ template <int LOGN, int C> static cudaError_t col_prep32_c()
         return cudaErrorInvalidValue;
     } else if constexpr (col_tma_fits<LOGN, C>()) {
         static std::atomic<unsigned long long> mask{0};
-        return ensure_smem(k_col_tma<LOGN, C>, ColPlan<LOGN, C>::total, mask);
+        return ensure_smem(ColForm<LOGN, C>::kernel(), ColForm<LOGN, C>::smem, mask);
     } else {
         return col_attr<float, LOGN, C, MODE_DIFF>();
     }

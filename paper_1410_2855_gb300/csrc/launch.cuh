@@ -34,6 +34,31 @@ template <int LOGN, int C> constexpr bool col_tma_fits()
     return col_fits32<LOGN, C>() && C >= 2 && ColPlan<LOGN, C>::total <= 227 * 1024;
 }
 
+// Form of the persistent column sweeps: 0 one column per thread
+// (k_col_tma), 1 column pairs with two stages and register tables
+// (k_col_pair), 2 column pairs with one stage, two or more blocks per SM
+// (k_col_pair1).  All three give the same bits.
+#ifndef RTK_COL_FORM
+#define RTK_COL_FORM 2
+#endif
+template <int LOGN, int C> struct ColForm {
+    static constexpr int form = RTK_COL_FORM;
+    static constexpr int threads = (form == 0 ? C : C / 2) * Plan<LOGN>::T;
+    static constexpr size_t smem = form == 2 ? ColStage1<LOGN, C>::total : ColPlan<LOGN, C>::total;
+    static constexpr auto kernel()
+    {
+        if constexpr (form == 2) return k_col_pair1<LOGN, C>;
+        else if constexpr (form == 1) return k_col_pair<LOGN, C>;
+        else return k_col_tma<LOGN, C>;
+    }
+    static constexpr auto batch_kernel()
+    {
+        if constexpr (form == 2) return k_col_pair1_batch<LOGN, C>;
+        else if constexpr (form == 1) return k_col_pair_batch<LOGN, C>;
+        else return k_col_tma_batch<LOGN, C>;
+    }
+};
+
 // Rows per block of the persistent row sweeps: one row from n = 1024 up,
 // else enough rows for 64 threads.
 template <int LOGN> constexpr int tma_lpc() { return Plan<LOGN>::T >= 64 ? 1 : 64 / Plan<LOGN>::T; }

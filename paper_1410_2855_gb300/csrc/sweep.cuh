@@ -124,7 +124,7 @@ k_row(const cv<R> *in, cv<R> *out, const cv<R> *__restrict__ tw, const cv<R> *__
     } else if constexpr (MODE == MODE_FWD) {
         fft_line<LOGN, -1, 1>(v, t, lb, tw, sync);
     } else {  // diffraction: the propagator is applied as the forward transform ends
-        fft_line<LOGN, -1, 1, false, false, true>(v, t, lb, tw, sync, h);
+        fft_line<LOGN, -1, 1, false, true>(v, t, lb, tw, sync, h);
         fft_line<LOGN, +1, 1>(v, t, lb, tw, sync);
     }
     V *dst = out + (size_t)row * N + t;
@@ -157,7 +157,7 @@ k_col(cv<R> *X, const cv<R> *__restrict__ tw, const cv<R> *__restrict__ h)
     } else if constexpr (MODE == MODE_FWD) {
         fft_line<LOGN, -1, C>(v, t, lb, tw, sync);
     } else {  // diffraction, as in the persistent sweeps
-        fft_line<LOGN, -1, C, false, false, true>(v, t, lb, tw, sync, h);
+        fft_line<LOGN, -1, C, false, true>(v, t, lb, tw, sync, h);
         fft_line<LOGN, +1, C>(v, t, lb, tw, sync);
     }
 #pragma unroll

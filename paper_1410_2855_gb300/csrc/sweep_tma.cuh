@@ -33,12 +33,6 @@ constexpr int ERR_TIMEOUT = -5;
 #define RTK_COL_PP 1
 #endif
 
-// 1: the propagator factors are loaded ahead of the forward transform's last
-// exchange and applied as its outputs come out.
-#ifndef RTK_H_PREFETCH
-#define RTK_H_PREFETCH 1
-#endif
-
 // TAB: the stage also carries the rows' N0 (pump table) values.
 template <int LOGN, int LPC, bool PP, bool TAB = false> struct RowStage {
     static constexpr int N = 1 << LOGN;
@@ -227,21 +221,25 @@ __device__ __forceinline__ float row_local_map(float2 (&v)[16], int t, int row, 
 }
 
 // Forward FFT, x h, inverse FFT of the line held in v (exchanges in lb).
+// The propagator factors are fetched ahead of the forward transform's last
+// exchange and applied as its outputs come out.
 template <int LOGN, int CS, bool PP, typename SyncF>
 __device__ __forceinline__ void diffract_line(float2 (&v)[16], int t, LineBufs<float2, PP> &lb,
                                               const float2 *__restrict__ tw, const float2 *__restrict__ h,
                                               SyncF sync)
 {
-#if RTK_H_PREFETCH
-    fft_line<LOGN, -1, CS, PP, false, true>(v, t, lb, tw, sync, h);
-#else
-    constexpr int T = Plan<LOGN>::T;
-    fft_line<LOGN, -1, CS>(v, t, lb, tw, sync);
-    const float2 *hp = h + t;
-#pragma unroll
-    for (int si = 0; si < 16; ++si) v[si] = cmul_rn(v[si], __ldg(hp + si * T));
-#endif
+    fft_line<LOGN, -1, CS, PP, true>(v, t, lb, tw, sync, h);
     fft_line<LOGN, +1, CS>(v, t, lb, tw, sync);
+}
+
+// The same with the tables in registers (TabRegs: twiddles, and the
+// propagator factors in tab.h).
+template <int LOGN, int CS, bool PP, typename V, typename SyncF>
+__device__ __forceinline__ void diffract_line_regs(V (&v)[16], int t, LineBufs<V, PP> &lb,
+                                                   const TabRegs<LOGN, float2> &tab, SyncF sync)
+{
+    fft_line_t<LOGN, -1, CS, PP, true>(v, t, lb, tab, sync);
+    fft_line_t<LOGN, +1, CS, PP, false>(v, t, lb, tab, sync);
 }
 
 // Per-resonator mean intensity of a batched row sweep.  A block keeps one
@@ -398,6 +396,164 @@ k_col_tma(float2 *E, const float2 *__restrict__ tw, const float2 *__restrict__ h
     }
 }
 
+// Column-pair sweep: the column sweep with each thread carrying two adjacent
+// columns of the tile (C/2 pairs per row, thread (c2, t), c2 fastest) and
+// every table in registers.  The twiddles are loaded once per block and the
+// propagator factors once per resonator, so no table load remains inside the
+// tile loop; the pairs move through shared and global memory as 16-byte
+// accesses, half the instructions of one column at a time.  The arithmetic
+// of each column is exactly that of k_col_tma (bit-identical fields).
+#ifndef RTK_PAIR_REGS
+#define RTK_PAIR_REGS 192
+#endif
+constexpr int pair_min_blocks(int threads, size_t bytes)
+{
+    return smem_blocks(bytes) < 65536 / (threads * RTK_PAIR_REGS)
+               ? smem_blocks(bytes)
+               : (65536 / (threads * RTK_PAIR_REGS) > 0 ? 65536 / (threads * RTK_PAIR_REGS) : 1);
+}
+
+template <int LOGN, int C, bool PP = RTK_COL_PP>
+__global__ void __launch_bounds__((C / 2) * Plan<LOGN>::T,
+                                  pair_min_blocks((C / 2) * Plan<LOGN>::T, ColStage<LOGN, C, PP>::total))
+k_col_pair(float2 *E, const float2 *__restrict__ tw, const float2 *__restrict__ h,
+           const __grid_constant__ CUtensorMap tmap, int ntiles, int *err)
+{
+    static_assert(C >= 2 && C % 2 == 0, "whole column pairs");
+    using P = Plan<LOGN>;
+    using L = ColStage<LOGN, C, PP>;
+    constexpr int N = P::N, T = P::T, CP = C / 2;
+    extern __shared__ __align__(128) unsigned char sm[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
+    const int c2 = threadIdx.x % CP, t = threadIdx.x / CP;
+    auto stage = [](int s) { return reinterpret_cast<cpair *>(sm + 128 + s * L::stage); };
+    auto sync = []() { __syncthreads(); };
+    auto issue = [&](int s, int tile) {
+        mbar_arrive_expect_tx(&bar[s], (uint32_t)(N * C * sizeof(float2)));
+        for (int b = 0; b < L::NBOX; ++b)
+            tma_load_2d(stage(s) + b * L::BR * CP, &tmap, 2 * tile * C, b * L::BR, &bar[s]);
+    };
+
+    init_stage_barriers(bar);
+    int tile = blockIdx.x;
+    if (threadIdx.x == 0 && tile < ntiles) issue(0, tile);
+    TabRegs<LOGN, float2> tab;
+    tab.load_tw(tw, t);
+    tab.load_post(h, t);
+    for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+        const int s = it & 1;
+        const int nxt = tile + (int)gridDim.x;
+        if (threadIdx.x == 0 && nxt < ntiles) {
+            fence_proxy_async_smem();
+            issue(s ^ 1, nxt);
+        }
+        if (stage_wait_or_abort(bar, it, nxt < ntiles, err)) break;
+        cpair *base = stage(s);
+        cpair v[16];
+#pragma unroll
+        for (int si = 0; si < 16; ++si) v[si] = base[(t + si * T) * CP + c2];
+        LineBufs<cpair, PP> lb{{PP ? stage(2) + c2 : base + c2, base + c2}, 0, err};
+        diffract_line_regs<LOGN, CP>(v, t, lb, tab, sync);
+        cpair *col = reinterpret_cast<cpair *>(E + (size_t)t * N + tile * C) + c2;
+#pragma unroll
+        for (int si = 0; si < 16; ++si) col[(size_t)si * T * (N / 2)] = v[si];
+        __syncthreads();  // stage s fully consumed before it is refilled
+    }
+}
+
+// One-stage column-pair sweep: one shared stage per block that serves as the
+// copy engine's destination and then, in place, as the exchange buffer (two
+// barriers per exchange), and the tables read from global memory where they
+// are used.  That keeps a block within ~70 KB of shared memory and 128
+// registers per thread, so two or more blocks share an SM: one block's
+// exchanges overlap another's arithmetic, and each block's next copy is
+// issued as soon as its last exchange has been read (before the inverse
+// transform's last pass and the store).  Bit-identical to k_col_pair.
+template <int LOGN, int C> struct ColStage1 {
+    static constexpr int N = 1 << LOGN;
+    static constexpr int BR = N < 256 ? N : 256;
+    static constexpr int NBOX = N / BR;
+    static constexpr size_t stage = round128((size_t)C * padded_len(N) * sizeof(float2));
+    static constexpr size_t total = 128 + stage;
+};
+#ifndef RTK_PAIR1_REGS
+#define RTK_PAIR1_REGS 128
+#endif
+constexpr int pair1_min_blocks(int threads, size_t bytes)
+{
+    return smem_blocks(bytes) < 65536 / (threads * RTK_PAIR1_REGS)
+               ? smem_blocks(bytes)
+               : (65536 / (threads * RTK_PAIR1_REGS) > 0 ? 65536 / (threads * RTK_PAIR1_REGS) : 1);
+}
+
+// Issue the copy of the next item into the (single) stage once every thread
+// has read its last exchange: a barrier, then thread 0 orders the shared
+// writes before the copy engine's (proxy fence) and starts the copy.
+template <typename IssueF> struct IssueAfterReads {
+    IssueF issue;
+    int next;
+    bool valid;
+    __device__ __forceinline__ void operator()() const
+    {
+        __syncthreads();
+        if (threadIdx.x == 0 && valid) {
+            fence_proxy_async_smem();
+            issue(next);
+        }
+    }
+};
+
+template <int LOGN, int C>
+__global__ void __launch_bounds__((C / 2) * Plan<LOGN>::T,
+                                  pair1_min_blocks((C / 2) * Plan<LOGN>::T, ColStage1<LOGN, C>::total))
+k_col_pair1(float2 *E, const float2 *__restrict__ tw, const float2 *__restrict__ h,
+            const __grid_constant__ CUtensorMap tmap, int ntiles, int *err)
+{
+    static_assert(C >= 2 && C % 2 == 0, "whole column pairs");
+    using P = Plan<LOGN>;
+    using L = ColStage1<LOGN, C>;
+    constexpr int N = P::N, T = P::T, CP = C / 2;
+    extern __shared__ __align__(128) unsigned char sm[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
+    cpair *base = reinterpret_cast<cpair *>(sm + 128);
+    const int c2 = threadIdx.x % CP, t = threadIdx.x / CP;
+    auto sync = []() { __syncthreads(); };
+    auto issue = [&](int tile) {
+        mbar_arrive_expect_tx(&bar[0], (uint32_t)(N * C * sizeof(float2)));
+        for (int b = 0; b < L::NBOX; ++b) tma_load_2d(base + b * L::BR * CP, &tmap, 2 * tile * C, b * L::BR, &bar[0]);
+    };
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    int tile = blockIdx.x;
+    if (threadIdx.x == 0 && tile < ntiles) issue(tile);
+#ifdef RTK_SKEW_NS
+    if (blockIdx.x >= gridDim.x / 2) __nanosleep(RTK_SKEW_NS);
+#endif
+    const TabGlobal<LOGN, float2> tab{tw, h};
+    for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+        const int nxt = tile + (int)gridDim.x;
+        const bool late = !mbar_wait(&bar[0], (uint32_t)(it & 1));
+        if (__syncthreads_or(late)) {  // the copy in flight is this one: nothing else to drain
+            if (threadIdx.x == 0) atomicExch(err, ERR_TIMEOUT);
+            break;
+        }
+        cpair v[16];
+#pragma unroll
+        for (int si = 0; si < 16; ++si) v[si] = base[(t + si * T) * CP + c2];
+        LineBufs<cpair, false> lb{{base + c2, base + c2}, 0, err};
+        fft_line_t<LOGN, -1, CP, false, true>(v, t, lb, tab, sync);
+        const IssueAfterReads<decltype(issue)> next{issue, nxt, nxt < ntiles};
+        fft_line_t<LOGN, +1, CP, false, false>(v, t, lb, tab, sync, next);
+        cpair *col = reinterpret_cast<cpair *>(E + (size_t)t * N + tile * C) + c2;
+#pragma unroll
+        for (int si = 0; si < 16; ++si) col[(size_t)si * T * (N / 2)] = v[si];
+    }
+}
+
 // ---- batches of resonators of one grid size -----------------------------------
 
 // Row sweep over nres resonators: item i is row group i % G of resonator
@@ -535,6 +691,123 @@ k_col_tma_batch(const BatchRes *__restrict__ res, int nres, const float2 *__rest
 #pragma unroll
         for (int si = 0; si < 16; ++si) col[(size_t)si * T * N] = v[si];
         __syncthreads();  // stage s fully consumed before it is refilled
+        item = nxt;
+    }
+}
+
+// Column-pair sweep over nres resonators of one grid size (as
+// k_col_tma_batch; twiddles in registers for the whole launch, propagator
+// factors reloaded whenever the block moves to another resonator).
+template <int LOGN, int C, bool PP = RTK_COL_PP>
+__global__ void __launch_bounds__((C / 2) * Plan<LOGN>::T,
+                                  pair_min_blocks((C / 2) * Plan<LOGN>::T, ColStage<LOGN, C, PP>::total))
+k_col_pair_batch(const BatchRes *__restrict__ res, int nres, const float2 *__restrict__ tw, int *err)
+{
+    static_assert(C >= 2 && C % 2 == 0, "whole column pairs");
+    using P = Plan<LOGN>;
+    using L = ColStage<LOGN, C, PP>;
+    constexpr int N = P::N, T = P::T, CP = C / 2, TILES = N / C;
+    extern __shared__ __align__(128) unsigned char sm[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
+    const int c2 = threadIdx.x % CP, t = threadIdx.x / CP;
+    const int nitems = nres * TILES;
+    auto stage = [](int s) { return reinterpret_cast<cpair *>(sm + 128 + s * L::stage); };
+    auto sync = []() { __syncthreads(); };
+    auto issue = [&](int s, int item) {
+        const CUtensorMap *map = res[item / TILES].tmap;
+        const int tile = item % TILES;
+        mbar_arrive_expect_tx(&bar[s], (uint32_t)(N * C * sizeof(float2)));
+        for (int b = 0; b < L::NBOX; ++b)
+            tma_load_2d(stage(s) + b * L::BR * CP, map, 2 * tile * C, b * L::BR, &bar[s]);
+    };
+    auto next_active = [&](int i) { return next_active_item(res, TILES, nitems, i); };
+
+    init_stage_barriers(bar);
+    int item = next_active(blockIdx.x);
+    if (threadIdx.x == 0 && item < nitems) issue(0, item);
+    TabRegs<LOGN, float2> tab;
+    tab.load_tw(tw, t);
+    int cur = -1;  // resonator whose propagator factors are in tab.h
+    for (int it = 0; item < nitems; ++it) {
+        const int s = it & 1;
+        const int nxt = next_active(item + (int)gridDim.x);
+        if (threadIdx.x == 0 && nxt < nitems) {
+            fence_proxy_async_smem();
+            issue(s ^ 1, nxt);
+        }
+        const int r = item / TILES;
+        const BatchRes &R = res[r];
+        if (r != cur) {
+            tab.load_post(R.h, t);
+            cur = r;
+        }
+        if (stage_wait_or_abort(bar, it, nxt < nitems, err)) break;
+        const int tile = item % TILES;
+        cpair *base = stage(s);
+        cpair v[16];
+#pragma unroll
+        for (int si = 0; si < 16; ++si) v[si] = base[(t + si * T) * CP + c2];
+        LineBufs<cpair, PP> lb{{PP ? stage(2) + c2 : base + c2, base + c2}, 0, err};
+        diffract_line_regs<LOGN, CP>(v, t, lb, tab, sync);
+        cpair *col = reinterpret_cast<cpair *>(R.E + (size_t)t * N + tile * C) + c2;
+#pragma unroll
+        for (int si = 0; si < 16; ++si) col[(size_t)si * T * (N / 2)] = v[si];
+        __syncthreads();  // stage s fully consumed before it is refilled
+        item = nxt;
+    }
+}
+
+// One-stage column-pair sweep over nres resonators of one grid size.
+template <int LOGN, int C>
+__global__ void __launch_bounds__((C / 2) * Plan<LOGN>::T,
+                                  pair1_min_blocks((C / 2) * Plan<LOGN>::T, ColStage1<LOGN, C>::total))
+k_col_pair1_batch(const BatchRes *__restrict__ res, int nres, const float2 *__restrict__ tw, int *err)
+{
+    static_assert(C >= 2 && C % 2 == 0, "whole column pairs");
+    using P = Plan<LOGN>;
+    using L = ColStage1<LOGN, C>;
+    constexpr int N = P::N, T = P::T, CP = C / 2, TILES = N / C;
+    extern __shared__ __align__(128) unsigned char sm[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
+    cpair *base = reinterpret_cast<cpair *>(sm + 128);
+    const int c2 = threadIdx.x % CP, t = threadIdx.x / CP;
+    const int nitems = nres * TILES;
+    auto sync = []() { __syncthreads(); };
+    auto issue = [&](int item) {
+        const CUtensorMap *map = res[item / TILES].tmap;
+        const int tile = item % TILES;
+        mbar_arrive_expect_tx(&bar[0], (uint32_t)(N * C * sizeof(float2)));
+        for (int b = 0; b < L::NBOX; ++b) tma_load_2d(base + b * L::BR * CP, map, 2 * tile * C, b * L::BR, &bar[0]);
+    };
+    auto next_active = [&](int i) { return next_active_item(res, TILES, nitems, i); };
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    int item = next_active(blockIdx.x);
+    if (threadIdx.x == 0 && item < nitems) issue(item);
+    for (int it = 0; item < nitems; ++it) {
+        const int nxt = next_active(item + (int)gridDim.x);
+        const BatchRes &R = res[item / TILES];
+        const int tile = item % TILES;
+        const bool late = !mbar_wait(&bar[0], (uint32_t)(it & 1));
+        if (__syncthreads_or(late)) {
+            if (threadIdx.x == 0) atomicExch(err, ERR_TIMEOUT);
+            break;
+        }
+        const TabGlobal<LOGN, float2> tab{tw, R.h};
+        cpair v[16];
+#pragma unroll
+        for (int si = 0; si < 16; ++si) v[si] = base[(t + si * T) * CP + c2];
+        LineBufs<cpair, false> lb{{base + c2, base + c2}, 0, err};
+        fft_line_t<LOGN, -1, CP, false, true>(v, t, lb, tab, sync);
+        const IssueAfterReads<decltype(issue)> next{issue, nxt, nxt < nitems};
+        fft_line_t<LOGN, +1, CP, false, false>(v, t, lb, tab, sync, next);
+        cpair *col = reinterpret_cast<cpair *>(R.E + (size_t)t * N + tile * C) + c2;
+#pragma unroll
+        for (int si = 0; si < 16; ++si) col[(size_t)si * T * (N / 2)] = v[si];
         item = nxt;
     }
 }

@@ -1,8 +1,9 @@
 """The reference arm of bench.py on the host: `--impl reference` times the FP64
-oracle on the headline workload (two 2048^2 resonators, one bounce each per
-step) and prints one JSON line with the same metric, unit and workload
-configuration as the GPU arm, the oracle described as the CPU baseline, and
-an end-to-end figure with no host-device traffic."""
+oracle on the headline workload (two 2048^2 resonators, a few bounces each
+per step, the oracle's per-call set-up timed apart) and prints one JSON line
+with the same metric, unit and workload configuration as the GPU arm, the
+oracle described as the CPU baseline, and an end-to-end figure with no
+host-device traffic."""
 import json
 import os
 import subprocess
@@ -23,7 +24,8 @@ def test_reference_arm_prints_the_contract_line():
     assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
     assert line["higher_is_better"] is True and line["n_gpus"] == 1
     assert line["steps"] == 1 and line["warmup"] == 0 and line["value"] > 0.0
-    assert line["config"] == bench.config_block(1, {"l2": "n/a (host)"})
+    assert line["config"] == bench.config_block()
+    assert line["bounces_per_step"] == bench.REF_BOUNCES_PER_STEP and line["oracle_setup_s_per_call"] > 0.0
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
     e2e = line["e2e"]
