@@ -8,8 +8,13 @@ z/F = 0.16 and the seeded 0.05 rad rms roughness of workloads.C2_CURVED).
 Beyond a few tens of bounces the map is chaotic, so the stored values are
 statistics that a faithful FP32 run must reproduce rather than the field
 itself: the mean intensity averaged over the last 1000 bounces, the mean
-intensity every 100 bounces, and the dominant spatial frequency of the final
-field (all bins, and bins with max(|mx|, |my|) >= 2), with m and -m folded.
+intensity every 100 bounces, the dominant spatial frequency of the final
+field (all bins, and bins with max(|mx|, |my|) >= 2), with m and -m folded,
+and the spectrum's ring fractions: the share of the power |DFT2(E)|^2 in
+each Chebyshev ring max(|mx|, |my|) = 0, [1, 2), [2, 4), ... of doubling
+radius, at each of the ten snapshots 100 bounces apart that end the run, with
+their mean over the snapshots and the largest distance of one snapshot from
+that mean (the spread of a single sample of the attractor).
 
 Calls only the oracle:  python tests/golden/make_longrun.py [flat|curved] [threads]
 """
@@ -27,6 +32,21 @@ import oracle as orc  # noqa: E402
 from paper_1410_2855_gb300 import workloads as wl  # noqa: E402
 
 
+def ring_fractions(S):
+    """Share of the spectral power in each Chebyshev ring of doubling radius
+    (signed frequencies: ring 0 is the DC bin, ring k >= 1 holds
+    2^(k-1) <= max(|mx|, |my|) < 2^k, the last ring includes n/2)."""
+    n = S.shape[0]
+    m = np.abs(np.fft.fftfreq(n, 1.0 / n)).astype(np.int64)
+    rho = np.maximum(m[:, None], m[None, :])
+    k = np.zeros_like(rho)
+    nz = rho > 0
+    k[nz] = np.floor(np.log2(rho[nz])).astype(np.int64) + 1
+    k = np.minimum(k, int(np.log2(n // 2)))
+    tot = float(S.sum())
+    return [float(S[k == r].sum()) / tot for r in range(int(np.log2(n // 2)) + 1)]
+
+
 def main():
     case = sys.argv[1] if len(sys.argv) > 1 else "flat"
     threads = int(sys.argv[2]) if len(sys.argv) > 2 else (os.cpu_count() or 1)
@@ -36,7 +56,15 @@ def main():
                         roughness=c.roughness())
     E, N = orc.init_state(p, c.seed, c.noise_amp)
     t0 = time.time()
-    E, N, hist = orc.run(p, E, N, nb, nthreads=threads)
+    snaps, every = 10, 100
+    E, N, hist = orc.run(p, E, N, nb - snaps * every, nthreads=threads)
+    hists, fracs = [hist], []
+    for _ in range(snaps):
+        E, N, h = orc.run(p, E, N, every, nthreads=threads)
+        hists.append(h)
+        fracs.append(ring_fractions(orc.spectrum(E, nthreads=threads)))
+    hist = np.concatenate(hists)
+    fracs = np.array(fracs)
     S = orc.spectrum(E, nthreads=threads)
     peaks = {}
     for ring in (0, 2):
@@ -54,6 +82,10 @@ def main():
         "final_mean_intensity": float(hist[-1]),
         "final_mean_inversion": float(np.mean(N)),
         "peaks": peaks,
+        "ring_fractions": {"rings": "max(|mx|,|my|) = 0, [1,2), [2,4), ..., [n/4, n/2]",
+                           "snapshot_bounces": [nb - snaps * every + every * (k + 1) for k in range(snaps)],
+                           "snapshots": fracs.tolist(), "mean": fracs.mean(axis=0).tolist(),
+                           "spread": np.abs(fracs - fracs.mean(axis=0)).max(axis=0).tolist()},
         "oracle_seconds": round(time.time() - t0, 1),
         "threads": threads,
     }

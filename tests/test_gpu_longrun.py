@@ -3,18 +3,32 @@ R = 0.95), with a flat mirror and with the paper's curved, rough mirror, run
 for 1e4 bounces from the seeded noise start.  The map is chaotic well before
 that, so the FP32 and FP64 GPU paths are held to the statistics the FP64
 oracle fixed in tests/golden/longrun_512*.json (written by
-tests/golden/make_longrun.py): the mean intensity over the last 1000 bounces
-within 1%, and the dominant spatial frequency (m and -m folded) exactly,
-unless the oracle's runner-up is within 1e-3 of its peak.  Where the final
-spectrum has no dominant peak (runner-up above half the peak, as with the
-curved mirror) only the mean intensity is compared."""
+tests/golden/make_longrun.py):
+
+- the mean intensity over the last 1000 bounces within 1%;
+- the dominant spatial frequency (m and -m folded) exactly, unless the
+  oracle's runner-up is within 1e-3 of its peak; where the final spectrum
+  has no dominant peak (runner-up above half the peak, as with the curved
+  mirror) the argmax is not compared;
+- the spectrum's ring fractions (the share of |DFT2(E)|^2 in each Chebyshev
+  ring max(|mx|, |my|) = 0, [1, 2), [2, 4), ...), averaged over the ten
+  snapshots 100 bounces apart that end the run: each ring within twice the
+  oracle's own single-snapshot spread plus 0.01.  The GPU run is another
+  trajectory on the same attractor, so its average is a second estimate of
+  the same time average; the oracle's snapshots fix how far one estimate
+  strays, and the margin covers the difference of two.  This pins the
+  spatial structure where no single peak dominates."""
 import json
 import os
+import sys
 
 import numpy as np
 import pytest
 
 from paper_1410_2855_gb300 import build, rt, workloads as wl
+
+sys.path.insert(0, os.path.join(os.path.dirname(__file__), "golden"))
+from make_longrun import ring_fractions  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -26,8 +40,15 @@ def test_long_run_statistics_match_oracle(precision, case):
     build.build()
     g = json.load(open(os.path.join(GOLDEN, "longrun_512.json" if case == "flat" else "longrun_512_curved.json")))
     c = wl.C2 if case == "flat" else wl.C2_CURVED
+    rf = g["ring_fractions"]
+    snaps = rf["snapshot_bounces"]
+    fracs = []
     with rt.Resonator.from_params(c, precision=precision, history_cap=20000, chunk=500) as r:
-        r.step(g["bounces"])
+        r.step(snaps[0] - (snaps[1] - snaps[0]))
+        for b in snaps:
+            r.step(b - r.stats().bounces)
+            fracs.append(ring_fractions(r.spectrum().astype(np.float64)))
+        assert r.stats().bounces == g["bounces"]
         hist = r.history(g["bounces"])
         peaks = {ring: r.peak(ring) for ring in (0, 2)}
     assert len(hist) == g["bounces"] and np.all(np.isfinite(hist))
@@ -39,3 +60,6 @@ def test_long_run_statistics_match_oracle(precision, case):
             continue                                     # no dominant peak to compare
         tie = ref["runner_up"] >= (1.0 - 1e-3) * ref["power"]
         assert tie or (mx, my) == (ref["mx"], ref["my"]), (ring, mx, my, ref)
+    got = np.mean(np.array(fracs), axis=0)
+    want, spread = np.array(rf["mean"]), np.array(rf["spread"])
+    assert np.all(np.abs(got - want) <= 2.0 * spread + 0.01), (got.tolist(), want.tolist(), spread.tolist())
