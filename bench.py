@@ -231,6 +231,70 @@ def oracle_rate(params_list, E0s, N0s, budget_s=12.0, horizons=(1, 20)):
     return done / t_total, threads, done, fields, statistics.mean(setup)
 
 
+def radix_passes(n: int, order: int) -> str:
+    """The radix sequence of a column transform of side n in radix order
+    `order` (16s with the small pass last, first or second), e.g. "16.16.8"."""
+    logn = n.bit_length() - 1
+    p = [16] * (logn // 4)
+    if logn % 4:
+        p.insert(len(p) if order == 0 else (0 if order == 1 or len(p) < 2 else 1), 1 << (logn % 4))
+    return ".".join(map(str, p))
+
+
+def multi_stream_rate(rt, torch, params, B, steps=3):
+    """Round trips/s of len(params) resonators, each on its own stream with
+    graphs of B bounces, stepped together; L2 flushed before each timed step."""
+    main = torch.cuda.Stream()
+    streams = [torch.cuda.Stream() for _ in params]
+    res = [rt.Resonator.from_params(p, cuda_stream=s.cuda_stream, chunk=B) for p, s in zip(params, streams)]
+    fork = Fork(torch, main, streams)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def step():
+        fork.begin()
+        for r in res:
+            rt.rt_step(r.h, B)
+        fork.end()
+
+    with torch.cuda.stream(main):
+        step()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(main)
+            step()
+            b.record(main)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+    for r in res:
+        r.sync()
+        r.close()
+    return len(params) * B * steps / (sum(ms) / 1e3)
+
+
+def graph_sweep_ms(rt, torch, r, stream, kind, reps=100):
+    """Average duration of one sweep of `kind`: a CUDA graph of reps back-to-back
+    launches on the resonator's stream, events around a replay."""
+    for _ in range(3):
+        rt.rt_sweep(r.h, kind)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        for _ in range(reps):
+            rt.rt_sweep(r.h, kind)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        g.replay()
+        a.record(stream)
+        g.replay()
+        b.record(stream)
+    torch.cuda.synchronize()
+    del g
+    return a.elapsed_time(b) / reps
+
+
 def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a, np.complex128) - b) / np.linalg.norm(b))
 
@@ -483,8 +547,11 @@ def run_ours(args):
         tune.rt_tune_set(params[0].n, args.col_tile)
         col_tile, tile_source = args.col_tile, "fixed on the command line"
     else:
-        col_tile, _ = tune.rt_autotune(params[0].n, reps=50)   # column-sweep tile width for this GPU
+        # column-sweep tile width and radix order for this GPU (2048^2 and the larger-than-L2 4096^2)
+        col_tile, _ = tune.rt_autotune(params[0].n, reps=50)
+        tune.rt_autotune(4096, reps=20)
         tile_source = "autotuned at start-up"
+    col_order = tune.rt_tune_get_order(params[0].n)[0]
     streams = [torch.cuda.Stream(device=dev) for _ in params]
     res = [rt.Resonator.from_params(p, precision=rt.RT_FP32, cuda_stream=s.cuda_stream, chunk=B)
            for p, s in zip(params, streams)]
@@ -589,7 +656,10 @@ def run_ours(args):
         "config": config_block(),
         "bounces_per_step": B,
         "launch": {"graph": f"one CUDA graph per {B} bounces per resonator",
-                   "streams": "one per resonator, concurrent", "col_tile": col_tile, "col_tile_source": tile_source},
+                   "streams": "one per resonator, concurrent", "col_tile": col_tile, "col_tile_source": tile_source,
+                   "col_radix_order": col_order,
+                   "col_radix_passes": radix_passes(params[0].n, col_order),
+                   "batch_launch": "autotuned in the batch_sweep leg"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": dom_gbs, "peak": peak, "unit": "GB/s",
                      "frac": dom_gbs / peak, "peak_kind": f"of {peak_kind}",
                      "traffic": profiled_traffic(dom, params[0].n),
@@ -609,6 +679,13 @@ def run_ours(args):
 
     if not args.no_comparisons:
         out.update(comparisons(args, rt, torch, main, streams, params, res, E0, N0, rank, world))
+        big = out["larger_than_l2"]["two_4096"]
+        # the case whose state really streams through HBM, as a second roofline entry
+        out["roofline"]["larger_than_l2"] = {
+            "bound": "hbm", "kernel": "bounce (column + row sweep) of two 4096^2 resonators on two streams",
+            "achieved": big["bounce_gbs"], "peak": peak, "unit": "GB/s", "frac": big["bounce_hbm_frac"],
+            "peak_kind": f"of {peak_kind}", "algorithmic_bytes_per_bounce": 40 * 4096 ** 2, "traffic": None,
+            "timing": "CUDA events around steps of 100 bounces per resonator, L2 flushed before each step"}
     if world > 1:
         torch.distributed.barrier()
     for r in res:
@@ -620,6 +697,7 @@ def run_ours(args):
 
 
 def comparisons(args, rt, torch, main, streams, params, res, E0, N0, rank, world):
+    from paper_1410_2855_gb300 import tune
     B = args.bounces_per_step
     extra = {}
     P = params[0].n ** 2
@@ -727,26 +805,36 @@ def comparisons(args, rt, torch, main, streams, params, res, E0, N0, rank, world
     extra["extensions"]["workload"] = ("2048^2, N_F 1000, g0 0.3, R 0.9, one stream; field_at and the pattern "
                                        "include the host copy / synchronisation (wall clock)")
 
-    # ---- a resonator larger than L2: 4096^2 (192 MiB of state), one stream
-    big = dataclasses.replace(base, n=4096, fresnel=4000.0)
-    with torch.cuda.stream(main):
-        with rt.Resonator.from_params(big, cuda_stream=main.cuda_stream, chunk=100) as r:
-            r.step(100)
-            torch.cuda.synchronize()
-            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s.record(main)
-            r.step(300)
-            e.record(main)
-            torch.cuda.synchronize()
-            r.sync()
-            rate = 300 / (s.elapsed_time(e) / 1e3)
-    peak, _ = measured_peak()
-    extra["larger_than_l2"] = {"workload": "one 4096^2 resonator (N_F 4000, g0 0.3, R 0.9): 192 MiB of state "
-                                           "against a 126 MB L2; one stream, graphs of 100 bounces",
-                               "round_trips_per_s": rate, "bounce_hbm_frac": 40 * 4096 ** 2 * rate / 1e9 / peak}
+    # ---- state larger than L2 (126 MB): the bounce streams its state through HBM
+    peak, peak_kind = measured_peak()
+    big = [dataclasses.replace(base, n=4096, fresnel=4000.0, seed=base.seed + 100 + i) for i in range(2)]
+    four = [dataclasses.replace(base, seed=base.seed + 200 + i) for i in range(4)]
+    rate_big = multi_stream_rate(rt, torch, big, 100)
+    rate_one = multi_stream_rate(rt, torch, big[:1], 100)
+    rate_four = multi_stream_rate(rt, torch, four, B // 5)
+    st = torch.cuda.Stream()
+    with rt.Resonator.from_params(big[0], cuda_stream=st.cuda_stream, chunk=0) as r:
+        col4 = graph_sweep_ms(rt, torch, r, st, rt.RT_SWEEP_COLUMNS)
+        row4 = graph_sweep_ms(rt, torch, r, st, rt.RT_SWEEP_ROWS)
+    P4 = 4096 ** 2
+    extra["larger_than_l2"] = {
+        "two_4096": {"workload": "two 4096^2 resonators (N_F 4000, g0 0.3, R 0.9) on two streams: 384 MiB of "
+                                 "state against a 126 MB L2; graphs of 100 bounces",
+                     "round_trips_per_s": rate_big, "bounce_gbs": 40 * P4 * rate_big / 1e9,
+                     "bounce_hbm_frac": 40 * P4 * rate_big / 1e9 / peak},
+        "one_4096": {"round_trips_per_s": rate_one, "bounce_hbm_frac": 40 * P4 * rate_one / 1e9 / peak},
+        "four_2048": {"workload": "four 2048^2 resonators on four streams (192 MiB of state), graphs of "
+                                  f"{B // 5} bounces", "round_trips_per_s": rate_four,
+                      "bounce_hbm_frac": 40 * P * rate_four / 1e9 / peak},
+        "sweeps_4096": {"column_ms": col4, "column_frac": COL_BYTES_PER_PT * P4 / (col4 / 1e3) / 1e9 / peak,
+                        "row_ms": row4, "row_frac": ROW_BYTES_PER_PT * P4 / (row4 / 1e3) / 1e9 / peak,
+                        "col_tile": tune.rt_tune_get(4096)[0], "timing": "graph of 100 back-to-back launches"},
+        "peak_kind": f"of {peak_kind}"}
 
-    # ---- batched parameter sweep: 256 resonators of side 256/512/1024 in one graph per 100 bounces
+    # ---- batched parameter sweep: 256 resonators of side 256/512/1024 in one graph per 100 bounces;
+    # the launch form (one launch per sweep across sizes, or one per size class) autotuned first
     jobs = wl.batch_sweep(count=256, sides=(256, 512, 1024))
+    form = tune.autotune_batch(jobs, bounces=100, cuda_stream=main.cuda_stream)
     with torch.cuda.stream(main):
         with rt.Batch(jobs, chunk=100, history_cap=128, cuda_stream=main.cuda_stream) as bt:
             bt.step(100)
@@ -764,7 +852,10 @@ def comparisons(args, rt, torch, main, streams, params, res, E0, N0, rank, world
                 "workload": "256 resonators, sides uniform over {256,512,1024}, N_F log-uniform [100,1000], "
                             "g0 U[0.1,0.3], T1 U[1e3,1e4], R=0.95; one CUDA graph per 100 bounces",
                 "round_trips_per_s": len(jobs) * 200 / secs, "point_bounces_per_s": Pb * 200 / secs,
-                "hbm_frac": 40 * Pb * 200 / secs / 1e9 / peak, "footprint_bytes": bt.footprint()}
+                "hbm_frac": 40 * Pb * 200 / secs / 1e9 / peak, "footprint_bytes": bt.footprint(),
+                "launch_form": "one launch per sweep across sizes (3 graph branches)" if form["mixed"]
+                else "one launch per sweep and size class (3 graph branches per class)",
+                "autotune_round_trips_per_s": form["round_trips_per_s"]}
 
     # ---- serving: the first requests of the seeded 50 req/s Poisson stream
     # (several times what the GPU can serve: latency there is the backlog),

@@ -263,17 +263,38 @@ rt_status rt_spectrum_peak(rt_handle *h, int ring, int *mx, int *my, double *pow
 /* ---- autotuning ---------------------------------------------------------
  * The column sweep's tile width (columns per block: 2, 4, 8 or 16) trades
  * load balance and copy-engine box width against shared memory and
- * occupancy.  rt_autotune times the sweep of a scratch n x n FP32 resonator
- * on the current device for every width that fits (reps launches each,
- * CUDA events) and records the fastest for this process; handles, batches
- * and servers created afterwards with col_tile = 0 use it.  rt_tune_set
- * records a width directly (e.g. loaded from a JSON cache file by the
- * Python binding); rt_tune_get reports the width in use for n (tuned, or
- * the built-in default; *tuned says which).  Not part of the paper's
- * method. */
+ * occupancy, and its radix order decides where the one pass of radix 2, 4
+ * or 8 goes when 4 does not divide log2 n (order 0: after the radix-16
+ * passes; 1: first; 2: second, after one radix-16 pass), which changes the
+ * exchange and twiddle pattern.  rt_autotune times the column sweep of a
+ * scratch n x n field on the current device for every width that fits and
+ * every order (reps launches each, CUDA events) and records the fastest pair
+ * for this process; handles created afterwards with col_tile = 0 use both
+ * (batches and servers use the width).  rt_tune_set / rt_tune_set_order
+ * record a width or an order directly (e.g. loaded from a JSON cache file by
+ * the Python binding); rt_tune_get reports the width in use for n (tuned,
+ * or the built-in default; *tuned says which) and rt_tune_get_order the
+ * order and the number of orders n offers.  Every order computes the same
+ * DFT; the roundings differ.  Not part of the paper's method. */
 rt_status rt_autotune(int n, int reps, int *best_col_tile, double *best_us);
 rt_status rt_tune_set(int n, int col_tile);
 rt_status rt_tune_get(int n, int *col_tile, int *tuned);
+rt_status rt_tune_set_order(int n, int order);
+rt_status rt_tune_get_order(int n, int *order, int *orders);
+
+/* Launch form of batches and servers created afterwards.  mixed = 1:
+ * resonators of sides 128..2048 share one persistent launch per sweep
+ * whatever their sizes; every work item holds the same number of points
+ * (column tiles of 8192/n columns, row groups of 2048/n rows) and is
+ * dispatched on its grid size inside the launch, so the classes fill one
+ * another's tails (batches split their resonators into three such launches,
+ * one per graph branch).  mixed = 0 (the default): one launch per sweep and
+ * size class, column tiles of the tuned width, three branches per class.
+ * Batches created with a nonzero col_tile always use per-class launches.
+ * The fields are the same either way; the Python binding's
+ * tune.autotune_batch times both on a batch and keeps the faster. */
+rt_status rt_tune_set_batch_mixed(int mixed);
+rt_status rt_tune_get_batch_mixed(int *mixed);
 
 /* ---- batches of resonators ---------------------------------------------
  * Many independent resonators (eq. conv_map per resonator, each with its

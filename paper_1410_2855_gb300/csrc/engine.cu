@@ -1,6 +1,7 @@
 // Shared by batches and the server (engine.h): slot set-up, the batched
 // bounce launches, and their capture into graphs with one branch per part
 // of a size class.
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstring>
@@ -187,14 +188,66 @@ cudaError_t slot_set_target(BatchRes *d_desc, long long target, cudaStream_t s)
     return cudaMemcpyAsync(&d_desc->target, &target, sizeof(target), cudaMemcpyHostToDevice, s);
 }
 
-cudaError_t enqueue_classes_bounce(const std::vector<ClassLaunch> &cls, int *err, cudaStream_t s)
+static std::atomic<bool> g_batch_mixed{false};
+bool batch_mixed() { return g_batch_mixed.load(); }
+void set_batch_mixed(bool on) { g_batch_mixed.store(on); }
+
+int class_col_tile(int logn, int requested, bool *mixed)
+{
+    *mixed = requested == 0 && batch_mixed() && mix_supported(logn);
+    if (*mixed) return mix_col_tile(logn);
+    return requested ? requested : default_col_tile32(logn);
+}
+
+static std::vector<MixLaunch> mixed_of(const std::vector<ClassLaunch> &cls)
+{
+    std::vector<MixLaunch> m;
+    for (const ClassLaunch &c : cls)
+        if (c.mixed && c.nres > 0) m.push_back({c.logn, c.d_res, c.nres, c.tw});
+    return m;
+}
+
+static std::vector<ClassLaunch> unmixed_of(const std::vector<ClassLaunch> &cls)
+{
+    std::vector<ClassLaunch> r;
+    for (const ClassLaunch &c : cls)
+        if (!c.mixed) r.push_back(c);
+    return r;
+}
+
+cudaError_t enqueue_sweep(const std::vector<ClassLaunch> &cls, int which, int *err, cudaStream_t s)
 {
     cudaError_t e;
-    for (const ClassLaunch &c : cls)
-        if ((e = launch_col_batch32(c.logn, c.colC, c.d_res, c.nres, c.tw, err, s)) != cudaSuccess) return e;
-    for (const ClassLaunch &c : cls)
-        if ((e = launch_row_batch32(c.logn, c.d_res, c.nres, c.tw, err, s)) != cudaSuccess) return e;
+    const std::vector<MixLaunch> m = mixed_of(cls);
+    if (!m.empty()) {
+        e = which == RT_SWEEP_COLUMNS ? launch_col_mixed32(m.data(), (int)m.size(), err, s)
+                                      : launch_row_mixed32(m.data(), (int)m.size(), err, s);
+        if (e != cudaSuccess) return e;
+    }
+    for (const ClassLaunch &c : cls) {
+        if (c.mixed) continue;
+        e = which == RT_SWEEP_COLUMNS ? launch_col_batch32(c.logn, c.colC, c.d_res, c.nres, c.tw, err, s)
+                                      : launch_row_batch32(c.logn, c.d_res, c.nres, c.tw, err, s);
+        if (e != cudaSuccess) return e;
+    }
     return cudaSuccess;
+}
+
+cudaError_t enqueue_classes_bounce(const std::vector<ClassLaunch> &cls, int *err, cudaStream_t s)
+{
+    cudaError_t e = enqueue_sweep(cls, RT_SWEEP_COLUMNS, err, s);
+    return e == cudaSuccess ? enqueue_sweep(cls, RT_SWEEP_ROWS, err, s) : e;
+}
+
+cudaError_t prepare_classes(const std::vector<ClassLaunch> &cls)
+{
+    cudaError_t e;
+    bool any_mixed = false;
+    for (const ClassLaunch &c : cls) {
+        if (c.mixed) any_mixed = true;
+        else if ((e = prepare_batch32(c.logn, c.colC)) != cudaSuccess) return e;
+    }
+    return any_mixed ? prepare_mixed32() : cudaSuccess;
 }
 
 
@@ -219,9 +272,38 @@ static std::vector<ClassLaunch> class_parts(const std::vector<ClassLaunch> &cls,
     return out;
 }
 
+// The mixed classes split into up to `split` parts: part q holds the q-th
+// share of the resonators of every mixed class, so each part is one launch
+// per sweep across sizes and the parts (on their own graph branches) fill
+// one another's phases and tails.
+static std::vector<std::vector<MixLaunch>> mixed_parts(const std::vector<ClassLaunch> &cls, int split)
+{
+    const std::vector<MixLaunch> m = mixed_of(cls);
+    int most = 0;
+    for (const MixLaunch &c : m) most = c.nres > most ? c.nres : most;
+    const int parts = most == 0 ? 0 : (split < 1 ? 1 : (most < split ? most : split));
+    std::vector<std::vector<MixLaunch>> out(parts);
+    for (const MixLaunch &c : m) {
+        int first = 0;
+        for (int q = 0; q < parts; ++q) {
+            const int cnt = c.nres / parts + (q < c.nres % parts ? 1 : 0);
+            if (cnt > 0) out[q].push_back({c.logn, c.res + first, cnt, c.tw});
+            first += cnt;
+        }
+    }
+    return out;
+}
+
+// Chains of a capture: the parts of the mixed launches, then the parts of
+// the other classes.
+static size_t chain_count(const std::vector<ClassLaunch> &cls, int split)
+{
+    return mixed_parts(cls, split).size() + class_parts(unmixed_of(cls), split).size();
+}
+
 cudaError_t branches_prepare(Branches &br, const std::vector<ClassLaunch> &cls, int split)
 {
-    const size_t nb = class_parts(cls, split).size();
+    const size_t nb = chain_count(cls, split);
     const size_t want = nb > 1 ? nb - 1 : 0;
     if (want > 0 && !br.fork) {
         cudaError_t e = cudaEventCreateWithFlags(&br.fork, cudaEventDisableTiming);
@@ -262,21 +344,37 @@ static cudaError_t enqueue_class_chain(const ClassLaunch &c, int *err, long long
     return e;
 }
 
+static cudaError_t enqueue_mixed_chain(const std::vector<MixLaunch> &m, int *err, long long k, cudaStream_t s)
+{
+    cudaError_t e = cudaSuccess;
+    for (long long i = 0; i < k && e == cudaSuccess; ++i) {
+        e = launch_col_mixed32(m.data(), (int)m.size(), err, s);
+        if (e == cudaSuccess) e = launch_row_mixed32(m.data(), (int)m.size(), err, s);
+    }
+    return e;
+}
+
 cudaError_t capture_class_bounces(const std::vector<ClassLaunch> &classes, int *err, long long k, cudaStream_t cap,
                                   Branches &br, int split)
 {
-    const std::vector<ClassLaunch> cls = class_parts(classes, split);
-    if (cls.empty()) return cudaSuccess;
-    if (cls.size() == 1) return enqueue_class_chain(cls[0], err, k, cap);
-    if (br.streams.size() < cls.size() - 1 || !br.fork) return cudaErrorInvalidValue;
+    const std::vector<std::vector<MixLaunch>> mix = mixed_parts(classes, split);
+    const std::vector<ClassLaunch> cls = class_parts(unmixed_of(classes), split);
+    const size_t chains = mix.size() + cls.size();
+    // chain j: the mixed parts first, then the parts of the other classes
+    auto chain = [&](size_t j, cudaStream_t s) {
+        if (j < mix.size()) return enqueue_mixed_chain(mix[j], err, k, s);
+        return enqueue_class_chain(cls[j - mix.size()], err, k, s);
+    };
+    if (chains == 0) return cudaSuccess;
+    if (chains == 1) return chain(0, cap);
+    if (br.streams.size() < chains - 1 || !br.fork) return cudaErrorInvalidValue;
     cudaError_t e = cudaEventRecord(br.fork, cap);
     if (e != cudaSuccess) return e;
     size_t joined = 0;  // branches forked into the capture
-    for (size_t j = 1; j < cls.size() && e == cudaSuccess; ++j)
+    for (size_t j = 1; j < chains && e == cudaSuccess; ++j)
         if ((e = cudaStreamWaitEvent(br.streams[j - 1], br.fork, 0)) == cudaSuccess) ++joined;
-    if (e == cudaSuccess) e = enqueue_class_chain(cls[0], err, k, cap);
-    for (size_t j = 1; j < cls.size() && e == cudaSuccess; ++j)
-        e = enqueue_class_chain(cls[j], err, k, br.streams[j - 1]);
+    if (e == cudaSuccess) e = chain(0, cap);
+    for (size_t j = 1; j < chains && e == cudaSuccess; ++j) e = chain(j, br.streams[j - 1]);
     // join every branch that was forked, whatever happened
     for (size_t j = 0; j < joined; ++j) {
         cudaError_t je = cudaEventRecord(br.join[j], br.streams[j]);

@@ -59,16 +59,34 @@ cudaError_t slot_start(const rt_job &job, const SlotBufs &b, int colC, float2 *c
 // Set only the bounce target of a slot's descriptor (stops or idles it).
 cudaError_t slot_set_target(BatchRes *d_desc, long long target, cudaStream_t s);
 
-// Grid sizes of one persistent batched launch set.
+// Grid sizes of one persistent batched launch set.  `mixed`: the class runs
+// in the launches shared by every mixed class (one per sweep across sizes;
+// its tensor maps use mix_col_tile columns); otherwise it has its own.
 struct ClassLaunch {
     int logn, colC;
     const BatchRes *d_res;
     int nres;
     const float2 *tw;
+    bool mixed = false;
 };
+
+// Process-wide choice for batches and servers created from now on: classes
+// of sides 128..2048 share one launch per sweep (true) or each class gets its
+// own launches (false, the default: measured faster for the 256-resonator
+// sweep, 209k against 198k round trips/s, because three branches per class
+// overlap more than three mixed ones).
+bool batch_mixed();
+void set_batch_mixed(bool on);
+// Column tile width of a new class of side 2^logn: the mixed width when the
+// class runs mixed, else `requested` (0: the tuned or built-in width).
+int class_col_tile(int logn, int requested, bool *mixed);
 
 // One bounce of every class: all column sweeps, then all row sweeps.
 cudaError_t enqueue_classes_bounce(const std::vector<ClassLaunch> &cls, int *err, cudaStream_t s);
+// One sweep (RT_SWEEP_COLUMNS or RT_SWEEP_ROWS) of every class.
+cudaError_t enqueue_sweep(const std::vector<ClassLaunch> &cls, int which, int *err, cudaStream_t s);
+// Kernel attributes (shared memory) of every launch the classes use.
+cudaError_t prepare_classes(const std::vector<ClassLaunch> &cls);
 
 // Side streams and fork/join events for capturing graph branches: one per
 // size class, or per part of one (class_parts).  Created before a capture

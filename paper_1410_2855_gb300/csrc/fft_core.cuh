@@ -201,6 +201,8 @@ template <int DIR, typename V> __device__ __forceinline__ void dft4(V &a0, V &a1
     a3 = csub(t1, t3);
 }
 
+template <int RAD, int DIR, typename V> __device__ __forceinline__ void dft_dif(V (&v)[RAD]);
+
 // In-register DFT of size RAD (2, 4, 8, 16): X[k] = sum_j x[j] exp(DIR 2 pi i jk/RAD).
 // Size 16 is split 4 x 4 (j = 4 j1 + j2, k = k1 + 4 k2): radix-4 DFTs over
 // j1, the factors exp(DIR 2 pi i j2 k1 / 16), radix-4 DFTs over j2; eight
@@ -227,9 +229,18 @@ __device__ __forceinline__ void dft(V (&v)[RAD])
             for (int k2 = 0; k2 < 4; ++k2) t[k1 + 4 * k2] = v[4 * k1 + k2];
 #pragma unroll
         for (int k = 0; k < 16; ++k) v[k] = t[k];
-        return;
-    }
+    } else
 #endif
+    {
+        dft_dif<RAD, DIR>(v);
+    }
+}
+
+// Radix-2 decimation in frequency of size RAD, then the bit-reversal
+// reordering (register renaming) back to natural order.
+template <int RAD, int DIR, typename V>
+__device__ __forceinline__ void dft_dif(V (&v)[RAD])
+{
 #pragma unroll
     for (int half = RAD / 2; half >= 1; half >>= 1) {
 #pragma unroll
@@ -316,46 +327,64 @@ __device__ __forceinline__ cpair cmul_rn(cpair x, float2 w) { return {cmul_rn(x.
 template <typename V> struct table_of { using type = V; };
 template <> struct table_of<cpair> { using type = float2; };
 
-// Offset of pass p's block in the pass-major twiddle table (passes p >= 1;
-// p = P16 is the trailing pass).
-template <int LOGN> __host__ __device__ constexpr int tw_pass_off(int p)
-{
-    int s = 0, Ns = 16;
-    for (int q = 1; q < p; ++q, Ns *= 16) s += 15 * Ns;
-    return s;
-}
+// ---- radix sequences --------------------------------------------------------
+// A line of 2^LOGN points is transformed in P16 = floor(LOGN/4) passes of
+// radix 16 and, when 4 does not divide LOGN, one pass of radix 2^(LOGN mod 4).
+// ORDER places that small pass: 0 last, 1 first, 2 second (after one radix-16
+// pass).  Pass p has radix R_p and span Ns_p = R_0 ... R_(p-1); its butterfly
+// j (0 <= j < N/R_p) combines x[j + k N/R_p], k < R_p, after multiplying
+// input k by exp(-2 pi i (j mod Ns_p) k / (Ns_p R_p)), and writes output r to
+// position (j / Ns_p) Ns_p R_p + (j mod Ns_p) + r Ns_p (Stockham autosort):
+// after the last pass the line is in natural order.  A thread holds 16
+// values and runs 16 / R_p butterflies j = t + i T of each pass.
+template <int LOGN, int ORDER = 0> struct Seq {
+    static constexpr int N = 1 << LOGN;
+    static constexpr int P16 = LOGN / 4, LASTLOG = LOGN % 4;
+    static constexpr int NP = P16 + (LASTLOG ? 1 : 0);  // passes
+    static constexpr int SMALL = LASTLOG == 0 ? -1 : (ORDER == 1 ? 0 : (ORDER == 2 && P16 >= 2 ? 1 : P16));
+    static constexpr int logr(int p) { return p == SMALL ? LASTLOG : 4; }
+    static constexpr int radix(int p) { return 1 << logr(p); }
+    static constexpr int span(int p)
+    {
+        int s = 1;
+        for (int q = 0; q < p; ++q) s *= radix(q);
+        return s;
+    }
+    // pass-major twiddle table: pass p >= 1 owns (R_p - 1) Ns_p entries,
+    // entry (k - 1) Ns_p + j' = exp(-2 pi i j' k / (Ns_p R_p)); N - R_0 in all
+    static constexpr int tw_off(int p)
+    {
+        int o = 0;
+        for (int q = 1; q < p; ++q) o += (radix(q) - 1) * span(q);
+        return o;
+    }
+    static constexpr int tw_size() { return tw_off(NP); }
+};
+
+// Radix orders a line of 2^logn points can use (ORDER < orders); one when
+// every pass has radix 16 or there is a single radix-16 pass to move.
+__host__ __device__ constexpr int radix_orders(int logn) { return logn % 4 == 0 ? 1 : (logn / 4 >= 2 ? 3 : 2); }
 
 // ---- table sources of the line FFT -------------------------------------------
-// A line FFT needs, per thread, 15 twiddles for each radix-16 pass after the
-// first, NB (RL - 1) for the trailing radix-RL pass, and (POST) the 16
+// A line FFT needs, per thread, the twiddles of every pass after the first
+// (16 / R_p butterflies x (R_p - 1) of them, at most 15) and (POST) the 16
 // factors of its output elements.  TabGlobal loads them from global memory
 // (read-only cache) where they are used; TabRegs holds them in registers for
 // the life of a kernel, loaded once.
-template <int LOGN, typename W> struct TabShape {
-    using P = Plan<LOGN>;
-    static constexpr int NP = P::P16 - 1;                                          // radix-16 passes with twiddles
-    static constexpr int NL = P::LASTLOG ? (16 / P::LASTR) * (P::LASTR - 1) : 0;  // trailing-pass twiddles
-};
-
-template <int LOGN, typename W> struct TabGlobal {
+template <int LOGN, typename W, int ORDER = 0> struct TabGlobal {
     const W *__restrict__ tw;
     const W *__restrict__ post;
+    // twiddle (k - 1) + i (R_p - 1) of pass p: input k of butterfly t + i T
     __device__ __forceinline__ void pass(int p, int t, W (&w)[15]) const
     {
-        const int Ns = 1 << (4 * p);
-        const W *q = tw + tw_pass_off<LOGN>(p) + (t & (Ns - 1));
-#pragma unroll
-        for (int r = 1; r < 16; ++r) w[r - 1] = __ldg(q + (r - 1) * Ns);
-    }
-    template <int NL> __device__ __forceinline__ void last(int t, W (&w)[NL]) const
-    {
-        using P = Plan<LOGN>;
-        constexpr int RL = P::LASTR, NB = 16 / RL, NsL = P::N / RL, T = P::T;
-        const W *q = tw + tw_pass_off<LOGN>(P::P16) + t;
+        using S = Seq<LOGN, ORDER>;
+        constexpr int T = Plan<LOGN>::T;
+        const int R = S::radix(p), Ns = S::span(p), NB = 16 / R;
+        const W *q = tw + S::tw_off(p);
 #pragma unroll
         for (int i = 0; i < NB; ++i)
 #pragma unroll
-            for (int r = 1; r < RL; ++r) w[i * (RL - 1) + r - 1] = __ldg(q + i * T + (r - 1) * NsL);
+            for (int k = 1; k < R; ++k) w[i * (R - 1) + k - 1] = __ldg(q + (k - 1) * Ns + ((t + i * T) & (Ns - 1)));
     }
     __device__ __forceinline__ void postv(int t, W (&w)[16]) const
     {
@@ -364,32 +393,25 @@ template <int LOGN, typename W> struct TabGlobal {
     }
 };
 
-template <int LOGN, typename W> struct TabRegs {
-    using S = TabShape<LOGN, W>;
-    W pw[S::NP > 0 ? S::NP : 1][15];
-    W lw[S::NL > 0 ? S::NL : 1];
+template <int LOGN, typename W, int ORDER = 0> struct TabRegs {
+    static constexpr int NP = Seq<LOGN, ORDER>::NP;
+    W pw[NP > 1 ? NP - 1 : 1][15];
     W h[16];
     __device__ __forceinline__ void load_tw(const W *__restrict__ tw, int t)
     {
-        const TabGlobal<LOGN, W> g{tw, nullptr};
+        const TabGlobal<LOGN, W, ORDER> g{tw, nullptr};
 #pragma unroll
-        for (int p = 1; p <= S::NP; ++p) g.pass(p, t, pw[p - 1]);
-        if constexpr (S::NL > 0) g.last(t, lw);
+        for (int p = 1; p < NP; ++p) g.pass(p, t, pw[p - 1]);
     }
     __device__ __forceinline__ void load_post(const W *__restrict__ post, int t)
     {
-        const TabGlobal<LOGN, W> g{nullptr, post};
+        const TabGlobal<LOGN, W, ORDER> g{nullptr, post};
         g.postv(t, h);
     }
     __device__ __forceinline__ void pass(int p, int t, W (&w)[15]) const
     {
 #pragma unroll
         for (int r = 0; r < 15; ++r) w[r] = pw[p - 1][r];
-    }
-    template <int NL> __device__ __forceinline__ void last(int t, W (&w)[NL]) const
-    {
-#pragma unroll
-        for (int i = 0; i < NL; ++i) w[i] = lw[i];
     }
     __device__ __forceinline__ void postv(int t, W (&w)[16]) const
     {
@@ -435,50 +457,91 @@ __device__ __forceinline__ bool sm_in(const V *base, const V *p, int *chk)
 #endif
 }
 
-// One Stockham FFT of a line.  On entry v[s] = x[t + T s]; on exit
-// v[s] = X[t + T s], X[k] = sum_j x[j] exp(DIR 2 pi i jk / N) (unnormalised).
-// `lb` holds this line's padded shared buffer(s) (element stride CS); sync()
-// is a barrier over every thread that shares them.  Shared addresses are a
-// per-thread base plus compile-time offsets: spans and T are multiples of 16
-// wherever the pad arithmetic allows it.  A pass's twiddles are fetched
-// before its exchange, so their latency overlaps the barrier.
-// POST: multiply the result by factor k of `tab` (element k of the output
-// line); the factors are fetched ahead of the last exchange when there is a
-// trailing pass.  read_done() runs once every read of the last exchange is
-// issued (by this thread): a caller can release the buffer there.
+// One Stockham FFT of a line, passes in the radix order ORDER (Seq).  On
+// entry v[s] = x[t + T s]; on exit v[s] = X[t + T s],
+// X[k] = sum_j x[j] exp(DIR 2 pi i jk / N) (unnormalised).  `lb` holds this
+// line's padded shared buffer(s) (element stride CS); sync() is a barrier
+// over every thread that shares them.  Between passes the outputs go to
+// shared memory at their Stockham positions and every thread reads back the
+// 16 elements t + T s: the inputs of its butterflies of the next pass.
+// Shared addresses are a per-thread base plus compile-time offsets wherever
+// the spans are multiples of 16.  A pass's twiddles are fetched before its
+// exchange, so their latency overlaps the barrier.  POST: multiply the result
+// by factor k of `tab` (element k of the output line), fetched ahead of the
+// last exchange.  read_done() runs once this thread has issued every read of
+// the last exchange: a caller can release the buffer there.
 struct NoHook {
     __device__ __forceinline__ void operator()() const {}
 };
-template <int LOGN, int DIR, int CS, bool PP, bool POST, typename V, typename Tab, typename SyncF,
+
+// The butterflies of pass p in registers: butterfly i of the thread takes
+// slots i + k NB (k < R), optionally twiddled, and returns its outputs there.
+template <int DIR, int R, typename V, typename W>
+__device__ __forceinline__ void pass_butterflies(V (&v)[16], const W (&w)[15], bool twiddled)
+{
+    constexpr int NB = 16 / R;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        V u[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) u[k] = v[i + k * NB];
+        if (twiddled) {
+#pragma unroll
+            for (int k = 1; k < R; ++k) u[k] = twm<DIR>(u[k], w[i * (R - 1) + k - 1]);
+        }
+        dft<R, DIR>(u);
+#pragma unroll
+        for (int k = 0; k < R; ++k) v[i + k * NB] = u[k];
+    }
+}
+
+template <int LOGN, int DIR, int CS, bool PP, bool POST, int ORDER = 0, typename V, typename Tab, typename SyncF,
           typename Hook = NoHook>
 __device__ __forceinline__ void fft_line_t(V (&v)[16], const int t, LineBufs<V, PP> &lb, const Tab &tab, SyncF sync,
                                            Hook read_done = Hook{})
 {
-    using P = Plan<LOGN>;
+    using S = Seq<LOGN, ORDER>;
     using W = typename table_of<V>::type;
-    constexpr int N = P::N, T = P::T;
+    constexpr int T = Plan<LOGN>::T;
     constexpr bool T16 = (T % 16) == 0;
-    dft<16, DIR>(v);
+    W none[15];
+    pass_butterflies<DIR, S::radix(0)>(v, none, false);
 #pragma unroll
-    for (int p = 1; p < P::P16; ++p) {
-        const int NsPrev = 1 << (4 * (p - 1));
+    for (int p = 1; p < S::NP; ++p) {
+        const int R = S::radix(p);
+        const int Rp = S::radix(p - 1), Nsp = S::span(p - 1), NBp = 16 / Rp;
         V *line = lb.take();
         V *rd_base = line + padi(t) * CS;
-        W wpre[15];
-        tab.pass(p, t, wpre);
+        W w[15];
+        tab.pass(p, t, w);
+        W pl[16];
+        if constexpr (POST) {
+            if (p == S::NP - 1) tab.postv(t, pl);
+        }
         if (!PP) sync();
-        if (NsPrev == 1) {
-            V *w = line + 17 * t * CS;
+        // outputs of pass p - 1: butterfly t + i T, output r at (j / Ns) Ns R + (j mod Ns) + r Ns
+        if (Nsp == 1 && Rp == 16) {
+            V *wr = line + 17 * t * CS;
 #pragma unroll
             for (int r = 0; r < 16; ++r)
-                if (sm_in<LOGN, CS>(line, &w[r * CS], lb.chk)) w[r * CS] = v[r];
+                if (sm_in<LOGN, CS>(line, &wr[r * CS], lb.chk)) wr[r * CS] = v[r];
+        } else if (Nsp % 16 == 0 && Rp == 16) {
+            const int idxD = (t / Nsp) * Nsp * 16 + (t % Nsp);
+            V *wr = line + padi(idxD) * CS;
+#pragma unroll
+            for (int r = 0; r < 16; ++r)
+                if (sm_in<LOGN, CS>(line, &wr[r * (17 * Nsp / 16) * CS], lb.chk)) wr[r * (17 * Nsp / 16) * CS] = v[r];
         } else {
-            const int idxD = (t / NsPrev) * NsPrev * 16 + (t % NsPrev);
-            V *w = line + padi(idxD) * CS;
 #pragma unroll
-            for (int r = 0; r < 16; ++r)
-                if (sm_in<LOGN, CS>(line, &w[r * (17 * NsPrev / 16) * CS], lb.chk))
-                    w[r * (17 * NsPrev / 16) * CS] = v[r];
+            for (int i = 0; i < NBp; ++i) {
+                const int j = t + i * T;
+                const int base = (j / Nsp) * Nsp * Rp + (j % Nsp);
+#pragma unroll
+                for (int r = 0; r < Rp; ++r) {
+                    V *q = &sm_at<CS>(line, base + r * Nsp);
+                    if (sm_in<LOGN, CS>(line, q, lb.chk)) *q = v[i + r * NBp];
+                }
+            }
         }
         sync();
         if constexpr (T16) {
@@ -491,68 +554,23 @@ __device__ __forceinline__ void fft_line_t(V (&v)[16], const int t, LineBufs<V, 
             for (int r = 0; r < 16; ++r)
                 if (sm_in<LOGN, CS>(line, &sm_at<CS>(line, t + r * T), lb.chk)) v[r] = sm_at<CS>(line, t + r * T);
         }
-        if (P::LASTLOG == 0 && p == P::P16 - 1) read_done();
+        if (p == S::NP - 1) read_done();
+        if (R == 16) pass_butterflies<DIR, 16>(v, w, true);
+        else if (R == 8) pass_butterflies<DIR, 8>(v, w, true);
+        else if (R == 4) pass_butterflies<DIR, 4>(v, w, true);
+        else pass_butterflies<DIR, 2>(v, w, true);
+        if constexpr (POST) {
+            if (p == S::NP - 1) {
 #pragma unroll
-        for (int r = 1; r < 16; ++r) v[r] = twm<DIR>(v[r], wpre[r - 1]);
-        dft<16, DIR>(v);
-    }
-    if constexpr (P::LASTLOG > 0) {
-        constexpr int RL = P::LASTR, NB = 16 / RL, NsL = N / RL;
-        constexpr int NsPrev = NsL / 16;
-        V *line = lb.take();
-        V *rd_base = line + padi(t) * CS;
-        W pl[POST ? 16 : 1];
-        if constexpr (POST) tab.postv(t, pl);
-        W wl[NB * (RL - 1)];
-        tab.last(t, wl);
-        if (!PP) sync();
-        if constexpr (NsPrev == 1) {
-            V *w = line + 17 * t * CS;
-#pragma unroll
-            for (int r = 0; r < 16; ++r)
-                if (sm_in<LOGN, CS>(line, &w[r * CS], lb.chk)) w[r * CS] = v[r];
-        } else {
-            const int idxD = (t / NsPrev) * NsPrev * 16 + (t % NsPrev);
-            V *w = line + padi(idxD) * CS;
-#pragma unroll
-            for (int r = 0; r < 16; ++r)
-                if (sm_in<LOGN, CS>(line, &w[r * (17 * NsPrev / 16) * CS], lb.chk))
-                    w[r * (17 * NsPrev / 16) * CS] = v[r];
-        }
-        sync();
-        // every read of the exchange first (the values' old copies in v are
-        // dead once written), then the passes
-        V ua[16];
-#pragma unroll
-        for (int i = 0; i < NB; ++i) {
-            const int j = t + i * T;
-            V *rb = T16 ? rd_base + i * (17 * T / 16) * CS : line + padi(j) * CS;
-#pragma unroll
-            for (int r = 0; r < RL; ++r)
-                ua[i * RL + r] = sm_in<LOGN, CS>(line, &rb[r * (17 * NsL / 16) * CS], lb.chk)
-                                     ? rb[r * (17 * NsL / 16) * CS]
-                                     : v[i];
-        }
-        read_done();
-#pragma unroll
-        for (int i = 0; i < NB; ++i) {
-            V u[RL];
-#pragma unroll
-            for (int r = 0; r < RL; ++r) u[r] = ua[i * RL + r];
-#pragma unroll
-            for (int r = 1; r < RL; ++r) u[r] = twm<DIR>(u[r], wl[i * (RL - 1) + r - 1]);
-            dft<RL, DIR>(u);
-#pragma unroll
-            for (int r = 0; r < RL; ++r) {
-                if constexpr (POST) v[i + r * NB] = cmul_rn(u[r], pl[i + r * NB]);
-                else v[i + r * NB] = u[r];
+                for (int s2 = 0; s2 < 16; ++s2) v[s2] = cmul_rn(v[s2], pl[s2]);
             }
         }
-    } else if constexpr (POST) {
+    }
+    if constexpr (POST && S::NP == 1) {
         W pl[16];
         tab.postv(t, pl);
 #pragma unroll
-        for (int s = 0; s < 16; ++s) v[s] = cmul_rn(v[s], pl[s]);
+        for (int s2 = 0; s2 < 16; ++s2) v[s2] = cmul_rn(v[s2], pl[s2]);
     }
 }
 

@@ -90,16 +90,29 @@ cudaError_t launch_col_diffract_plain32(int logn, float2 *X, const float2 *tw, c
 
 // ---- set-up and readout -------------------------------------------------------
 
-int twiddle_entries(int logn) { return twiddle_count(logn); }
+// The most entries a table of any radix order of side 2^logn needs.
+int twiddle_entries(int logn)
+{
+    int m = 0;
+    for (int o = 0; o < radix_orders(logn); ++o) m = twiddle_count(logn, o) > m ? twiddle_count(logn, o) : m;
+    return m;
+}
 
-cudaError_t launch_tables32(int n, double alpha, float2 *tw, float2 *h, cudaStream_t s)
+cudaError_t launch_twiddles32(int n, int order, float2 *tw, cudaStream_t s)
 {
     int logn = 0;
     while ((1 << logn) < n) ++logn;
-    const int total = twiddle_count(logn);
-    k_prop_table<float2><<<(n + 255) / 256, 256, 0, s>>>(n, alpha, h);
-    if (total > 0) k_twiddles<float2><<<(total + 255) / 256, 256, 0, s>>>(logn, total, tw);
+    if (order < 0 || order >= radix_orders(logn)) return cudaErrorInvalidValue;
+    const int total = twiddle_count(logn, order);
+    if (total > 0) k_twiddles<float2><<<(total + 255) / 256, 256, 0, s>>>(logn, order, total, tw);
     return cudaGetLastError();
+}
+
+cudaError_t launch_tables32(int n, double alpha, float2 *tw, float2 *h, cudaStream_t s)
+{
+    k_prop_table<float2><<<(n + 255) / 256, 256, 0, s>>>(n, alpha, h);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? launch_twiddles32(n, 0, tw, s) : e;
 }
 
 cudaError_t launch_prop32(int n, double alpha, float2 *h, cudaStream_t s)

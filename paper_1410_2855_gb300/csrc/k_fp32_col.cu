@@ -30,25 +30,45 @@ cudaError_t make_col_tensor_map(void *map, float2 *E, int n, int colC)
 
 // Persistent copy-engine-fed sweep where the tile fits it; otherwise (wide
 // tiles at large n) one block per tile, loading straight from global memory.
+// order: radix order of the transforms (the one-stage form only; tw must be
+// that order's table).
+template <int LOGN, int C, int ORDER>
+static cudaError_t col_launch32(float2 *E, const float2 *tw, const float2 *h, const void *tmap, int *err,
+                                cudaStream_t s)
+{
+    using F = ColForm<LOGN, C>;
+    auto k = [] {
+        if constexpr (ORDER == 0) return F::kernel();
+        else return k_col_pair1<LOGN, C, ORDER>;
+    }();
+    constexpr int threads = F::threads;
+    static std::atomic<unsigned long long> mask{0};
+    static std::atomic<int> per_sm{0};
+    cudaError_t e = ensure_smem(k, F::smem, mask);
+    if (e != cudaSuccess) return e;
+    const int ntiles = (1 << LOGN) / C;
+    const int grid = persistent_grid(k, threads, F::smem, ntiles, per_sm);
+    k<<<grid, threads, F::smem, s>>>(E, tw, h, *static_cast<const CUtensorMap *>(tmap), ntiles, err);
+    return cudaGetLastError();
+}
+
 template <int LOGN, int C>
 static cudaError_t col_diff32_c(float2 *E, const float2 *tw, const float2 *h, const void *tmap, int *err,
-                                cudaStream_t s)
+                                cudaStream_t s, int order)
 {
     if constexpr (!col_fits32<LOGN, C>()) {
         return cudaErrorInvalidValue;
     } else if constexpr (col_tma_fits<LOGN, C>()) {
-        using F = ColForm<LOGN, C>;
-        auto k = F::kernel();
-        constexpr int threads = F::threads;
-        static std::atomic<unsigned long long> mask{0};
-        static std::atomic<int> per_sm{0};
-        cudaError_t e = ensure_smem(k, F::smem, mask);
-        if (e != cudaSuccess) return e;
-        const int ntiles = (1 << LOGN) / C;
-        const int grid = persistent_grid(k, threads, F::smem, ntiles, per_sm);
-        k<<<grid, threads, F::smem, s>>>(E, tw, h, *static_cast<const CUtensorMap *>(tmap), ntiles, err);
-        return cudaGetLastError();
+        if (order == 0) return col_launch32<LOGN, C, 0>(E, tw, h, tmap, err, s);
+        if constexpr (ColForm<LOGN, C>::form == 2 && radix_orders(LOGN) > 1) {
+            if (order == 1) return col_launch32<LOGN, C, 1>(E, tw, h, tmap, err, s);
+            if constexpr (radix_orders(LOGN) > 2) {
+                if (order == 2) return col_launch32<LOGN, C, 2>(E, tw, h, tmap, err, s);
+            }
+        }
+        return cudaErrorInvalidValue;
     } else {
+        if (order != 0) return cudaErrorInvalidValue;
         cudaError_t e = col_attr<float, LOGN, C, MODE_DIFF>();
         if (e != cudaSuccess) return e;
         k_col<float, LOGN, C, MODE_DIFF>
@@ -59,22 +79,37 @@ static cudaError_t col_diff32_c(float2 *E, const float2 *tw, const float2 *h, co
 
 template <int LOGN>
 static cudaError_t col_diff32(int colC, float2 *E, const float2 *tw, const float2 *h, const void *tmap, int *err,
-                              cudaStream_t s)
+                              cudaStream_t s, int order)
 {
     switch (colC) {
-    case 2: return col_diff32_c<LOGN, 2>(E, tw, h, tmap, err, s);
-    case 4: return col_diff32_c<LOGN, 4>(E, tw, h, tmap, err, s);
-    case 8: return col_diff32_c<LOGN, 8>(E, tw, h, tmap, err, s);
-    case 16: return col_diff32_c<LOGN, 16>(E, tw, h, tmap, err, s);
+    case 2: return col_diff32_c<LOGN, 2>(E, tw, h, tmap, err, s, order);
+    case 4: return col_diff32_c<LOGN, 4>(E, tw, h, tmap, err, s, order);
+    case 8: return col_diff32_c<LOGN, 8>(E, tw, h, tmap, err, s, order);
+    case 16: return col_diff32_c<LOGN, 16>(E, tw, h, tmap, err, s, order);
     default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_col_diffract32(int logn, int colC, float2 *E, const float2 *tw, const float2 *h, const void *tmap,
-                                  int *err, cudaStream_t s)
+                                  int *err, cudaStream_t s, int order)
 {
-    RTK_LOGN_CASES(col_diff32, colC, E, tw, h, tmap, err, s)
+    RTK_LOGN_CASES(col_diff32, colC, E, tw, h, tmap, err, s, order)
 }
+
+// Radix orders the column sweep of side 2^logn offers at tile width colC.
+template <int LOGN> static int col_orders_impl(int colC)
+{
+    auto orders = [](bool tma) { return RTK_COL_FORM == 2 && tma ? radix_orders(LOGN) : 1; };
+    switch (colC) {
+    case 2: return col_fits32<LOGN, 2>() ? orders(col_tma_fits<LOGN, 2>()) : 0;
+    case 4: return col_fits32<LOGN, 4>() ? orders(col_tma_fits<LOGN, 4>()) : 0;
+    case 8: return col_fits32<LOGN, 8>() ? orders(col_tma_fits<LOGN, 8>()) : 0;
+    case 16: return col_fits32<LOGN, 16>() ? orders(col_tma_fits<LOGN, 16>()) : 0;
+    default: return 0;
+    }
+}
+
+int col_orders32(int logn, int colC) { RTK_LOGN_CASES(col_orders_impl, colC) }
 
 template <int LOGN, int C> static cudaError_t col_prep32_c()
 {
@@ -140,5 +175,17 @@ int set_tuned_col_tile32(int logn, int colC)
 }
 
 int tuned_col_tile32(int logn) { return (logn >= 0 && logn < 13) ? g_tuned_col[logn].load() : 0; }
+
+// Radix orders chosen by the autotuner (0: the built-in sequence), per log2 n.
+static std::atomic<int> g_tuned_order[13];
+
+int set_tuned_col_order32(int logn, int order)
+{
+    if (logn < 5 || logn > 12 || order < 0 || order >= radix_orders(logn)) return 0;
+    g_tuned_order[logn].store(order);
+    return 1;
+}
+
+int tuned_col_order32(int logn) { return (logn >= 0 && logn < 13) ? g_tuned_order[logn].load() : 0; }
 
 }  // namespace rtk

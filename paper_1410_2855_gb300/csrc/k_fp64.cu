@@ -171,7 +171,7 @@ cudaError_t launch_tables64(int n, double alpha, double2 *tw, double2 *h, cudaSt
     while ((1 << logn) < n) ++logn;
     const int total = twiddle_count(logn);
     k_prop_table<double2><<<(n + 255) / 256, 256, 0, s>>>(n, alpha, h);
-    if (total > 0) k_twiddles<double2><<<(total + 255) / 256, 256, 0, s>>>(logn, total, tw);
+    if (total > 0) k_twiddles<double2><<<(total + 255) / 256, 256, 0, s>>>(logn, 0, total, tw);
     return cudaGetLastError();
 }
 

@@ -28,12 +28,6 @@ template <int LOGN, int C> constexpr bool col_fits32()
     return C <= (1 << LOGN) && C * Plan<LOGN>::T <= 1024 && col_smem_bytes<float, LOGN, C>() <= 227 * 1024;
 }
 
-// ... and its copy-engine-fed persistent form fits too.
-template <int LOGN, int C> constexpr bool col_tma_fits()
-{
-    return col_fits32<LOGN, C>() && C >= 2 && ColPlan<LOGN, C>::total <= 227 * 1024;
-}
-
 // Form of the persistent column sweeps: 0 one column per thread
 // (k_col_tma), 1 column pairs with two stages and register tables
 // (k_col_pair), 2 column pairs with one stage, two or more blocks per SM
@@ -58,6 +52,12 @@ template <int LOGN, int C> struct ColForm {
         else return k_col_tma_batch<LOGN, C>;
     }
 };
+
+// ... and its copy-engine-fed persistent form (the one built) fits too.
+template <int LOGN, int C> constexpr bool col_tma_fits()
+{
+    return col_fits32<LOGN, C>() && C >= 2 && ColForm<LOGN, C>::smem <= 227 * 1024;
+}
 
 // Rows per block of the persistent row sweeps: one row from n = 1024 up,
 // else enough rows for 64 threads.

@@ -94,6 +94,8 @@ struct rt_handle {
     int slices = 1;
     long long bounces = 0;
     int colC = 4;
+    int col_order = 0;            // radix order of the FP32 column transforms (0: built-in)
+    void *tw_col = nullptr;       // that order's twiddles (only when col_order != 0; else tw serves)
     int pe = 0;                   // pump evaluation of the FP32 row sweep (PumpEval)
     alignas(64) unsigned char tmap[128] = {};  // tensor map of E for the column sweep's tile loads
     std::map<long long, cudaGraphExec_t> graphs;
@@ -148,6 +150,11 @@ GainParams<R> gain_params(rt_handle *h, bool last = true)
 
 // One bounce: per slice (one unless the gain medium is sliced) the
 // diffraction over z/m and the slice's local map on its own inversion.
+const float2 *col_twiddles(const rt_handle *h)
+{
+    return static_cast<const float2 *>(h->col_order ? h->tw_col : h->tw);
+}
+
 cudaError_t enqueue_bounce(rt_handle *h, cudaStream_t s)
 {
     const size_t P = h->points();
@@ -158,7 +165,8 @@ cudaError_t enqueue_bounce(rt_handle *h, cudaStream_t s)
         if (h->precision == RT_FP32) {
             float2 *E = static_cast<float2 *>(h->E);
             const float2 *tw = static_cast<const float2 *>(h->tw), *hh = static_cast<const float2 *>(h->h);
-            if ((e = launch_col_diffract32(h->logn, h->colC, E, tw, hh, h->tmap, &h->ctl->err, s)) != cudaSuccess)
+            if ((e = launch_col_diffract32(h->logn, h->colC, E, col_twiddles(h), hh, h->tmap, &h->ctl->err, s,
+                                           h->col_order)) != cudaSuccess)
                 return e;
             e = launch_row_diffract_gain32(h->logn, h->pe, E, static_cast<float *>(h->N) + k * P, tw, hh,
                                            gain_params<float>(h, last), st, s);
@@ -225,7 +233,7 @@ void release(rt_handle *h)
 {
     for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
-    void *bufs[] = {h->E, h->N, h->tw, h->h, h->pump_tab, h->lens, h->phase, h->ones, h->profile, h->X, h->S, h->hz,
+    void *bufs[] = {h->E, h->N, h->tw, h->tw_col, h->h, h->pump_tab, h->lens, h->phase, h->ones, h->profile, h->X, h->S, h->hz,
                     h->part, h->peak_val, h->peak_idx, h->hist, h->ctl, h->slice_ctl};
     for (void *p : bufs)
         if (p) cudaFree(p);
@@ -343,6 +351,11 @@ rt_status rt_create(int n, double fresnel, const rt_pump *pump, double g0, doubl
     h->slices = o.slices > 1 ? o.slices : 1;
     h->stream = static_cast<cudaStream_t>(o.cuda_stream);
     h->colC = o.col_tile ? o.col_tile : default_col_tile32(h->logn);
+    // the tuned radix order goes with the tuned tile width
+    if (h->precision == RT_FP32 && o.col_tile == 0) {
+        const int ord = tuned_col_order32(h->logn);
+        h->col_order = ord < col_orders32(h->logn, h->colC) ? ord : 0;
+    }
     // N0 on the fly for the order-10 super-Gaussian and the uniform pump, else from a table
     h->pe = p.kind == RT_PUMP_UNIFORM ? 1 : ((p.kind == RT_PUMP_SUPERGAUSS && p.order == 10.0) ? 0 : 2);
 #if RTK_ROW_PUMP_TABLE
@@ -408,6 +421,10 @@ rt_status rt_create(int n, double fresnel, const rt_pump *pump, double g0, doubl
     if (h->precision == RT_FP32) {
         RT_CREATE_TRY(launch_tables32(n, h->alpha / h->slices, static_cast<float2 *>(h->tw), static_cast<float2 *>(h->h),
                                       h->stream));
+        if (h->col_order) {
+            RT_CREATE_TRY(dev_alloc(&h->tw_col, (size_t)(twiddle_entries(h->logn) + 1) * sizeof(float2)));
+            RT_CREATE_TRY(launch_twiddles32(n, h->col_order, static_cast<float2 *>(h->tw_col), h->stream));
+        }
         RT_CREATE_TRY(make_col_tensor_map(h->tmap, static_cast<float2 *>(h->E), n, h->colC));
         RT_CREATE_TRY(launch_noise32(n, o.seed, o.noise_amp, static_cast<float2 *>(h->E), h->stream));
         RT_CREATE_TRY(launch_pump32(n, p.kind, g0s, p.order, p.radius, h->profile, static_cast<float *>(h->N), h->stream));
@@ -467,7 +484,8 @@ rt_status rt_sweep(rt_handle *h, int which)
     float2 *E = static_cast<float2 *>(h->E);
     const float2 *tw = static_cast<const float2 *>(h->tw), *hh = static_cast<const float2 *>(h->h);
     if (which == RT_SWEEP_COLUMNS) {
-        RT_TRY(launch_col_diffract32(h->logn, h->colC, E, tw, hh, h->tmap, &h->ctl->err, h->stream));
+        RT_TRY(launch_col_diffract32(h->logn, h->colC, E, col_twiddles(h), hh, h->tmap, &h->ctl->err, h->stream,
+                                     h->col_order));
     } else {
         RT_TRY(launch_row_diffract_gain32(h->logn, h->pe, E, static_cast<float *>(h->N), tw, hh, gain_params<float>(h),
                                           stat_params(h), h->stream));

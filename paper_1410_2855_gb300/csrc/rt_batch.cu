@@ -26,6 +26,7 @@ struct Slot {
 
 struct SizeClass {
     int logn = 0, colC = 4;
+    bool mixed = false;  // runs in the launches shared across sizes
     std::vector<int> slots;
     BatchRes *d_res = nullptr;
     float2 *tw = nullptr;
@@ -66,7 +67,7 @@ cudaError_t start_slot(rt_batch *b, int i)
 std::vector<ClassLaunch> launches(rt_batch *b)
 {
     std::vector<ClassLaunch> v;
-    for (SizeClass &c : b->classes) v.push_back({c.logn, c.colC, c.d_res, (int)c.slots.size(), c.tw});
+    for (SizeClass &c : b->classes) v.push_back({c.logn, c.colC, c.d_res, (int)c.slots.size(), c.tw, c.mixed});
     return v;
 }
 
@@ -93,9 +94,8 @@ cudaError_t batch_graph(rt_batch *b, long long k, cudaGraphExec_t *out)
         return cudaSuccess;
     }
     cudaError_t e;
-    for (SizeClass &c : b->classes)
-        if ((e = prepare_batch32(c.logn, c.colC)) != cudaSuccess) return e;
     const std::vector<ClassLaunch> cl = launches(b);
+    if ((e = prepare_classes(cl)) != cudaSuccess) return e;
     if ((e = branches_prepare(b->branches, cl, kBatchSplit)) != cudaSuccess) return e;
     if ((e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
     const cudaError_t le = capture_class_bounces(cl, b->err, k, b->capture, b->branches, kBatchSplit);
@@ -195,8 +195,8 @@ rt_status rt_batch_create(const rt_job *jobs, int count, const rt_opts *opts, rt
         if (it == class_of.end()) {
             SizeClass c;
             c.logn = logn;
-            c.colC = o.col_tile ? o.col_tile : default_col_tile32(logn);
-            if (!col_tile_ok32(logn, c.colC)) return fail(RT_EINVAL);
+            c.colC = class_col_tile(logn, o.col_tile, &c.mixed);
+            if (!c.mixed && !col_tile_ok32(logn, c.colC)) return fail(RT_EINVAL);
             it = class_of.emplace(logn, (int)b->classes.size()).first;
             b->classes.push_back(c);
         }
@@ -248,12 +248,7 @@ rt_status rt_batch_sweep(rt_batch *b, int which)
 {
     if (!b || (which != RT_SWEEP_COLUMNS && which != RT_SWEEP_ROWS)) return RT_EINVAL;
     DeviceGuard g(b->device);
-    for (SizeClass &c : b->classes) {
-        if (which == RT_SWEEP_COLUMNS)
-            BT_TRY(launch_col_batch32(c.logn, c.colC, c.d_res, (int)c.slots.size(), c.tw, b->err, b->stream));
-        else
-            BT_TRY(launch_row_batch32(c.logn, c.d_res, (int)c.slots.size(), c.tw, b->err, b->stream));
-    }
+    BT_TRY(enqueue_sweep(launches(b), which, b->err, b->stream));
     return RT_OK;
 }
 

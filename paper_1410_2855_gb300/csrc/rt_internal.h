@@ -89,12 +89,33 @@ cudaError_t launch_row_batch32(int logn, const BatchRes *res, int nres, const fl
 cudaError_t prepare_batch32(int logn, int colC);
 int row_groups32(int logn);  // row groups per resonator of a batched row sweep
 
+// One launch per sweep over size classes of uneven sides 128..2048
+// (mix_supported): every item holds the same number of points, the column
+// tile of side n is mix_col_tile(n) columns wide (the slots' tensor maps must
+// use that width).
+struct MixLaunch {
+    int logn;
+    const BatchRes *res;
+    int nres;
+    const float2 *tw;
+};
+bool mix_supported(int logn);
+int mix_col_tile(int logn);
+cudaError_t prepare_mixed32();
+cudaError_t launch_col_mixed32(const MixLaunch *cls, int ncls, int *err, cudaStream_t s);
+cudaError_t launch_row_mixed32(const MixLaunch *cls, int ncls, int *err, cudaStream_t s);
+
 // ---- FP32 fused path: two sweeps per bounce --------------------------------
 // Column sweep: per column, forward FFT, x h(my), inverse FFT (in place).
 // tmap: the field's column-tile tensor map (make_col_tensor_map); err: the
 // handle's sticky error word (set to RT_ETIMEOUT if a copy wait runs out).
 cudaError_t launch_col_diffract32(int logn, int colC, float2 *E, const float2 *tw, const float2 *h, const void *tmap,
-                                  int *err, cudaStream_t s);
+                                  int *err, cudaStream_t s, int order = 0);
+// Radix orders (0 .. col_orders32 - 1) of the column sweep at tile width colC
+// (0 if the width does not fit); order 0 is the built-in sequence.
+int col_orders32(int logn, int colC);
+// Pass-major twiddles of radix order `order` (twiddle_entries(log2 n) entries suffice).
+cudaError_t launch_twiddles32(int n, int order, float2 *tw, cudaStream_t s);
 // Encode the 128-byte tensor map of an n x n complex64 field for column
 // tiles of colC columns (copy-engine loads of the column sweep).
 cudaError_t make_col_tensor_map(void *map, float2 *E, int n, int colC);
@@ -118,6 +139,8 @@ int default_col_tile32(int logn);      // column tile width used when none is re
 int builtin_col_tile32(int logn);      // the built-in choice
 int set_tuned_col_tile32(int logn, int colC);  // record a tuned width (0 clears); 1 on success
 int tuned_col_tile32(int logn);        // tuned width or 0
+int set_tuned_col_order32(int logn, int order);  // record a tuned radix order (0: built-in); 1 on success
+int tuned_col_order32(int logn);       // tuned radix order or 0
 
 // Plain diffraction of a copy of the field (intracavity readout): rows out
 // of place (in -> out), then columns in place, each forward FFT, x h,

@@ -54,6 +54,7 @@ struct SSlot {
 
 struct SClass {
     int logn = 0, colC = 4;
+    bool mixed = false;         // runs in the launches shared across sizes
     BatchRes *d_res = nullptr;  // capacity entries
     SlotCtl *ctl = nullptr;     // capacity entries
     float2 *tw = nullptr;
@@ -101,12 +102,12 @@ size_t request_bytes(const rt_job &j) { return slot_bytes(j.n, kHistCap, false, 
 cudaError_t class_init(rt_server *s, SClass &c, int logn)
 {
     c.logn = logn;
-    c.colC = default_col_tile32(logn);
+    c.colC = class_col_tile(logn, 0, &c.mixed);
     const int cap = s->opts.max_per_size;
     cudaError_t e = dev_alloc(&c.d_res, sizeof(BatchRes) * cap);
     if (e == cudaSuccess) e = dev_alloc(&c.ctl, sizeof(SlotCtl) * cap);
     if (e == cudaSuccess) e = dev_alloc(&c.tw, sizeof(float2) * (twiddle_entries(logn) + 1));
-    if (e == cudaSuccess) e = prepare_batch32(logn, c.colC);
+    if (e == cudaSuccess) e = c.mixed ? prepare_mixed32() : prepare_batch32(logn, c.colC);
     if (e != cudaSuccess) {  // the class is dropped: release what it holds
         if (c.d_res) cudaFree(c.d_res);
         if (c.ctl) cudaFree(c.ctl);
@@ -196,7 +197,7 @@ cudaError_t round_graph(rt_server *s, cudaGraphExec_t *out)
     for (auto &kv : s->classes) {
         SClass &c = kv.second;
         if (c.slots.empty()) continue;
-        cl.push_back({c.logn, c.colC, c.d_res, (int)c.slots.size(), c.tw});
+        cl.push_back({c.logn, c.colC, c.d_res, (int)c.slots.size(), c.tw, c.mixed});
         key += "/" + std::to_string(c.logn) + ":" + std::to_string(c.slots.size());
     }
     auto it = s->graphs.find(key);

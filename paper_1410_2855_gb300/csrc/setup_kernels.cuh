@@ -182,21 +182,36 @@ __global__ void k_pattern(int n, int kind, int q, int alt, double w, double env,
 // fft_core.cuh): for each pass after the first, with span Ns and radix R,
 // entry (r-1)*Ns + j holds exp(-2 pi i r j / (Ns R)).  FP64 sincospi on the
 // exact rational argument 2 r j / (Ns R).
+// Radix sequence of a line of 2^logn points (the runtime twin of Seq in
+// fft_core.cuh): passes of radix 16 and, when 4 does not divide logn, one of
+// radix 2^(logn mod 4), placed last (order 0), first (1) or second (2).
+__host__ __device__ inline int seq_passes(int logn) { return logn / 4 + (logn % 4 ? 1 : 0); }
+__host__ __device__ inline int seq_small(int logn, int order)
+{
+    const int p16 = logn / 4;
+    return logn % 4 == 0 ? -1 : (order == 1 ? 0 : (order == 2 && p16 >= 2 ? 1 : p16));
+}
+__host__ __device__ inline int seq_radix(int logn, int order, int p)
+{
+    return p == seq_small(logn, order) ? (1 << (logn % 4)) : 16;
+}
+
+// Pass-major twiddles of the sequence: pass p >= 1 (radix R, span Ns, the
+// product of the radices before it) owns (R - 1) Ns entries, entry
+// (k - 1) Ns + j = exp(-2 pi i j k / (Ns R)), computed in FP64 from the
+// exact rational argument 2 j k / (Ns R).
 template <typename V>
-__global__ void k_twiddles(int logn, int total, V *tw)
+__global__ void k_twiddles(int logn, int order, int total, V *tw)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= total) return;
-    const int p16 = logn / 4, lastlog = logn % 4;
-    int base = 0, Ns = 16;
-    int R = 16;
-    for (int p = 1;; ++p) {
-        const bool trailing = p >= p16;
-        R = trailing ? (1 << lastlog) : 16;
+    int base = 0, Ns = seq_radix(logn, order, 0), R = 16;
+    for (int p = 1; p < seq_passes(logn); ++p) {
+        R = seq_radix(logn, order, p);
         const int size = (R - 1) * Ns;
         if (e < base + size) break;
         base += size;
-        Ns *= 16;
+        Ns *= R;
     }
     const int local = e - base;
     const int r = local / Ns + 1, j = local % Ns;
@@ -205,11 +220,14 @@ __global__ void k_twiddles(int logn, int total, V *tw)
     tw[e] = store_factor<V>(c, -s, 1.0);
 }
 
-__host__ __device__ inline int twiddle_count(int logn)
+__host__ __device__ inline int twiddle_count(int logn, int order = 0)
 {
-    int s = 0, Ns = 16;
-    for (int p = 1; p < logn / 4; ++p, Ns *= 16) s += 15 * Ns;
-    if (logn % 4) s += ((1 << (logn % 4)) - 1) * Ns;
+    int s = 0, Ns = seq_radix(logn, order, 0);
+    for (int p = 1; p < seq_passes(logn); ++p) {
+        const int R = seq_radix(logn, order, p);
+        s += (R - 1) * Ns;
+        Ns *= R;
+    }
     return s;
 }
 

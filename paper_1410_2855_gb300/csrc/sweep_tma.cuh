@@ -503,7 +503,8 @@ template <typename IssueF> struct IssueAfterReads {
     }
 };
 
-template <int LOGN, int C>
+// ORDER: radix order of the column transforms (Seq); tw is that order's table.
+template <int LOGN, int C, int ORDER = 0>
 __global__ void __launch_bounds__((C / 2) * Plan<LOGN>::T,
                                   pair1_min_blocks((C / 2) * Plan<LOGN>::T, ColStage1<LOGN, C>::total))
 k_col_pair1(float2 *E, const float2 *__restrict__ tw, const float2 *__restrict__ h,
@@ -530,10 +531,7 @@ k_col_pair1(float2 *E, const float2 *__restrict__ tw, const float2 *__restrict__
     __syncthreads();
     int tile = blockIdx.x;
     if (threadIdx.x == 0 && tile < ntiles) issue(tile);
-#ifdef RTK_SKEW_NS
-    if (blockIdx.x >= gridDim.x / 2) __nanosleep(RTK_SKEW_NS);
-#endif
-    const TabGlobal<LOGN, float2> tab{tw, h};
+    const TabGlobal<LOGN, float2, ORDER> tab{tw, h};
     for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
         const int nxt = tile + (int)gridDim.x;
         const bool late = !mbar_wait(&bar[0], (uint32_t)(it & 1));
@@ -545,9 +543,9 @@ k_col_pair1(float2 *E, const float2 *__restrict__ tw, const float2 *__restrict__
 #pragma unroll
         for (int si = 0; si < 16; ++si) v[si] = base[(t + si * T) * CP + c2];
         LineBufs<cpair, false> lb{{base + c2, base + c2}, 0, err};
-        fft_line_t<LOGN, -1, CP, false, true>(v, t, lb, tab, sync);
+        fft_line_t<LOGN, -1, CP, false, true, ORDER>(v, t, lb, tab, sync);
         const IssueAfterReads<decltype(issue)> next{issue, nxt, nxt < ntiles};
-        fft_line_t<LOGN, +1, CP, false, false>(v, t, lb, tab, sync, next);
+        fft_line_t<LOGN, +1, CP, false, false, ORDER>(v, t, lb, tab, sync, next);
         cpair *col = reinterpret_cast<cpair *>(E + (size_t)t * N + tile * C) + c2;
 #pragma unroll
         for (int si = 0; si < 16; ++si) col[(size_t)si * T * (N / 2)] = v[si];

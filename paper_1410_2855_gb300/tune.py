@@ -1,4 +1,5 @@
-"""Autotuning of the column-sweep tile width, with a JSON cache on disk.
+"""Autotuning of the column sweep (tile width and radix order), with a JSON
+cache on disk.
 
 ``autotune(sizes)`` runs rt_autotune on the current GPU for each grid side
 (the library keeps the winners for this process) and writes them to the
@@ -22,7 +23,12 @@ def _sig():
     L.rt_autotune.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
     L.rt_tune_set.argtypes = [ctypes.c_int, ctypes.c_int]
     L.rt_tune_get.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
-    for f in (L.rt_autotune, L.rt_tune_set, L.rt_tune_get):
+    L.rt_tune_set_order.argtypes = [ctypes.c_int, ctypes.c_int]
+    L.rt_tune_get_order.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    L.rt_tune_set_order.restype = L.rt_tune_get_order.restype = ctypes.c_int
+    L.rt_tune_set_batch_mixed.argtypes = [ctypes.c_int]
+    L.rt_tune_get_batch_mixed.argtypes = [ctypes.POINTER(ctypes.c_int)]
+    for f in (L.rt_autotune, L.rt_tune_set, L.rt_tune_get, L.rt_tune_set_batch_mixed, L.rt_tune_get_batch_mixed):
         f.restype = ctypes.c_int
     return L
 
@@ -48,8 +54,53 @@ def rt_tune_get(n: int):
     return c.value, bool(tuned.value)
 
 
+def rt_tune_set_order(n: int, order: int):
+    rt._check(_sig().rt_tune_set_order(n, order), "rt_tune_set_order")
+
+
+def rt_tune_get_order(n: int):
+    """(radix order in use for side n, number of orders n offers)."""
+    o, k = ctypes.c_int(), ctypes.c_int()
+    rt._check(_sig().rt_tune_get_order(n, ctypes.byref(o), ctypes.byref(k)), "rt_tune_get_order")
+    return o.value, k.value
+
+
+def rt_tune_set_batch_mixed(mixed: bool):
+    rt._check(_sig().rt_tune_set_batch_mixed(1 if mixed else 0), "rt_tune_set_batch_mixed")
+
+
+def rt_tune_get_batch_mixed() -> bool:
+    m = ctypes.c_int()
+    rt._check(_sig().rt_tune_get_batch_mixed(ctypes.byref(m)), "rt_tune_get_batch_mixed")
+    return bool(m.value)
+
+
+def autotune_batch(jobs, bounces: int = 100, **batch_opts) -> dict:
+    """Time `bounces` bounces of a batch of `jobs` in each launch form (one
+    launch per sweep across sizes, or one per size class; both give the same
+    fields) and keep the faster for batches and servers created afterwards.
+    Returns the form chosen and both rates in round trips per second."""
+    import time
+    rates = {}
+    for mixed in (False, True):
+        rt_tune_set_batch_mixed(mixed)
+        with rt.Batch(jobs, chunk=bounces, **batch_opts) as b:
+            b.step(bounces)
+            b.sync()
+            t0 = time.perf_counter()
+            b.step(bounces)
+            b.sync()
+            rates[mixed] = len(jobs) * bounces / (time.perf_counter() - t0)
+    best = max(rates, key=rates.get)
+    rt_tune_set_batch_mixed(best)
+    return {"mixed": best, "round_trips_per_s": {"mixed": rates[True], "per_class": rates[False]}}
+
+
 def autotune(sizes=(256, 512, 1024, 2048), reps: int = 50, cache: str | None = CACHE) -> dict:
-    found = {str(n): dict(zip(("col_tile", "us"), rt_autotune(n, reps))) for n in sizes}
+    found = {}
+    for n in sizes:
+        tile, us = rt_autotune(n, reps)
+        found[str(n)] = {"col_tile": tile, "col_order": rt_tune_get_order(n)[0], "us": us}
     if cache:
         data = {}
         if os.path.exists(cache):
@@ -68,4 +119,5 @@ def load(cache: str = CACHE) -> dict:
         entries = json.load(f).get(gpu_name(), {})
     for n, e in entries.items():
         rt_tune_set(int(n), int(e["col_tile"]))
+        rt_tune_set_order(int(n), int(e.get("col_order", 0)))
     return entries

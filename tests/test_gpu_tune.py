@@ -1,36 +1,99 @@
-"""Autotuning of the column-sweep tile width: rt_autotune picks a width that
-fits and records it for later handles; results do not depend on the width
-(each column's transform is the same arithmetic), and a cache round-trips."""
+"""Autotuning of the column sweep: rt_autotune picks a tile width and a radix
+order that fit and records them for later handles.  Every choice it can make
+is a correct transform: for each radix order (and tile width) the bounce map
+matches the FP64 oracle at the parity tolerances after 1 and 20 bounces, the
+tile width does not change a single bit for a given order, and the tuned
+choices round-trip through the JSON cache.  The batch launch form (one launch
+per sweep across sizes, or one per size class) does not change the fields
+either."""
 import json
 
 import numpy as np
 import pytest
 
+import oracle as orc
 from paper_1410_2855_gb300 import build, rt, tune, workloads as wl
 
 pytestmark = pytest.mark.gpu
 
 
-def test_autotune_picks_a_valid_width_and_results_do_not_depend_on_it(tmp_path):
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.complex128) - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(autouse=True)
+def _clean():
     build.build()
+    orc.build()
+    yield
+    for n in (128, 256, 512, 1024, 2048):
+        tune.rt_tune_set(n, 0)
+        tune.rt_tune_set_order(n, 0)
+    tune.rt_tune_set_batch_mixed(False)
+
+
+def test_autotune_picks_a_width_and_order_that_fit():
     best, us = tune.rt_autotune(512, reps=20)
     assert best in (2, 4, 8, 16) and us > 0
     assert tune.rt_tune_get(512) == (best, True)
-    p = wl.Resonator(n=1024, fresnel=300.0, g0=0.25, T1=1000.0, R=0.95, seed=3)
-    fields = []
-    for c in (4, 8, 16):
-        with rt.Resonator.from_params(p, col_tile=c, chunk=0) as r:
-            r.set_field(wl.smooth_field(1024, 2, 1.0, dtype=np.complex64))
-            r.step(5)
-            fields.append(r.field())
-    assert all(np.array_equal(f, fields[0]) for f in fields[1:])
+    order, orders = tune.rt_tune_get_order(512)
+    assert orders == 3 and 0 <= order < orders
+
+
+@pytest.mark.parametrize("n", [128, 512, 1024, 2048])
+def test_every_radix_order_matches_the_oracle(n):
+    p = wl.Resonator(n=n, fresnel=300.0 * n / 1024, g0=0.25, T1=1000.0, R=0.95, seed=3)
+    E0 = wl.smooth_field(n, 2, 1.0, dtype=np.complex64)
+    q = orc.make_params(n, orc.alpha_from_fresnel(p.fresnel, p.d_over_w), p.g0, p.T1, p.R)
+    o1, _, _ = orc.run(q, E0.astype(np.complex128), orc.pump(q), 1, nthreads=4, history=False)
+    o20, _, _ = orc.run(q, E0.astype(np.complex128), orc.pump(q), 20, nthreads=4, history=False)
+    _, orders = tune.rt_tune_get_order(n)
+    assert orders == (3 if n >= 512 else 2)
+    runs = {}
+    for order in range(orders):
+        tune.rt_tune_set_order(n, order)
+        for tile in (2, 4):
+            tune.rt_tune_set(n, tile)
+            with rt.Resonator.from_params(p, chunk=0) as r:
+                r.set_field(E0)
+                r.step(1)
+                e1 = r.field()
+                r.step(19)
+                runs[(order, tile)] = (e1, r.field())
+        assert np.array_equal(runs[(order, 2)][0], runs[(order, 4)][0])
+        assert np.array_equal(runs[(order, 2)][1], runs[(order, 4)][1])
+        assert rel(runs[(order, 4)][0], o1) <= 1e-5, (order, rel(runs[(order, 4)][0], o1))
+        assert rel(runs[(order, 4)][1], o20) <= 1e-3, (order, rel(runs[(order, 4)][1], o20))
+
+
+def test_tuned_choices_round_trip_through_the_cache(tmp_path):
     cache = tmp_path / "tune.json"
-    found = tune.autotune(sizes=(256,), reps=10, cache=str(cache))
+    found = tune.autotune(sizes=(256, 1024), reps=10, cache=str(cache))
     data = json.loads(cache.read_text())
-    assert data[tune.gpu_name()]["256"]["col_tile"] == found["256"]["col_tile"]
+    for n in ("256", "1024"):
+        assert data[tune.gpu_name()][n]["col_tile"] == found[n]["col_tile"]
+        assert data[tune.gpu_name()][n]["col_order"] == found[n]["col_order"]
     tune.rt_tune_set(256, 0)
+    tune.rt_tune_set_order(1024, 0)
     assert tune.rt_tune_get(256)[1] is False
-    assert tune.load(str(cache))["256"]["col_tile"] == found["256"]["col_tile"]
-    assert tune.rt_tune_get(256) == (found["256"]["col_tile"], True)
-    for n in (256, 512):
-        tune.rt_tune_set(n, 0)
+    loaded = tune.load(str(cache))
+    assert tune.rt_tune_get(256) == (loaded["256"]["col_tile"], True)
+    assert tune.rt_tune_get_order(1024)[0] == loaded["1024"]["col_order"]
+
+
+def test_batch_launch_form_does_not_change_the_fields():
+    jobs = [wl.Resonator(n=s, fresnel=150.0, g0=0.25, T1=800.0, R=0.93, seed=90 + j)
+            for j, s in enumerate((128, 256, 512, 1024, 256, 2048, 64))]
+    fields = {}
+    for mixed in (True, False):
+        tune.rt_tune_set_batch_mixed(mixed)
+        assert tune.rt_tune_get_batch_mixed() is mixed
+        with rt.Batch(jobs, chunk=5) as b:
+            b.step(12)
+            fields[mixed] = [b.field(i) for i in range(len(jobs))]
+            means = [b.stats(i).mean_intensity for i in range(len(jobs))]
+        fields[(mixed, "mean")] = means
+    for a, c in zip(fields[True], fields[False]):
+        assert np.array_equal(a, c)
+    for a, c in zip(fields[(True, "mean")], fields[(False, "mean")]):
+        assert abs(a - c) <= 1e-12 * abs(c)
