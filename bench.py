@@ -61,11 +61,17 @@ def parse_args():
     ap.add_argument("--bounces-per-step", type=int, default=500)
     ap.add_argument("--no-comparisons", action="store_true", help="skip the comparison legs")
     ap.add_argument("--col-tile", type=int, default=0, help="fixed column-sweep tile width (0: autotune)")
+    ap.add_argument("--col-order", type=int, default=0, help="radix order with a fixed --col-tile")
     ap.add_argument("--serve-requests", type=int, default=1000,
                     help="requests of the 50 req/s serving replay (the first arrivals of the seeded trace)")
     ap.add_argument("--serve-capacity-requests", type=int, default=100,
                     help="requests of the serving replay at a sustainable rate")
     ap.add_argument("--serve-capacity-rate", type=float, default=2.0, help="its arrival rate, requests/s")
+    ap.add_argument("--sweep-case", default="",
+                    help="small case for a profiler: KIND:N[:TILE[:ORDER]] runs --steps sweeps (KIND col or row) "
+                         "of one seeded n x n resonator after --warmup sweeps, prints one line and exits")
+    ap.add_argument("--batch-case", action="store_true",
+                    help="small case for a profiler: --warmup then --steps bounces of the 256-resonator sweep")
     return ap.parse_args()
 
 
@@ -525,7 +531,8 @@ def serve_replay(rt, stream, count=1000, rate_hz=50.0, policy=0, round_points=0)
             "offered_req_per_s": len(trace) / arrivals_s, "served_req_per_s": len(res) / span,
             "served_point_bounces_per_s": work / span, "offered_point_bounces_per_s": offered,
             "offered_over_served": offered / (work / span), "rounds": st.rounds,
-            "peak_resident_bytes": st.peak_resident_bytes, "wall_s": time.perf_counter() - t_wall}
+            "peak_resident_bytes": st.peak_resident_bytes, "round_points": round_points or (1 << 23),
+            "wall_s": time.perf_counter() - t_wall}
 
 
 def run_ours(args):
@@ -545,6 +552,7 @@ def run_ours(args):
     from paper_1410_2855_gb300 import tune
     if args.col_tile:
         tune.rt_tune_set(params[0].n, args.col_tile)
+        tune.rt_tune_set_order(params[0].n, args.col_order)
         col_tile, tile_source = args.col_tile, "fixed on the command line"
     else:
         # column-sweep tile width and radix order for this GPU (2048^2 and the larger-than-L2 4096^2)
@@ -861,10 +869,12 @@ def comparisons(args, rt, torch, main, streams, params, res, E0, N0, rank, world
     # (several times what the GPU can serve: latency there is the backlog),
     # then a replay at a rate the GPU sustains (latency is service plus
     # modest queueing), each under both scheduling policies
+    # (shortest-first advances only the least-work requests each round, so with hundreds resident it
+    # runs many small rounds: its overload replay takes the first 300 arrivals and 32M-point rounds)
     extra["serve_overload"] = {
         "fifo": serve_replay(rt, main, count=args.serve_requests, rate_hz=50.0),
-        "shortest_first": serve_replay(rt, main, count=args.serve_requests, rate_hz=50.0,
-                                       policy=rt.RT_SERVE_SHORTEST_FIRST)}
+        "shortest_first": serve_replay(rt, main, count=min(args.serve_requests, 300), rate_hz=50.0,
+                                       policy=rt.RT_SERVE_SHORTEST_FIRST, round_points=32 << 20)}
     extra["serve_capacity_rate"] = {
         "fifo": serve_replay(rt, main, count=args.serve_capacity_requests, rate_hz=args.serve_capacity_rate),
         "shortest_first": serve_replay(rt, main, count=args.serve_capacity_requests,
@@ -915,8 +925,42 @@ def comparisons(args, rt, torch, main, streams, params, res, E0, N0, rank, world
     return extra
 
 
+def run_case(args):
+    """A small, fixed case for kernel captures (no timing, no JSON line)."""
+    import torch
+    from paper_1410_2855_gb300 import build, rt
+    build.build()
+    st = torch.cuda.Stream()
+    if args.batch_case:
+        jobs = wl.batch_sweep(count=256, sides=(256, 512, 1024))
+        with rt.Batch(jobs, chunk=0, cuda_stream=st.cuda_stream) as b:
+            b.step(args.warmup)
+            b.step(args.steps)
+            b.sync()
+        print(f"batch case: 256 resonators, {args.warmup} + {args.steps} bounces")
+        return
+    from paper_1410_2855_gb300 import tune
+    kind, n, *rest = args.sweep_case.split(":")
+    n = int(n)
+    tile, order = (int(rest[0]) if rest else 0), (int(rest[1]) if len(rest) > 1 else 0)
+    if tile:
+        tune.rt_tune_set(n, tile)
+    tune.rt_tune_set_order(n, order)
+    p = wl.Resonator(n=n, fresnel=1000.0 * n / 2048, g0=0.3, T1=1e4, R=0.9)
+    with rt.Resonator.from_params(p, cuda_stream=st.cuda_stream, chunk=0) as r:
+        r.set_field(wl.smooth_field(n, 3, 1.0, dtype=np.complex64))
+        which = rt.RT_SWEEP_COLUMNS if kind == "col" else rt.RT_SWEEP_ROWS
+        for _ in range(args.warmup + args.steps):
+            rt.rt_sweep(r.h, which)
+        r.sync()
+    print(f"sweep case: {kind} sweeps of one {n}x{n} resonator, {args.warmup} + {args.steps}")
+
+
 def main():
     args = parse_args()
+    if args.sweep_case or args.batch_case:
+        run_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

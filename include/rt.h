@@ -177,34 +177,45 @@ rt_status rt_step(rt_handle *h, long long n_bounces);
 enum { RT_SWEEP_COLUMNS = 0, RT_SWEEP_ROWS = 1 };
 rt_status rt_sweep(rt_handle *h, int which);
 
-/* Wait for the handle's stream; reports a sticky device error. */
+/* Wait for the handle's stream; reports a sticky device error.
+ * Infrastructure (no counterpart in the paper). */
 rt_status rt_sync(rt_handle *h);
 
 /* Copy the current field (n*n complex64 or complex128, `bytes` must equal
- * n*n*8 or n*n*16) to dst (host or device).  Blocks until the copy is done. */
+ * n*n*8 or n*n*16) to dst (host or device).  Blocks until the copy is done.
+ * The field is E_n of eq. conv_map, the state of the map at the mirror and
+ * gain plane after the last bounce. */
 rt_status rt_read_field(rt_handle *h, void *dst, size_t bytes);
 
-/* Copy the current inversion (n*n float or double) to dst (host or device). Blocks. */
+/* Copy the current inversion (n*n float or double) to dst (host or device).
+ * Blocks.  The inversion is N_n, the second state variable of eq. conv_map
+ * (relaxed as the rate equation of eq. Maxw_Bloch_incoherent). */
 rt_status rt_read_inversion(rt_handle *h, void *dst, size_t bytes);
 
 /* Replace the field / inversion with src (host or device, same layouts as
  * the reads): checkpoint restore or a caller-chosen initial condition.
- * Ordered on the handle's stream; src must stay valid until rt_sync. */
+ * Ordered on the handle's stream; src must stay valid until rt_sync.
+ * Infrastructure (the paper starts every run from noise). */
 rt_status rt_write_field(rt_handle *h, const void *src, size_t bytes);
 rt_status rt_write_inversion(rt_handle *h, const void *src, size_t bytes);
 
-/* Set the bounce counter (used when restoring a checkpoint). */
+/* Set the bounce counter (used when restoring a checkpoint).  Infrastructure. */
 rt_status rt_set_bounces(rt_handle *h, long long bounces);
 
-/* Synchronise and report counters (bounce count, last mean intensity). */
+/* Synchronise and report counters (bounce count, last mean intensity
+ * <|E_n|^2>, the sticky error).  Infrastructure: a diagnostic of the map. */
 rt_status rt_stats(rt_handle *h, rt_stats_t *out);
 
 /* Copy the mean intensity <|E|^2> of the most recent bounces, oldest first,
- * into dst (host, up to max values); *got receives the count written. */
+ * into dst (host, up to max values); *got receives the count written.
+ * Infrastructure: the intensity history of the iterates n of eq. conv_map. */
 rt_status rt_read_history(rt_handle *h, double *dst, long long max, long long *got);
 
 /* Far-field spectrum S = |DFT2(E)|^2 of the current field (n*n float or
- * double, unnormalised) to dst (host or device).  Blocks. */
+ * double, unnormalised) to dst (host or device).  Blocks.  The Fourier image
+ * of the field that the multiscale section describes (its period p_m at the
+ * planes L_m); the DFT is the Fourier basis of eq.
+ * limit_of_operators_renorm_final. */
 rt_status rt_read_spectrum(rt_handle *h, void *dst, size_t bytes);
 
 /* Structured starting fields of the exact solutions (section "Exact
@@ -269,8 +280,9 @@ rt_status rt_spectrum_peak(rt_handle *h, int ring, int *mx, int *my, double *pow
  * exchange and twiddle pattern.  rt_autotune times the column sweep of a
  * scratch n x n field on the current device for every width that fits and
  * every order (reps launches each, CUDA events) and records the fastest pair
- * for this process; handles created afterwards with col_tile = 0 use both
- * (batches and servers use the width).  rt_tune_set / rt_tune_set_order
+ * for this process; handles, batches and servers created afterwards with
+ * col_tile = 0 use both (per-class batch launches; mixed launches use order
+ * 0), so a batch slot or a served request gives the bits of a handle.  rt_tune_set / rt_tune_set_order
  * record a width or an order directly (e.g. loaded from a JSON cache file by
  * the Python binding); rt_tune_get reports the width in use for n (tuned,
  * or the built-in default; *tuned says which) and rt_tune_get_order the
@@ -493,13 +505,14 @@ rt_status rt_debug_fail_alloc(int after);
  * `after`).  rt_debug_fail_alloc(a) is rt_debug_fail_alloc_n(a, 1). */
 rt_status rt_debug_fail_alloc_n(int after, int count);
 
-/* Release every device buffer and graph of the handle (NULL is accepted). */
+/* Release every device buffer and graph of the handle (NULL is accepted).
+ * Infrastructure. */
 rt_status rt_destroy(rt_handle *h);
 
-/* Static, human-readable name of a status code. */
+/* Static, human-readable name of a status code.  Infrastructure. */
 const char *rt_status_string(rt_status s);
 
-/* Library version (major * 10000 + minor * 100 + patch). */
+/* Library version (major * 10000 + minor * 100 + patch).  Infrastructure. */
 int rt_version(void);
 
 #ifdef __cplusplus

@@ -199,6 +199,13 @@ int class_col_tile(int logn, int requested, bool *mixed)
     return requested ? requested : default_col_tile32(logn);
 }
 
+int class_col_order(int logn, int colC, int requested, bool mixed)
+{
+    if (mixed || requested != 0) return 0;
+    const int ord = tuned_col_order32(logn);
+    return ord < col_orders32(logn, colC) ? ord : 0;
+}
+
 static std::vector<MixLaunch> mixed_of(const std::vector<ClassLaunch> &cls)
 {
     std::vector<MixLaunch> m;
@@ -226,7 +233,7 @@ cudaError_t enqueue_sweep(const std::vector<ClassLaunch> &cls, int which, int *e
     }
     for (const ClassLaunch &c : cls) {
         if (c.mixed) continue;
-        e = which == RT_SWEEP_COLUMNS ? launch_col_batch32(c.logn, c.colC, c.d_res, c.nres, c.tw, err, s)
+        e = which == RT_SWEEP_COLUMNS ? launch_col_batch32(c.logn, c.colC, c.d_res, c.nres, c.col_tw(), err, s, c.order)
                                       : launch_row_batch32(c.logn, c.d_res, c.nres, c.tw, err, s);
         if (e != cudaSuccess) return e;
     }
@@ -245,7 +252,7 @@ cudaError_t prepare_classes(const std::vector<ClassLaunch> &cls)
     bool any_mixed = false;
     for (const ClassLaunch &c : cls) {
         if (c.mixed) any_mixed = true;
-        else if ((e = prepare_batch32(c.logn, c.colC)) != cudaSuccess) return e;
+        else if ((e = prepare_batch32(c.logn, c.colC, c.order)) != cudaSuccess) return e;
     }
     return any_mixed ? prepare_mixed32() : cudaSuccess;
 }
@@ -265,7 +272,10 @@ static std::vector<ClassLaunch> class_parts(const std::vector<ClassLaunch> &cls,
         int first = 0;
         for (int q = 0; q < parts; ++q) {
             const int cnt = c.nres / parts + (q < c.nres % parts ? 1 : 0);
-            out.push_back({c.logn, c.colC, c.d_res + first, cnt, c.tw});
+            ClassLaunch part = c;
+            part.d_res = c.d_res + first;
+            part.nres = cnt;
+            out.push_back(part);
             first += cnt;
         }
     }
@@ -338,7 +348,7 @@ static cudaError_t enqueue_class_chain(const ClassLaunch &c, int *err, long long
 {
     cudaError_t e = cudaSuccess;
     for (long long i = 0; i < k && e == cudaSuccess; ++i) {
-        e = launch_col_batch32(c.logn, c.colC, c.d_res, c.nres, c.tw, err, s);
+        e = launch_col_batch32(c.logn, c.colC, c.d_res, c.nres, c.col_tw(), err, s, c.order);
         if (e == cudaSuccess) e = launch_row_batch32(c.logn, c.d_res, c.nres, c.tw, err, s);
     }
     return e;

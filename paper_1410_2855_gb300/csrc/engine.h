@@ -68,6 +68,9 @@ struct ClassLaunch {
     int nres;
     const float2 *tw;
     bool mixed = false;
+    int order = 0;                   // radix order of the column transforms (per-class launches)
+    const float2 *tw_col = nullptr;  // that order's twiddles (order != 0)
+    const float2 *col_tw() const { return order ? tw_col : tw; }
 };
 
 // Process-wide choice for batches and servers created from now on: classes
@@ -80,6 +83,10 @@ void set_batch_mixed(bool on);
 // Column tile width of a new class of side 2^logn: the mixed width when the
 // class runs mixed, else `requested` (0: the tuned or built-in width).
 int class_col_tile(int logn, int requested, bool *mixed);
+// Radix order of a new class's column transforms: the tuned order when the
+// class uses the tuned (or built-in) tile width in per-class launches, as a
+// handle would; 0 otherwise.
+int class_col_order(int logn, int colC, int requested, bool mixed);
 
 // One bounce of every class: all column sweeps, then all row sweeps.
 cudaError_t enqueue_classes_bounce(const std::vector<ClassLaunch> &cls, int *err, cudaStream_t s);

@@ -27,6 +27,8 @@ struct Slot {
 struct SizeClass {
     int logn = 0, colC = 4;
     bool mixed = false;  // runs in the launches shared across sizes
+    int order = 0;       // radix order of the column transforms
+    float2 *tw_col = nullptr;  // that order's twiddles (order != 0)
     std::vector<int> slots;
     BatchRes *d_res = nullptr;
     float2 *tw = nullptr;
@@ -67,7 +69,8 @@ cudaError_t start_slot(rt_batch *b, int i)
 std::vector<ClassLaunch> launches(rt_batch *b)
 {
     std::vector<ClassLaunch> v;
-    for (SizeClass &c : b->classes) v.push_back({c.logn, c.colC, c.d_res, (int)c.slots.size(), c.tw, c.mixed});
+    for (SizeClass &c : b->classes)
+        v.push_back({c.logn, c.colC, c.d_res, (int)c.slots.size(), c.tw, c.mixed, c.order, c.tw_col});
     return v;
 }
 
@@ -79,6 +82,7 @@ void release(rt_batch *b)
     for (SizeClass &c : b->classes) {
         if (c.d_res) cudaFree(c.d_res);
         if (c.tw) cudaFree(c.tw);
+        if (c.tw_col) cudaFree(c.tw_col);
     }
     if (b->ctl) cudaFree(b->ctl);
     if (b->err) cudaFree(b->err);
@@ -197,6 +201,7 @@ rt_status rt_batch_create(const rt_job *jobs, int count, const rt_opts *opts, rt
             c.logn = logn;
             c.colC = class_col_tile(logn, o.col_tile, &c.mixed);
             if (!c.mixed && !col_tile_ok32(logn, c.colC)) return fail(RT_EINVAL);
+            c.order = class_col_order(logn, c.colC, o.col_tile, c.mixed);
             it = class_of.emplace(logn, (int)b->classes.size()).first;
             b->classes.push_back(c);
         }
@@ -214,6 +219,11 @@ rt_status rt_batch_create(const rt_job *jobs, int count, const rt_opts *opts, rt
         if (dev_alloc(&c.d_res, sizeof(BatchRes) * c.slots.size()) != cudaSuccess) return fail(RT_ENOMEM);
         if (dev_alloc(&c.tw, twb) != cudaSuccess) return fail(RT_ENOMEM);
         b->shared_bytes += sizeof(BatchRes) * c.slots.size() + twb;
+        if (c.order) {
+            if (dev_alloc(&c.tw_col, twb) != cudaSuccess) return fail(RT_ENOMEM);
+            if (launch_twiddles32(1 << c.logn, c.order, c.tw_col, b->stream) != cudaSuccess) return fail(RT_ECUDA);
+            b->shared_bytes += twb;
+        }
     }
     for (int i = 0; i < count; ++i) {
         Slot &s = b->slots[i];

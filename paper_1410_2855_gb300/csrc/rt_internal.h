@@ -84,9 +84,9 @@ struct BatchRes {
 // Batched sweeps over nres resonators of side 2^logn (descriptors `res` in
 // device memory); err receives RT_ETIMEOUT if a copy wait runs out.
 cudaError_t launch_col_batch32(int logn, int colC, const BatchRes *res, int nres, const float2 *tw, int *err,
-                               cudaStream_t s);
+                               cudaStream_t s, int order = 0);
 cudaError_t launch_row_batch32(int logn, const BatchRes *res, int nres, const float2 *tw, int *err, cudaStream_t s);
-cudaError_t prepare_batch32(int logn, int colC);
+cudaError_t prepare_batch32(int logn, int colC, int order = 0);
 int row_groups32(int logn);  // row groups per resonator of a batched row sweep
 
 // One launch per sweep over size classes of uneven sides 128..2048

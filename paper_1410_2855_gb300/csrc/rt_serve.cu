@@ -55,6 +55,8 @@ struct SSlot {
 struct SClass {
     int logn = 0, colC = 4;
     bool mixed = false;         // runs in the launches shared across sizes
+    int order = 0;              // radix order of the column transforms
+    float2 *tw_col = nullptr;   // that order's twiddles (order != 0)
     BatchRes *d_res = nullptr;  // capacity entries
     SlotCtl *ctl = nullptr;     // capacity entries
     float2 *tw = nullptr;
@@ -103,18 +105,24 @@ cudaError_t class_init(rt_server *s, SClass &c, int logn)
 {
     c.logn = logn;
     c.colC = class_col_tile(logn, 0, &c.mixed);
+    c.order = class_col_order(logn, c.colC, 0, c.mixed);
     const int cap = s->opts.max_per_size;
+    const size_t twb = sizeof(float2) * (twiddle_entries(logn) + 1);
     cudaError_t e = dev_alloc(&c.d_res, sizeof(BatchRes) * cap);
     if (e == cudaSuccess) e = dev_alloc(&c.ctl, sizeof(SlotCtl) * cap);
-    if (e == cudaSuccess) e = dev_alloc(&c.tw, sizeof(float2) * (twiddle_entries(logn) + 1));
-    if (e == cudaSuccess) e = c.mixed ? prepare_mixed32() : prepare_batch32(logn, c.colC);
+    if (e == cudaSuccess) e = dev_alloc(&c.tw, twb);
+    if (e == cudaSuccess && c.order) e = dev_alloc(&c.tw_col, twb);
+    if (e == cudaSuccess && c.order) e = launch_twiddles32(1 << logn, c.order, c.tw_col, s->stream);
+    if (e == cudaSuccess) e = c.mixed ? prepare_mixed32() : prepare_batch32(logn, c.colC, c.order);
     if (e != cudaSuccess) {  // the class is dropped: release what it holds
         if (c.d_res) cudaFree(c.d_res);
         if (c.ctl) cudaFree(c.ctl);
         if (c.tw) cudaFree(c.tw);
+        if (c.tw_col) cudaFree(c.tw_col);
         c.d_res = nullptr;
         c.ctl = nullptr;
         c.tw = nullptr;
+        c.tw_col = nullptr;
     }
     return e;
 }
@@ -197,7 +205,7 @@ cudaError_t round_graph(rt_server *s, cudaGraphExec_t *out)
     for (auto &kv : s->classes) {
         SClass &c = kv.second;
         if (c.slots.empty()) continue;
-        cl.push_back({c.logn, c.colC, c.d_res, (int)c.slots.size(), c.tw, c.mixed});
+        cl.push_back({c.logn, c.colC, c.d_res, (int)c.slots.size(), c.tw, c.mixed, c.order, c.tw_col});
         key += "/" + std::to_string(c.logn) + ":" + std::to_string(c.slots.size());
     }
     auto it = s->graphs.find(key);
@@ -439,6 +447,7 @@ void release(rt_server *s)
         if (c.d_res) cudaFree(c.d_res);
         if (c.ctl) cudaFree(c.ctl);
         if (c.tw) cudaFree(c.tw);
+        if (c.tw_col) cudaFree(c.tw_col);
     }
     if (s->d_err) cudaFree(s->d_err);
     if (s->capture) cudaStreamDestroy(s->capture);

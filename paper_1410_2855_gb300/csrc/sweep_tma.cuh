@@ -756,7 +756,7 @@ k_col_pair_batch(const BatchRes *__restrict__ res, int nres, const float2 *__res
 }
 
 // One-stage column-pair sweep over nres resonators of one grid size.
-template <int LOGN, int C>
+template <int LOGN, int C, int ORDER = 0>
 __global__ void __launch_bounds__((C / 2) * Plan<LOGN>::T,
                                   pair1_min_blocks((C / 2) * Plan<LOGN>::T, ColStage1<LOGN, C>::total))
 k_col_pair1_batch(const BatchRes *__restrict__ res, int nres, const float2 *__restrict__ tw, int *err)
@@ -795,14 +795,14 @@ k_col_pair1_batch(const BatchRes *__restrict__ res, int nres, const float2 *__re
             if (threadIdx.x == 0) atomicExch(err, ERR_TIMEOUT);
             break;
         }
-        const TabGlobal<LOGN, float2> tab{tw, R.h};
+        const TabGlobal<LOGN, float2, ORDER> tab{tw, R.h};
         cpair v[16];
 #pragma unroll
         for (int si = 0; si < 16; ++si) v[si] = base[(t + si * T) * CP + c2];
         LineBufs<cpair, false> lb{{base + c2, base + c2}, 0, err};
-        fft_line_t<LOGN, -1, CP, false, true>(v, t, lb, tab, sync);
+        fft_line_t<LOGN, -1, CP, false, true, ORDER>(v, t, lb, tab, sync);
         const IssueAfterReads<decltype(issue)> next{issue, nxt, nxt < nitems};
-        fft_line_t<LOGN, +1, CP, false, false>(v, t, lb, tab, sync, next);
+        fft_line_t<LOGN, +1, CP, false, false, ORDER>(v, t, lb, tab, sync, next);
         cpair *col = reinterpret_cast<cpair *>(R.E + (size_t)t * N + tile * C) + c2;
 #pragma unroll
         for (int si = 0; si < 16; ++si) col[(size_t)si * T * (N / 2)] = v[si];

@@ -66,6 +66,28 @@ def test_every_radix_order_matches_the_oracle(n):
         assert rel(runs[(order, 4)][1], o20) <= 1e-3, (order, rel(runs[(order, 4)][1], o20))
 
 
+def test_a_tuned_order_gives_the_same_bits_in_handles_batch_slots_and_served_requests():
+    p = wl.Resonator(n=1024, fresnel=400.0, g0=0.25, T1=900.0, R=0.93, seed=12)
+    tune.rt_tune_set_order(1024, 2)
+    with rt.Resonator.from_params(p, chunk=0) as r:
+        r.step(9)
+        ref = r.field()
+    with rt.Batch([p, wl.Resonator(n=512, fresnel=200.0, g0=0.2, T1=500.0, R=0.95, seed=13)], chunk=4) as b:
+        b.step(9)
+        slot = b.field(0)
+    out = np.zeros((1024, 1024), np.complex64)
+    with rt.Server(chunk=4, budget_bytes=1 << 30) as srv:
+        srv.submit(p, 9, out)
+        srv.drain(120)
+        assert srv.poll()[0].status == 0
+    assert np.array_equal(slot, ref) and np.array_equal(out, ref)
+    tune.rt_tune_set_order(1024, 0)
+    with rt.Resonator.from_params(p, chunk=0) as r:
+        r.step(9)
+        assert not np.array_equal(r.field(), ref)     # a different order rounds differently
+        assert rel(r.field(), ref.astype(np.complex128)) <= 1e-5
+
+
 def test_tuned_choices_round_trip_through_the_cache(tmp_path):
     cache = tmp_path / "tune.json"
     found = tune.autotune(sizes=(256, 1024), reps=10, cache=str(cache))
