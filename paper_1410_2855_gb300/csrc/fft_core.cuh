@@ -371,9 +371,11 @@ __host__ __device__ constexpr int radix_orders(int logn) { return logn % 4 == 0 
 // factors of its output elements.  TabGlobal loads them from global memory
 // (read-only cache) where they are used; TabRegs holds them in registers for
 // the life of a kernel, loaded once.
-template <int LOGN, typename W, int ORDER = 0> struct TabGlobal {
+// SHARED: the tables were staged in shared memory (plain loads there).
+template <int LOGN, typename W, int ORDER = 0, bool SHARED = false> struct TabMem {
     const W *__restrict__ tw;
     const W *__restrict__ post;
+    __device__ __forceinline__ W at(const W *q) const { return SHARED ? *q : __ldg(q); }
     // twiddle (k - 1) + i (R_p - 1) of pass p: input k of butterfly t + i T
     __device__ __forceinline__ void pass(int p, int t, W (&w)[15]) const
     {
@@ -384,14 +386,15 @@ template <int LOGN, typename W, int ORDER = 0> struct TabGlobal {
 #pragma unroll
         for (int i = 0; i < NB; ++i)
 #pragma unroll
-            for (int k = 1; k < R; ++k) w[i * (R - 1) + k - 1] = __ldg(q + (k - 1) * Ns + ((t + i * T) & (Ns - 1)));
+            for (int k = 1; k < R; ++k) w[i * (R - 1) + k - 1] = at(q + (k - 1) * Ns + ((t + i * T) & (Ns - 1)));
     }
     __device__ __forceinline__ void postv(int t, W (&w)[16]) const
     {
 #pragma unroll
-        for (int s = 0; s < 16; ++s) w[s] = __ldg(post + t + s * Plan<LOGN>::T);
+        for (int s = 0; s < 16; ++s) w[s] = at(post + t + s * Plan<LOGN>::T);
     }
 };
+template <int LOGN, typename W, int ORDER = 0> using TabGlobal = TabMem<LOGN, W, ORDER, false>;
 
 template <int LOGN, typename W, int ORDER = 0> struct TabRegs {
     static constexpr int NP = Seq<LOGN, ORDER>::NP;

@@ -42,13 +42,14 @@ static cudaError_t col_launch32(float2 *E, const float2 *tw, const float2 *h, co
         else return k_col_pair1<LOGN, C, ORDER>;
     }();
     constexpr int threads = F::threads;
+    constexpr size_t smem = F::smem_handle;
     static std::atomic<unsigned long long> mask{0};
     static std::atomic<int> per_sm{0};
-    cudaError_t e = ensure_smem(k, F::smem, mask);
+    cudaError_t e = ensure_smem(k, smem, mask);
     if (e != cudaSuccess) return e;
     const int ntiles = (1 << LOGN) / C;
-    const int grid = persistent_grid(k, threads, F::smem, ntiles, per_sm);
-    k<<<grid, threads, F::smem, s>>>(E, tw, h, *static_cast<const CUtensorMap *>(tmap), ntiles, err);
+    const int grid = persistent_grid(k, threads, smem, ntiles, per_sm);
+    k<<<grid, threads, smem, s>>>(E, tw, h, *static_cast<const CUtensorMap *>(tmap), ntiles, err);
     return cudaGetLastError();
 }
 
@@ -117,7 +118,7 @@ template <int LOGN, int C> static cudaError_t col_prep32_c()
         return cudaErrorInvalidValue;
     } else if constexpr (col_tma_fits<LOGN, C>()) {
         static std::atomic<unsigned long long> mask{0};
-        return ensure_smem(ColForm<LOGN, C>::kernel(), ColForm<LOGN, C>::smem, mask);
+        return ensure_smem(ColForm<LOGN, C>::kernel(), ColForm<LOGN, C>::smem_handle, mask);
     } else {
         return col_attr<float, LOGN, C, MODE_DIFF>();
     }

@@ -39,6 +39,8 @@ template <int LOGN, int C> struct ColForm {
     static constexpr int form = RTK_COL_FORM;
     static constexpr int threads = (form == 0 ? C : C / 2) * Plan<LOGN>::T;
     static constexpr size_t smem = form == 2 ? ColStage1<LOGN, C>::total : ColPlan<LOGN, C>::total;
+    // the handle kernel of form 2 may also stage its tables (ColStage1::tabs_fit)
+    static constexpr size_t smem_handle = form == 2 ? ColStage1<LOGN, C>::total_tabs : smem;
     static constexpr auto kernel()
     {
         if constexpr (form == 2) return k_col_pair1<LOGN, C>;

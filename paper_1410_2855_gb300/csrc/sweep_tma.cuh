@@ -469,12 +469,26 @@ k_col_pair(float2 *E, const float2 *__restrict__ tw, const float2 *__restrict__ 
 // exchanges overlap another's arithmetic, and each block's next copy is
 // issued as soon as its last exchange has been read (before the inverse
 // transform's last pass and the store).  Bit-identical to k_col_pair.
+// 1: the handle's one-stage column sweep stages its twiddle and propagator
+// tables in shared memory at n >= 2048 where two blocks still fit an SM with
+// them, instead of the L1 cache, where one table load in three missed (ncu,
+// two blocks per SM).  Measured on GB300 (graph-timed sweep): 2048^2
+// with 4-column tiles 24.7 against 25.6 us, 2-column tiles 29.7 against 33.7;
+// at 1024^2 and below, where a block runs about one tile, the copy costs more
+// than it saves (7.6 against 7.1 us).
+#ifndef RTK_COL_TABS
+#define RTK_COL_TABS 1
+#endif
 template <int LOGN, int C> struct ColStage1 {
     static constexpr int N = 1 << LOGN;
     static constexpr int BR = N < 256 ? N : 256;
     static constexpr int NBOX = N / BR;
     static constexpr size_t stage = round128((size_t)C * padded_len(N) * sizeof(float2));
     static constexpr size_t total = 128 + stage;
+    // tables: twiddles of any order (at most N entries) and the N propagator factors
+    static constexpr size_t tabs = round128((size_t)2 * N * sizeof(float2));
+    static constexpr bool tabs_fit = RTK_COL_TABS && LOGN >= 11 && 2 * (total + tabs + 1024) <= 228 * 1024;
+    static constexpr size_t total_tabs = tabs_fit ? total + tabs : total;
 };
 #ifndef RTK_PAIR1_REGS
 #define RTK_PAIR1_REGS 128
@@ -504,9 +518,11 @@ template <typename IssueF> struct IssueAfterReads {
 };
 
 // ORDER: radix order of the column transforms (Seq); tw is that order's table.
+// When they fit (ColStage1::tabs_fit) the tables are staged in shared memory
+// behind the stage once per block.
 template <int LOGN, int C, int ORDER = 0>
 __global__ void __launch_bounds__((C / 2) * Plan<LOGN>::T,
-                                  pair1_min_blocks((C / 2) * Plan<LOGN>::T, ColStage1<LOGN, C>::total))
+                                  pair1_min_blocks((C / 2) * Plan<LOGN>::T, ColStage1<LOGN, C>::total_tabs))
 k_col_pair1(float2 *E, const float2 *__restrict__ tw, const float2 *__restrict__ h,
             const __grid_constant__ CUtensorMap tmap, int ntiles, int *err)
 {
@@ -531,7 +547,18 @@ k_col_pair1(float2 *E, const float2 *__restrict__ tw, const float2 *__restrict__
     __syncthreads();
     int tile = blockIdx.x;
     if (threadIdx.x == 0 && tile < ntiles) issue(tile);
-    const TabGlobal<LOGN, float2, ORDER> tab{tw, h};
+    constexpr bool TABS = L::tabs_fit;
+    const float2 *stw = tw, *sh = h;
+    if constexpr (TABS) {
+        float2 *t2 = reinterpret_cast<float2 *>(sm + L::total);
+        constexpr int NTW = Seq<LOGN, ORDER>::tw_size();
+        for (int i = threadIdx.x; i < NTW; i += blockDim.x) t2[i] = __ldg(tw + i);
+        for (int i = threadIdx.x; i < N; i += blockDim.x) t2[N + i] = __ldg(h + i);
+        __syncthreads();
+        stw = t2;
+        sh = t2 + N;
+    }
+    const TabMem<LOGN, float2, ORDER, TABS> tab{stw, sh};
     for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
         const int nxt = tile + (int)gridDim.x;
         const bool late = !mbar_wait(&bar[0], (uint32_t)(it & 1));
