@@ -504,6 +504,14 @@ rt_status rt_debug_fail_alloc(int after);
  * (count < 0: every one from the after-th on, until cancelled by a negative
  * `after`).  rt_debug_fail_alloc(a) is rt_debug_fail_alloc_n(a, 1). */
 rt_status rt_debug_fail_alloc_n(int after, int count);
+/* Test of the sweeps' bounded copy waits: one block arms a stage barrier
+ * for a copy that is never issued (with drain != 0 also the second stage,
+ * as if the next item's copy were in flight) and runs the sweeps' own stage
+ * wait, which gives up after its limit (about 2 s; twice that with drain)
+ * with nothing left in flight.  *device_status receives the block's error
+ * word (RT_ETIMEOUT expected).  Returns RT_OK once the probe has ended,
+ * RT_ENOMEM or RT_ECUDA on a host-side failure, RT_EINVAL for NULL. */
+rt_status rt_debug_wait_probe(int drain, int *device_status);
 
 /* Release every device buffer and graph of the handle (NULL is accepted).
  * Infrastructure. */

@@ -139,6 +139,7 @@ def lib() -> ctypes.CDLL:
             "rt_serve_destroy": [vp],
             "rt_debug_fail_alloc": [i],
             "rt_debug_fail_alloc_n": [i, i],
+            "rt_debug_wait_probe": [i, ctypes.POINTER(i)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -265,6 +266,15 @@ def rt_debug_fail_alloc_n(after: int, count: int):
     """Fault injection (test hook): `count` consecutive device allocations
     starting with the after-th fail as out of memory (count < 0: all of them)."""
     _check(lib().rt_debug_fail_alloc_n(int(after), int(count)), "rt_debug_fail_alloc_n")
+
+
+def rt_debug_wait_probe(drain: bool = False) -> int:
+    """Test hook: run the sweeps' bounded copy wait on a barrier that no copy
+    completes; returns the device error word once the wait has given up
+    (RT_ETIMEOUT expected)."""
+    st = ctypes.c_int()
+    _check(lib().rt_debug_wait_probe(1 if drain else 0, ctypes.byref(st)), "rt_debug_wait_probe")
+    return st.value
 
 
 def rt_set_field_pattern(h, pattern: rt_pattern):

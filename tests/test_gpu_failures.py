@@ -4,7 +4,11 @@ handle's and a batch's set-up returns RT_ENOMEM and releases what was
 allocated; a resonator whose gain diverges reports RT_ENUMERIC from its
 device error word and stays usable for reads; the serving loop admits a
 request once a failed allocation is retried, and posts RT_ENOMEM for a
-request that cannot be placed even with nothing else resident."""
+request that cannot be placed even with nothing else resident; the sweeps'
+bounded copy waits give up on a copy that never completes and report
+RT_ETIMEOUT, and the context stays usable."""
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -115,3 +119,17 @@ def test_divergent_gain_reports_a_numeric_error():
             r.sync()
         assert ei.value.status == rt.RT_ENUMERIC
         assert r.stats().last_error == rt.RT_ENUMERIC
+
+
+@pytest.mark.parametrize("drain", [False, True])
+def test_copy_waits_are_bounded_and_the_context_survives(drain):
+    # a stage barrier armed for bytes that no copy delivers: the sweeps' own
+    # wait gives up after its limit (and, with drain, so does the wait for
+    # the next stage) and records RT_ETIMEOUT; nothing faults or hangs
+    t0 = time.perf_counter()
+    assert rt.rt_debug_wait_probe(drain) == rt.RT_ETIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    p = wl.Resonator(n=128, fresnel=60.0, g0=0.2, T1=500.0, R=0.9, seed=5)
+    with rt.Resonator.from_params(p, chunk=0) as h:
+        h.step(3)
+        assert h.stats().bounces == 3 and np.isfinite(h.stats().mean_intensity)

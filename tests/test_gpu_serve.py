@@ -8,7 +8,7 @@ import time
 import numpy as np
 import pytest
 
-from paper_1410_2855_gb300 import build, rt, workloads as wl
+from paper_1410_2855_gb300 import build, rt, tune, workloads as wl
 
 pytestmark = pytest.mark.gpu
 
@@ -25,7 +25,15 @@ def alone(p, nb):
         return h.field(), h.stats().mean_intensity
 
 
-def test_each_request_matches_its_run_alone():
+@pytest.fixture(params=[False, True], ids=["per_class", "mixed"])
+def launch_form(request):
+    tune.rt_tune_set_batch_mixed(request.param)
+    yield request.param
+    tune.rt_tune_set_batch_mixed(False)
+
+
+def test_each_request_matches_its_run_alone(launch_form):
+    # in every launch form (the classes are set up while the form is in force)
     reqs = [(wl.Resonator(n=64, fresnel=30.0, g0=0.25, T1=500.0, R=0.95, seed=21), 37),
             (wl.Resonator(n=128, fresnel=50.0, g0=0.2, T1=800.0, R=0.9, seed=22), 120),
             (wl.Resonator(n=256, fresnel=300.0, g0=0.3, T1=1000.0, R=0.95, seed=23), 75),

@@ -104,18 +104,19 @@ def test_tuned_choices_round_trip_through_the_cache(tmp_path):
 
 
 def test_batch_launch_form_does_not_change_the_fields():
+    # chunk 5 of 12 bounces: two chunks (graphs) and two bounces outside one
     jobs = [wl.Resonator(n=s, fresnel=150.0, g0=0.25, T1=800.0, R=0.93, seed=90 + j)
             for j, s in enumerate((128, 256, 512, 1024, 256, 2048, 64))]
-    fields = {}
+    fields, means = {}, {}
     for mixed in (True, False):
         tune.rt_tune_set_batch_mixed(mixed)
         assert tune.rt_tune_get_batch_mixed() is mixed
         with rt.Batch(jobs, chunk=5) as b:
             b.step(12)
             fields[mixed] = [b.field(i) for i in range(len(jobs))]
-            means = [b.stats(i).mean_intensity for i in range(len(jobs))]
-        fields[(mixed, "mean")] = means
+            means[mixed] = [b.stats(i).mean_intensity for i in range(len(jobs))]
+            assert all(b.stats(i).bounces == 12 for i in range(len(jobs)))
     for a, c in zip(fields[True], fields[False]):
         assert np.array_equal(a, c)
-    for a, c in zip(fields[(True, "mean")], fields[(False, "mean")]):
+    for a, c in zip(means[True], means[False]):
         assert abs(a - c) <= 1e-12 * abs(c)
