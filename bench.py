@@ -556,9 +556,15 @@ def run_ours(args):
         col_tile, tile_source = args.col_tile, "fixed on the command line"
     else:
         # column-sweep tile width and radix order for this GPU (2048^2 and the larger-than-L2 4096^2)
-        col_tile, _ = tune.rt_autotune(params[0].n, reps=50)
+        # first the sweep alone, then whole bounces of the resonators as this
+        # run steps them (one stream each), which decides: a tile that is
+        # fastest alone can hold shared memory the other stream's sweeps need
+        kernel_pick = tune.rt_autotune(params[0].n, reps=50)[0], tune.rt_tune_get_order(params[0].n)[0]
+        col_tile, order_pick, _ = tune.rt_autotune_concurrent(params[0].n, len(params), bounces=100, reps=3)
         tune.rt_autotune(4096, reps=20)
-        tile_source = "autotuned at start-up"
+        tune.rt_autotune_concurrent(4096, 2, bounces=20, reps=3)
+        tile_source = (f"autotuned at start-up on whole bounces of the {len(params)} resonators on their streams "
+                       f"(the column sweep alone picked tile {kernel_pick[0]}, order {kernel_pick[1]})")
     col_order = tune.rt_tune_get_order(params[0].n)[0]
     streams = [torch.cuda.Stream(device=dev) for _ in params]
     res = [rt.Resonator.from_params(p, precision=rt.RT_FP32, cuda_stream=s.cuda_stream, chunk=B)

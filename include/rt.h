@@ -289,6 +289,20 @@ rt_status rt_spectrum_peak(rt_handle *h, int ring, int *mx, int *my, double *pow
  * order and the number of orders n offers.  Every order computes the same
  * DFT; the roundings differ.  Not part of the paper's method. */
 rt_status rt_autotune(int n, int reps, int *best_col_tile, double *best_us);
+/* The same choice made for the work as it runs: `resonators` (1..16) n x n
+ * FP32 handles (N_F 1000, default pump, g0 0.3, T1 1e4, R 0.9), each on a
+ * stream of its own with one CUDA graph per `bounces` (1..1e5) bounces, are
+ * stepped together for every width that fits and every order; the pair with
+ * the highest rate (best of `reps` >= 1 timings, host clock around the steps
+ * and the waits) is recorded as rt_autotune records its pair, and written to
+ * *best_col_tile, *best_order and *best_rate (round trips/s over all the
+ * resonators).  A column sweep timed alone and the same sweep sharing the
+ * GPU with other resonators' sweeps can favour different pairs (a wider tile
+ * holds more shared memory per block, which the concurrent sweeps then
+ * cannot use).  Allocates and frees the handles' memory; blocks.  RT_EINVAL
+ * for arguments out of range; on a failure the earlier choice stays. */
+rt_status rt_autotune_concurrent(int n, int resonators, int bounces, int reps, int *best_col_tile, int *best_order,
+                                 double *best_rate);
 rt_status rt_tune_set(int n, int col_tile);
 rt_status rt_tune_get(int n, int *col_tile, int *tuned);
 rt_status rt_tune_set_order(int n, int order);

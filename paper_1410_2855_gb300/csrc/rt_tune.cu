@@ -1,4 +1,9 @@
-// Autotuning of the column sweep's tile width (include/rt.h, rt_autotune).
+// Autotuning of the column sweep's tile width and radix order (include/rt.h,
+// rt_autotune: the sweep alone; rt_autotune_concurrent: whole bounces of
+// resonators running together).
+#include <chrono>
+#include <vector>
+
 #include "engine.h"
 #include "fft_core.cuh"
 
@@ -68,6 +73,75 @@ rt_status rt_autotune(int n, int reps, int *best_col_tile, double *best_us)
     set_tuned_col_order32(logn, best_order);
     *best_col_tile = best;
     *best_us = best_t;
+    return RT_OK;
+}
+
+rt_status rt_autotune_concurrent(int n, int resonators, int bounces, int reps, int *best_col_tile, int *best_order,
+                                 double *best_rate)
+{
+    if (!best_col_tile || !best_order || !best_rate || n < 32 || n > 4096 || (n & (n - 1)) || resonators < 1 ||
+        resonators > 16 || bounces < 1 || bounces > 100000 || reps < 1)
+        return RT_EINVAL;
+    const int logn = log2_of(n);
+    const int keep_tile = tuned_col_tile32(logn), keep_order = tuned_col_order32(logn);
+    std::vector<cudaStream_t> streams(resonators, nullptr);
+    rt_status st = RT_OK;
+    for (cudaStream_t &s : streams)
+        if (st == RT_OK && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) st = RT_ECUDA;
+    int best = 0, best_o = 0;
+    double best_r = 0.0;
+    for (int colC : {2, 4, 8, 16}) {
+        if (st != RT_OK || !col_tile_ok32(logn, colC)) continue;
+        for (int o = 0; o < col_orders32(logn, colC) && st == RT_OK; ++o) {
+            // handles created with col_tile = 0 take the tuned pair
+            set_tuned_col_tile32(logn, colC);
+            set_tuned_col_order32(logn, o);
+            std::vector<rt_handle *> hs(resonators, nullptr);
+            for (int i = 0; i < resonators && st == RT_OK; ++i) {
+                rt_opts op;
+                rt_opts_default(&op);
+                op.cuda_stream = streams[i];
+                op.chunk = bounces;
+                op.history_cap = 0;
+                op.seed += (unsigned long long)i;
+                st = rt_create(n, 1000.0, nullptr, 0.3, 1e4, 0.9, &op, &hs[i]);
+            }
+            auto run = [&]() {
+                for (rt_handle *h : hs)
+                    if (st == RT_OK) st = rt_step(h, bounces);
+                for (rt_handle *h : hs)
+                    if (st == RT_OK) st = rt_sync(h);
+            };
+            run();  // warm-up: graph capture, first touch
+            double t = 1e300;
+            for (int r = 0; r < reps && st == RT_OK; ++r) {
+                const auto t0 = std::chrono::steady_clock::now();
+                run();
+                const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+                t = dt < t ? dt : t;
+            }
+            for (rt_handle *h : hs) rt_destroy(h);
+            if (st != RT_OK) break;
+            const double rate = (double)resonators * bounces / t;
+            if (rate > best_r) {
+                best_r = rate;
+                best = colC;
+                best_o = o;
+            }
+        }
+    }
+    for (cudaStream_t s : streams)
+        if (s) cudaStreamDestroy(s);
+    if (st != RT_OK || !best) {  // leave the earlier choice in force
+        set_tuned_col_tile32(logn, keep_tile);
+        set_tuned_col_order32(logn, keep_order);
+        return st != RT_OK ? st : RT_EINVAL;
+    }
+    set_tuned_col_tile32(logn, best);
+    set_tuned_col_order32(logn, best_o);
+    *best_col_tile = best;
+    *best_order = best_o;
+    *best_rate = best_r;
     return RT_OK;
 }
 

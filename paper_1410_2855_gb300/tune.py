@@ -44,6 +44,20 @@ def rt_autotune(n: int, reps: int = 50):
     return best.value, us.value
 
 
+def rt_autotune_concurrent(n: int, resonators: int = 2, bounces: int = 100, reps: int = 3):
+    """Tile width and radix order for `resonators` n x n resonators stepped
+    together, one stream each (rt_autotune_concurrent); recorded for this
+    process.  Returns (col_tile, order, round trips/s)."""
+    L = _sig()
+    L.rt_autotune_concurrent.argtypes = [ctypes.c_int] * 4 + [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                                              ctypes.POINTER(ctypes.c_double)]
+    L.rt_autotune_concurrent.restype = ctypes.c_int
+    tile, order, rate = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    rt._check(L.rt_autotune_concurrent(n, resonators, bounces, reps, ctypes.byref(tile), ctypes.byref(order),
+                                       ctypes.byref(rate)), "rt_autotune_concurrent")
+    return tile.value, order.value, rate.value
+
+
 def rt_tune_set(n: int, col_tile: int):
     rt._check(_sig().rt_tune_set(n, col_tile), "rt_tune_set")
 

@@ -96,6 +96,20 @@ def test_noalloc_rejects_oversize_and_unsupported_requests_on_the_host(lib):
     assert lib.rt_step_noalloc(64, 100.0, None, 0.2, 1000.0, 0.95, ctypes.byref(o), big, big, 1, None) == rt.RT_EINVAL
 
 
+def test_concurrent_autotune_rejects_arguments_out_of_range(lib):
+    t, o, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    f = lib.rt_autotune_concurrent
+    f.argtypes = [ctypes.c_int] * 4 + [ctypes.c_void_p] * 3
+    args = (ctypes.byref(t), ctypes.byref(o), ctypes.byref(r))
+    assert f(33, 2, 10, 1, *args) == rt.RT_EINVAL        # not a power of two
+    assert f(8192, 2, 10, 1, *args) == rt.RT_EINVAL      # too large
+    assert f(512, 0, 10, 1, *args) == rt.RT_EINVAL       # no resonators
+    assert f(512, 17, 10, 1, *args) == rt.RT_EINVAL      # too many
+    assert f(512, 2, 0, 1, *args) == rt.RT_EINVAL        # no bounces
+    assert f(512, 2, 10, 0, *args) == rt.RT_EINVAL       # no timings
+    assert f(512, 2, 10, 1, None, args[1], args[2]) == rt.RT_EINVAL
+
+
 def test_null_handles_are_rejected(lib):
     assert lib.rt_step(None, 1) == rt.RT_EINVAL
     assert lib.rt_read_field_at(None, 0.5, None, 0) == rt.RT_EINVAL

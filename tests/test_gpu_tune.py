@@ -40,6 +40,22 @@ def test_autotune_picks_a_width_and_order_that_fit():
     assert orders == 3 and 0 <= order < orders
 
 
+def test_concurrent_autotune_records_a_pair_that_matches_the_oracle():
+    n = 512
+    tile, order, rate = tune.rt_autotune_concurrent(n, resonators=2, bounces=10, reps=1)
+    assert tile in (2, 4, 8, 16) and 0 <= order < tune.rt_tune_get_order(n)[1] and rate > 0
+    assert tune.rt_tune_get(n) == (tile, True) and tune.rt_tune_get_order(n)[0] == order
+    # a handle created now runs the recorded pair and stays within the one-bounce bar
+    p = wl.Resonator(n=n, fresnel=150.0, g0=0.25, T1=1000.0, R=0.95, seed=4)
+    E0 = wl.smooth_field(n, 2, 1.0, dtype=np.complex64)
+    q = orc.make_params(n, orc.alpha_from_fresnel(p.fresnel, p.d_over_w), p.g0, p.T1, p.R)
+    o1, _, _ = orc.run(q, E0.astype(np.complex128), orc.pump(q), 1, nthreads=4, history=False)
+    with rt.Resonator.from_params(p, chunk=0) as r:
+        r.set_field(E0)
+        r.step(1)
+        assert rel(r.field(), o1) <= 1e-5
+
+
 @pytest.mark.parametrize("n", [128, 512, 1024, 2048])
 def test_every_radix_order_matches_the_oracle(n):
     p = wl.Resonator(n=n, fresnel=300.0 * n / 1024, g0=0.25, T1=1000.0, R=0.95, seed=3)
