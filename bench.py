@@ -846,7 +846,8 @@ def comparisons(args, rt, torch, main, streams, params, res, E0, N0, rank, world
         "peak_kind": f"of {peak_kind}"}
 
     # ---- batched parameter sweep: 256 resonators of side 256/512/1024 in one graph per 100 bounces;
-    # the launch form (one launch per sweep across sizes, or one per size class) autotuned first
+    # the launch form (one launch per sweep across sizes, or one per size class) and the graph chains
+    # per class autotuned first
     jobs = wl.batch_sweep(count=256, sides=(256, 512, 1024))
     form = tune.autotune_batch(jobs, bounces=100, cuda_stream=main.cuda_stream)
     with torch.cuda.stream(main):
@@ -867,8 +868,8 @@ def comparisons(args, rt, torch, main, streams, params, res, E0, N0, rank, world
                             "g0 U[0.1,0.3], T1 U[1e3,1e4], R=0.95; one CUDA graph per 100 bounces",
                 "round_trips_per_s": len(jobs) * 200 / secs, "point_bounces_per_s": Pb * 200 / secs,
                 "hbm_frac": 40 * Pb * 200 / secs / 1e9 / peak, "footprint_bytes": bt.footprint(),
-                "launch_form": "one launch per sweep across sizes (3 graph branches)" if form["mixed"]
-                else "one launch per sweep and size class (3 graph branches per class)",
+                "launch_form": (f"one launch per sweep across sizes ({form['split']} graph chains)" if form["mixed"]
+                                else f"one launch per sweep and size class ({form['split']} graph chains per class)"),
                 "autotune_round_trips_per_s": form["round_trips_per_s"]}
 
     # ---- serving: the first requests of the seeded 50 req/s Poisson stream

@@ -321,6 +321,16 @@ rt_status rt_tune_get_order(int n, int *order, int *orders);
  * tune.autotune_batch times both on a batch and keeps the faster. */
 rt_status rt_tune_set_batch_mixed(int mixed);
 rt_status rt_tune_get_batch_mixed(int *mixed);
+/* Graph branches of batches: a batch's graph of `chunk` bounces runs each
+ * size class (or, in the mixed form, the mixed launches) as `parts` chains
+ * of consecutive resonators on streams of their own, which overlap one
+ * another's phases and tails.  parts = 0 (the default) takes ceil(3 / c)
+ * parts for c chains at one part each, about three chains in all; 1..8 sets
+ * the parts per class for graphs captured from now on (the fields do not
+ * depend on it).  The Python binding's tune.autotune_batch times the launch
+ * forms with 1..4 parts and keeps the fastest.  RT_EINVAL outside 0..8. */
+rt_status rt_tune_set_batch_split(int parts);
+rt_status rt_tune_get_batch_split(int *parts);
 
 /* ---- batches of resonators ---------------------------------------------
  * Many independent resonators (eq. conv_map per resonator, each with its

@@ -304,6 +304,20 @@ static std::vector<std::vector<MixLaunch>> mixed_parts(const std::vector<ClassLa
     return out;
 }
 
+static std::atomic<int> g_batch_split{0};
+int batch_split_setting() { return g_batch_split.load(); }
+void set_batch_split(int parts) { g_batch_split.store(parts); }
+
+int batch_split(const std::vector<ClassLaunch> &cls)
+{
+    const int set = g_batch_split.load();
+    if (set > 0) return set;
+    int chains = mixed_of(cls).empty() ? 0 : 1;
+    for (const ClassLaunch &c : cls)
+        if (!c.mixed && c.nres > 0) ++chains;
+    return chains <= 0 ? 1 : (3 + chains - 1) / chains;
+}
+
 // Chains of a capture: the parts of the mixed launches, then the parts of
 // the other classes.
 static size_t chain_count(const std::vector<ClassLaunch> &cls, int split)

@@ -114,9 +114,15 @@ void branches_free(Branches &br);
 cudaError_t capture_class_bounces(const std::vector<ClassLaunch> &cls, int *err, long long k, cudaStream_t cap,
                                   Branches &br, int split);
 
-// Parts per size class: batches (many resonators per class) and serving
-// rounds (few per class, where more, smaller launches cost more than they fill).
-constexpr int kBatchSplit = 3;
+// Parts per size class of a batch's graph.  By default about three chains
+// in all: ceil(3 / c) parts per class for c chains at one part each (every
+// class of per-class launches, and the mixed launches as one).  A value set
+// by set_batch_split (1..8, e.g. by the Python binding's autotune_batch)
+// overrides it; 0 restores the rule.  Serving rounds (few requests per
+// class, where more, smaller launches cost more than they fill) use one.
+int batch_split(const std::vector<ClassLaunch> &cls);
+int batch_split_setting();
+void set_batch_split(int parts);
 constexpr int kServeSplit = 1;
 
 // Device index guard.

@@ -100,9 +100,10 @@ cudaError_t batch_graph(rt_batch *b, long long k, cudaGraphExec_t *out)
     cudaError_t e;
     const std::vector<ClassLaunch> cl = launches(b);
     if ((e = prepare_classes(cl)) != cudaSuccess) return e;
-    if ((e = branches_prepare(b->branches, cl, kBatchSplit)) != cudaSuccess) return e;
+    const int split = batch_split(cl);
+    if ((e = branches_prepare(b->branches, cl, split)) != cudaSuccess) return e;
     if ((e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
-    const cudaError_t le = capture_class_bounces(cl, b->err, k, b->capture, b->branches, kBatchSplit);
+    const cudaError_t le = capture_class_bounces(cl, b->err, k, b->capture, b->branches, split);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(b->capture, &g);
     if (le != cudaSuccess) e = le;

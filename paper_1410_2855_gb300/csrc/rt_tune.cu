@@ -181,6 +181,20 @@ rt_status rt_tune_set_batch_mixed(int mixed)
     return RT_OK;
 }
 
+rt_status rt_tune_set_batch_split(int parts)
+{
+    if (parts < 0 || parts > 8) return RT_EINVAL;
+    set_batch_split(parts);
+    return RT_OK;
+}
+
+rt_status rt_tune_get_batch_split(int *parts)
+{
+    if (!parts) return RT_EINVAL;
+    *parts = batch_split_setting();
+    return RT_OK;
+}
+
 rt_status rt_tune_get_batch_mixed(int *mixed)
 {
     if (!mixed) return RT_EINVAL;

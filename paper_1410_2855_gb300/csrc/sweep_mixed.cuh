@@ -213,23 +213,34 @@ __global__ void __launch_bounds__(kMixRowThreads, 4) k_row_mixed(const __grid_co
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
     auto stage = [](int s) { return sm + 128 + s * kMixRowStage; };
     auto issue = [&](int s, int item) { mix_row_issue(p, item, stage(s), &bar[s]); };
+    // A block runs a contiguous share of the items (BlockRange) and keeps one
+    // running sum per resonator while it works through that resonator's
+    // items, filing it when it moves on: the blocks that touch resonator r,
+    // items [f, f + G), are block_of(f) .. block_of(f + G - 1), and block b
+    // files under slot b - block_of(f).  A finished resonator is skipped in
+    // one step.
+    const BlockRange br(p.nitems);
+    auto next_active = [&](int i) {
+        while (i < br.end) {
+            const MixClass &c = p.c[mix_class(p, i)];
+            const int r = (i - c.item0) / c.per;
+            if (res_active(c.res[r])) return i;
+            i = c.item0 + (r + 1) * c.per;
+        }
+        return br.end;
+    };
     init_stage_barriers(bar);
-    int item = mix_next_active(p, blockIdx.x);
-    if (threadIdx.x == 0 && item < p.nitems) issue(0, item);
-    // A block keeps one running sum per resonator while it works through that
-    // resonator's items and files it when it moves on: the blocks that touch
-    // resonator r are the residues modulo the grid of its items [f, f + G),
-    // min(G, grid) of them, and block b files under slot (b - f) mod grid.
-    const int grid = (int)gridDim.x;
+    int item = next_active(br.lo);
+    if (threadIdx.x == 0 && item < br.end) issue(0, item);
     double dacc = 0.0;
-    for (int it = 0; item < p.nitems; ++it) {
+    for (int it = 0; item < br.end; ++it) {
         const int s = it & 1;
-        const int nxt = mix_next_active(p, item + grid);
-        if (threadIdx.x == 0 && nxt < p.nitems) {
+        const int nxt = next_active(item + 1);
+        if (threadIdx.x == 0 && nxt < br.end) {
             fence_proxy_async_smem();
             issue(s ^ 1, nxt);
         }
-        if (stage_wait_or_abort(bar, it, nxt < p.nitems, err)) break;
+        if (stage_wait_or_abort(bar, it, nxt < br.end, err)) break;
         const int ci = mix_class(p, item);
         const MixClass &c = p.c[ci];
         const int local = item - c.item0, r = local / c.per, grp = local % c.per;
@@ -245,10 +256,11 @@ __global__ void __launch_bounds__(kMixRowThreads, 4) k_row_mixed(const __grid_co
         dacc += (double)acc;
         __syncthreads();  // stage s fully consumed before it is refilled
         const int first = c.item0 + r * c.per;
-        if (nxt >= p.nitems || nxt < first || nxt >= first + c.per) {
-            const int k = (int)((((long long)blockIdx.x - first) % grid + grid) % grid);
+        if (nxt >= br.end || nxt < first || nxt >= first + c.per) {
+            const int b0 = br.block_of(first);
+            const int k = (int)blockIdx.x - b0, arrivals = br.block_of(first + c.per - 1) - b0 + 1;
             const int n = 1 << c.logn;
-            res_finish<kMixRowThreads>(dacc, R.st, k, c.per < grid ? c.per : grid, 1.0 / ((double)n * (double)n));
+            res_finish<kMixRowThreads>(dacc, R.st, k, arrivals, 1.0 / ((double)n * (double)n));
             dacc = 0.0;
         }
         item = nxt;

@@ -97,6 +97,28 @@ __device__ __forceinline__ int next_active_item(const BatchRes *__restrict__ res
     return nitems;
 }
 
+// Contiguous share of a launch's items for this block: block b runs items
+// [lo, end), q or q + 1 of them for q = nitems / grid (a persistent grid
+// never exceeds its items, so q >= 1), and block_of(i) is the block that runs
+// item i.  A row sweep over many resonators uses it so that a block keeps one
+// running mean-intensity sum per resonator over many items and files it once.
+struct BlockRange {
+    int q, rem, lo, end;
+    __device__ __forceinline__ explicit BlockRange(int nitems)
+    {
+        const int grid = (int)gridDim.x, b = (int)blockIdx.x;
+        q = nitems / grid;
+        rem = nitems % grid;
+        lo = b * q + (b < rem ? b : rem);
+        end = lo + q + (b < rem ? 1 : 0);
+    }
+    __device__ __forceinline__ int block_of(int i) const
+    {
+        const int cut = rem * (q + 1);
+        return i < cut ? i / (q + 1) : rem + (i - cut) / q;
+    }
+};
+
 // ---- shared pieces ----------------------------------------------------------
 
 // Bounded wait on a stage barrier; on a timeout the block drains the copy
@@ -611,25 +633,34 @@ k_row_tma_batch(const BatchRes *__restrict__ res, int nres, const float2 *__rest
             bulk_g2s(stage_n(s) + l * N, R.N + row * N, N * sizeof(float), &bar[s]);
         }
     };
-    auto next_active = [&](int i) { return next_active_item(res, G, nitems, i); };
+    // Block b runs the contiguous items [lo, end) (BlockRange), so it stays
+    // with one resonator for many items and files one partial per resonator
+    // it touches: the blocks that touch resonator r are block_of(rG) ..
+    // block_of(rG + G - 1), and block b files under slot b - block_of(rG).
+    // A finished resonator is skipped in one step.
+    const BlockRange br(nitems);
+    const int end = br.end;
+    auto next_active = [&](int i) {
+        while (i < end) {
+            const int r = i / G;
+            if (res_active(res[r])) return i;
+            i = (r + 1) * G;
+        }
+        return end;
+    };
+    int item = next_active(br.lo);
 
     init_stage_barriers(bar);
-    int item = next_active(blockIdx.x);
-    if (threadIdx.x == 0 && item < nitems) issue(0, item);
-    // The blocks that touch an active resonator r are the residues modulo
-    // the grid of its items [rG, rG + G): min(G, grid) of them, and block b
-    // files its partial under slot (b - rG) mod grid, which is < min(G, grid).
-    const int grid = (int)gridDim.x;
-    const int arrivals = G < grid ? G : grid;
+    if (threadIdx.x == 0 && item < end) issue(0, item);
     double dacc = 0.0;
-    for (int it = 0; item < nitems; ++it) {
+    for (int it = 0; item < end; ++it) {
         const int s = it & 1;
-        const int nxt = next_active(item + grid);
-        if (threadIdx.x == 0 && nxt < nitems) {
+        const int nxt = next_active(item + 1);
+        if (threadIdx.x == 0 && nxt < end) {
             fence_proxy_async_smem();
             issue(s ^ 1, nxt);
         }
-        if (stage_wait_or_abort(bar, it, nxt < nitems, err)) break;
+        if (stage_wait_or_abort(bar, it, nxt < end, err)) break;
         const int r = item / G;
         const BatchRes &R = res[r];
         const int grp = item % G;
@@ -658,8 +689,9 @@ k_row_tma_batch(const BatchRes *__restrict__ res, int nres, const float2 *__rest
         }
         dacc += (double)acc;
         __syncthreads();  // stage s fully consumed before it is refilled
-        if (nxt >= nitems || nxt / G != r) {
-            const int k = (int)((((long long)blockIdx.x - (long long)r * G) % grid + grid) % grid);
+        if (nxt >= end || nxt / G != r) {
+            const int first = br.block_of(r * G);
+            const int k = (int)blockIdx.x - first, arrivals = br.block_of(r * G + G - 1) - first + 1;
             res_finish<NT>(dacc, R.st, k, arrivals, 1.0 / ((double)N * (double)N));
             dacc = 0.0;
         }

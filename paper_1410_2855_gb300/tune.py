@@ -28,7 +28,10 @@ def _sig():
     L.rt_tune_set_order.restype = L.rt_tune_get_order.restype = ctypes.c_int
     L.rt_tune_set_batch_mixed.argtypes = [ctypes.c_int]
     L.rt_tune_get_batch_mixed.argtypes = [ctypes.POINTER(ctypes.c_int)]
-    for f in (L.rt_autotune, L.rt_tune_set, L.rt_tune_get, L.rt_tune_set_batch_mixed, L.rt_tune_get_batch_mixed):
+    L.rt_tune_set_batch_split.argtypes = [ctypes.c_int]
+    L.rt_tune_get_batch_split.argtypes = [ctypes.POINTER(ctypes.c_int)]
+    for f in (L.rt_autotune, L.rt_tune_set, L.rt_tune_get, L.rt_tune_set_batch_mixed, L.rt_tune_get_batch_mixed,
+              L.rt_tune_set_batch_split, L.rt_tune_get_batch_split):
         f.restype = ctypes.c_int
     return L
 
@@ -89,25 +92,42 @@ def rt_tune_get_batch_mixed() -> bool:
     return bool(m.value)
 
 
-def autotune_batch(jobs, bounces: int = 100, **batch_opts) -> dict:
+def rt_tune_set_batch_split(parts: int):
+    """Chains per size class of batch graphs captured from now on (0: about
+    three chains in all; 1..8: that many per class)."""
+    rt._check(_sig().rt_tune_set_batch_split(int(parts)), "rt_tune_set_batch_split")
+
+
+def rt_tune_get_batch_split() -> int:
+    m = ctypes.c_int()
+    rt._check(_sig().rt_tune_get_batch_split(ctypes.byref(m)), "rt_tune_get_batch_split")
+    return m.value
+
+
+def autotune_batch(jobs, bounces: int = 100, splits=(1, 2, 3, 4), **batch_opts) -> dict:
     """Time `bounces` bounces of a batch of `jobs` in each launch form (one
-    launch per sweep across sizes, or one per size class; both give the same
-    fields) and keep the faster for batches and servers created afterwards.
-    Returns the form chosen and both rates in round trips per second."""
+    launch per sweep across sizes, or one per size class) with each number
+    of graph chains per class in `splits` (all give the same fields), and
+    keep the fastest pair for batches and servers created afterwards.
+    Returns the pair chosen and every rate in round trips per second."""
     import time
     rates = {}
     for mixed in (False, True):
         rt_tune_set_batch_mixed(mixed)
-        with rt.Batch(jobs, chunk=bounces, **batch_opts) as b:
-            b.step(bounces)
-            b.sync()
-            t0 = time.perf_counter()
-            b.step(bounces)
-            b.sync()
-            rates[mixed] = len(jobs) * bounces / (time.perf_counter() - t0)
+        for parts in splits:
+            rt_tune_set_batch_split(parts)
+            with rt.Batch(jobs, chunk=bounces, **batch_opts) as b:
+                b.step(bounces)
+                b.sync()
+                t0 = time.perf_counter()
+                b.step(bounces)
+                b.sync()
+                rates[(mixed, parts)] = len(jobs) * bounces / (time.perf_counter() - t0)
     best = max(rates, key=rates.get)
-    rt_tune_set_batch_mixed(best)
-    return {"mixed": best, "round_trips_per_s": {"mixed": rates[True], "per_class": rates[False]}}
+    rt_tune_set_batch_mixed(best[0])
+    rt_tune_set_batch_split(best[1])
+    return {"mixed": best[0], "split": best[1],
+            "round_trips_per_s": {("mixed" if m else "per_class") + f"_split{k}": r for (m, k), r in rates.items()}}
 
 
 def autotune(sizes=(256, 512, 1024, 2048), reps: int = 50, cache: str | None = CACHE) -> dict:

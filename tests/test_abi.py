@@ -110,6 +110,16 @@ def test_concurrent_autotune_rejects_arguments_out_of_range(lib):
     assert f(512, 2, 10, 1, None, args[1], args[2]) == rt.RT_EINVAL
 
 
+def test_batch_split_setting_is_checked(lib):
+    assert lib.rt_tune_set_batch_split(9) == rt.RT_EINVAL
+    assert lib.rt_tune_set_batch_split(-1) == rt.RT_EINVAL
+    assert lib.rt_tune_get_batch_split(None) == rt.RT_EINVAL
+    p = ctypes.c_int(-1)
+    assert lib.rt_tune_set_batch_split(2) == rt.RT_OK
+    assert lib.rt_tune_get_batch_split(ctypes.byref(p)) == rt.RT_OK and p.value == 2
+    assert lib.rt_tune_set_batch_split(0) == rt.RT_OK
+
+
 def test_null_handles_are_rejected(lib):
     assert lib.rt_step(None, 1) == rt.RT_EINVAL
     assert lib.rt_read_field_at(None, 0.5, None, 0) == rt.RT_EINVAL

@@ -124,15 +124,21 @@ def test_batch_launch_form_does_not_change_the_fields():
     jobs = [wl.Resonator(n=s, fresnel=150.0, g0=0.25, T1=800.0, R=0.93, seed=90 + j)
             for j, s in enumerate((128, 256, 512, 1024, 256, 2048, 64))]
     fields, means = {}, {}
-    for mixed in (True, False):
-        tune.rt_tune_set_batch_mixed(mixed)
-        assert tune.rt_tune_get_batch_mixed() is mixed
-        with rt.Batch(jobs, chunk=5) as b:
-            b.step(12)
-            fields[mixed] = [b.field(i) for i in range(len(jobs))]
-            means[mixed] = [b.stats(i).mean_intensity for i in range(len(jobs))]
-            assert all(b.stats(i).bounces == 12 for i in range(len(jobs)))
-    for a, c in zip(fields[True], fields[False]):
-        assert np.array_equal(a, c)
-    for a, c in zip(means[True], means[False]):
-        assert abs(a - c) <= 1e-12 * abs(c)
+    try:
+        for mixed, parts in ((True, 0), (False, 0), (False, 1), (True, 4)):
+            tune.rt_tune_set_batch_mixed(mixed)
+            tune.rt_tune_set_batch_split(parts)
+            assert tune.rt_tune_get_batch_mixed() is mixed and tune.rt_tune_get_batch_split() == parts
+            with rt.Batch(jobs, chunk=5) as b:
+                b.step(12)
+                fields[(mixed, parts)] = [b.field(i) for i in range(len(jobs))]
+                means[(mixed, parts)] = [b.stats(i).mean_intensity for i in range(len(jobs))]
+                assert all(b.stats(i).bounces == 12 for i in range(len(jobs)))
+    finally:
+        tune.rt_tune_set_batch_split(0)
+    ref = (False, 0)
+    for key in fields:
+        for a, c in zip(fields[key], fields[ref]):
+            assert np.array_equal(a, c), key
+        for a, c in zip(means[key], means[ref]):
+            assert abs(a - c) <= 1e-12 * abs(c), key
