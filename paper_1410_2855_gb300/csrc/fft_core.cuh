@@ -373,6 +373,9 @@ __host__ __device__ constexpr int radix_orders(int logn) { return logn % 4 == 0 
 // the life of a kernel, loaded once.
 // SHARED: the tables were staged in shared memory (plain loads there).
 template <int LOGN, typename W, int ORDER = 0, bool SHARED = false> struct TabMem {
+    // loads from shared memory are short: taken where they are used, after
+    // the exchange, so they are not live across it beside the line's values
+    static constexpr bool late = SHARED;
     const W *__restrict__ tw;
     const W *__restrict__ post;
     __device__ __forceinline__ W at(const W *q) const { return SHARED ? *q : __ldg(q); }
@@ -397,6 +400,7 @@ template <int LOGN, typename W, int ORDER = 0, bool SHARED = false> struct TabMe
 template <int LOGN, typename W, int ORDER = 0> using TabGlobal = TabMem<LOGN, W, ORDER, false>;
 
 template <int LOGN, typename W, int ORDER = 0> struct TabRegs {
+    static constexpr bool late = false;
     static constexpr int NP = Seq<LOGN, ORDER>::NP;
     W pw[NP > 1 ? NP - 1 : 1][15];
     W h[16];
@@ -507,6 +511,7 @@ __device__ __forceinline__ void fft_line_t(V (&v)[16], const int t, LineBufs<V, 
     using W = typename table_of<V>::type;
     constexpr int T = Plan<LOGN>::T;
     constexpr bool T16 = (T % 16) == 0;
+    constexpr bool LATE = Tab::late;
     W none[15];
     pass_butterflies<DIR, S::radix(0)>(v, none, false);
 #pragma unroll
@@ -516,10 +521,12 @@ __device__ __forceinline__ void fft_line_t(V (&v)[16], const int t, LineBufs<V, 
         V *line = lb.take();
         V *rd_base = line + padi(t) * CS;
         W w[15];
-        tab.pass(p, t, w);
         W pl[16];
-        if constexpr (POST) {
-            if (p == S::NP - 1) tab.postv(t, pl);
+        if constexpr (!LATE) {
+            tab.pass(p, t, w);
+            if constexpr (POST) {
+                if (p == S::NP - 1) tab.postv(t, pl);
+            }
         }
         if (!PP) sync();
         // outputs of pass p - 1: butterfly t + i T, output r at (j / Ns) Ns R + (j mod Ns) + r Ns
@@ -558,12 +565,14 @@ __device__ __forceinline__ void fft_line_t(V (&v)[16], const int t, LineBufs<V, 
                 if (sm_in<LOGN, CS>(line, &sm_at<CS>(line, t + r * T), lb.chk)) v[r] = sm_at<CS>(line, t + r * T);
         }
         if (p == S::NP - 1) read_done();
+        if constexpr (LATE) tab.pass(p, t, w);
         if (R == 16) pass_butterflies<DIR, 16>(v, w, true);
         else if (R == 8) pass_butterflies<DIR, 8>(v, w, true);
         else if (R == 4) pass_butterflies<DIR, 4>(v, w, true);
         else pass_butterflies<DIR, 2>(v, w, true);
         if constexpr (POST) {
             if (p == S::NP - 1) {
+                if constexpr (LATE) tab.postv(t, pl);
 #pragma unroll
                 for (int s2 = 0; s2 < 16; ++s2) v[s2] = cmul_rn(v[s2], pl[s2]);
             }
