@@ -299,8 +299,12 @@ rt_status rt_autotune(int n, int reps, int *best_col_tile, double *best_us);
  * resonators).  A column sweep timed alone and the same sweep sharing the
  * GPU with other resonators' sweeps can favour different pairs (a wider tile
  * holds more shared memory per block, which the concurrent sweeps then
- * cannot use).  Allocates and frees the handles' memory; blocks.  RT_EINVAL
- * for arguments out of range; on a failure the earlier choice stays. */
+ * cannot use).  Allocates and frees the handles' memory; blocks.  While it
+ * runs, the process-wide choice for side n goes through every candidate, so
+ * handles, batches or servers created meanwhile by other threads may take
+ * one of them (any pair gives results within the same tolerances).
+ * RT_EINVAL for arguments out of range; on a failure the earlier choice
+ * stays. */
 rt_status rt_autotune_concurrent(int n, int resonators, int bounces, int reps, int *best_col_tile, int *best_order,
                                  double *best_rate);
 rt_status rt_tune_set(int n, int col_tile);
