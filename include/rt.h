@@ -317,9 +317,10 @@ rt_status rt_tune_get_order(int n, int *order, int *orders);
  * whatever their sizes; every work item holds the same number of points
  * (column tiles of 8192/n columns, row groups of 2048/n rows) and is
  * dispatched on its grid size inside the launch, so the classes fill one
- * another's tails (batches split their resonators into three such launches,
- * one per graph branch).  mixed = 0 (the default): one launch per sweep and
- * size class, column tiles of the tuned width, three branches per class.
+ * another's tails (a batch's graph may split the resonators into several
+ * such launches, one per graph chain: rt_tune_set_batch_split).  mixed = 0
+ * (the default): one launch per sweep and size class, column tiles of the
+ * tuned width, one or more graph chains per class.
  * Batches created with a nonzero col_tile always use per-class launches.
  * The fields are the same either way; the Python binding's
  * tune.autotune_batch times both on a batch and keeps the faster. */

@@ -76,8 +76,8 @@ struct ClassLaunch {
 // Process-wide choice for batches and servers created from now on: classes
 // of sides 128..2048 share one launch per sweep (true) or each class gets its
 // own launches (false, the default: measured faster for the 256-resonator
-// sweep, 209k against 198k round trips/s, because three branches per class
-// overlap more than three mixed ones).
+// sweep, 251k against 225k round trips/s, because separate per-class chains
+// overlap one another's column and row phases).
 bool batch_mixed();
 void set_batch_mixed(bool on);
 // Column tile width of a new class of side 2^logn: the mixed width when the

@@ -1,7 +1,8 @@
 // Batches of resonators (include/rt.h, rt_batch_*): slots grouped by grid
 // size; each bounce is one batched column sweep and one batched row sweep per
-// size class, captured as CUDA graphs of `chunk` bounces with up to three
-// branches per size class (their launches overlap).  Each slot carries
+// size class, captured as CUDA graphs of `chunk` bounces with one or more
+// chains per size class on graph branches (batch_split; their launches
+// overlap).  Each slot carries
 // a stop-at-bounce target that the kernels honour, so slots with different
 // remaining work share the same launches and graphs.
 #include <climits>
