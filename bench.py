@@ -691,7 +691,10 @@ def run_ours(args):
         "clocks": clk.summary(),
     }
 
-    if not args.no_comparisons:
+    # the comparison legs (larger-than-L2, batch, serving, FP64 and cuFFT
+    # forms, the oracle on the host) run at N = 1 only: a multi-GPU run
+    # measures the scaling of the headline step
+    if not args.no_comparisons and world == 1:
         out.update(comparisons(args, rt, torch, main, streams, params, res, E0, N0, rank, world))
         big = out["larger_than_l2"]["two_4096"]
         # the case whose state really streams through HBM, as a second roofline entry
